@@ -1,0 +1,96 @@
+"""Pins of the seeded input generators (no GPU)."""
+
+import math
+
+import numpy as np
+
+from workload import configs, poses, scenes, trajectories
+
+
+def test_fibonacci_sphere_closed_form():
+    n = 257
+    p = poses.fibonacci_directions(n)
+    assert np.allclose(np.linalg.norm(p, axis=1), 1.0, atol=1e-14)
+    assert np.allclose(np.diff(p[:, 2]), -2.0 / n, atol=1e-14)
+    az = np.arctan2(p[:, 1], p[:, 0])
+    dphi = np.mod(np.diff(az), 2 * math.pi)
+    assert np.allclose(dphi, poses.GOLDEN_ANGLE % (2 * math.pi), atol=1e-12)
+
+
+def test_eq1_uniform_in_ball():
+    """Eq. 1: |p|^3 / r_S^3 is uniform on [0, 1] and directions are isotropic."""
+    x, xr = poses.muller_draws(200_000, seed=4)
+    r_s = 1.0
+    p = poses.muller_ball(x, xr, r_s)
+    u = np.linalg.norm(p, axis=1) ** 3 / r_s ** 3
+    assert np.all(u <= 1.0 + 1e-12)
+    assert abs(u.mean() - 0.5) < 5e-3
+    hist, _ = np.histogram(u, bins=10, range=(0, 1))
+    assert np.all(np.abs(hist / len(u) - 0.1) < 5e-3)
+    dirs = p / np.linalg.norm(p, axis=1, keepdims=True)
+    assert np.all(np.abs(dirs.mean(axis=0)) < 1e-2)
+    # without the cube root the radii would crowd the centre: mean |p|^3 would be 1/4
+    p_wrong = r_s * xr[:, None] * x / np.linalg.norm(x, axis=1, keepdims=True)
+    assert abs((np.linalg.norm(p_wrong, axis=1) ** 3).mean() - 0.25) < 5e-3
+
+
+def test_look_at_orientation():
+    rng = np.random.default_rng(0)
+    poi = np.array([1.0, 2.0, 0.5])
+    pos = poi + rng.standard_normal((100, 3))
+    pos[0] = poi + np.array([0.0, 0.0, 0.7])  # vertical optical axis
+    R = poses.look_at_rotation(pos, poi)
+    for k in range(len(pos)):
+        assert np.allclose(R[k].T @ R[k], np.eye(3), atol=1e-12)
+        assert abs(np.linalg.det(R[k]) - 1.0) < 1e-12
+        to = (poi - pos[k]) / np.linalg.norm(poi - pos[k])
+        assert np.allclose(R[k][:, 2], to, atol=1e-12)
+        if abs(to[2]) < 0.999:
+            assert abs(R[k][2, 0]) < 1e-12          # image x axis horizontal
+            assert R[k][2, 1] <= 1e-12              # image y axis points down
+    q = poses.rotation_to_quaternion(R)
+    assert np.allclose(np.linalg.norm(q, axis=1), 1.0)
+    for k in range(len(pos)):
+        w, x, y, z = q[k]
+        Rq = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                       [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                       [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        assert np.allclose(Rq, R[k], atol=1e-12)
+
+
+def test_scene_generators_are_seeded_and_shaped():
+    a = scenes.boxes_spheres(32, 10, seed=3)
+    b = scenes.boxes_spheres(32, 10, seed=3)
+    assert np.array_equal(a, b) and a.dtype == np.uint8 and a.shape == (32, 32, 32)
+    assert np.all(a[:, :, 16:] == 0) and np.any(a[:, :, :16] == 2)
+    p = scenes.tabletop_probabilities(64, 20, seed=1)
+    assert p.dtype == np.float32 and np.all((p >= 0) & (p <= 1))
+    assert np.any(p == 0.5) and np.any(p > 0.7) and np.any(p < 0.3)
+    r = scenes.room_states(64, 40, 0.4, seed=2)
+    assert abs((r == 0).mean() - 0.4) < 0.08
+
+
+def test_box_fill_uses_voxel_centres():
+    m = np.zeros((8, 8, 8), bool)
+    scenes.fill_box(m, (1.4, 2.6, 0.0), (3.5, 4.4, 1.0))
+    xs = np.unique(np.nonzero(m)[2])
+    ys = np.unique(np.nonzero(m)[1])
+    zs = np.unique(np.nonzero(m)[0])
+    assert list(xs) == [1, 2] and list(ys) == [3] and list(zs) == [0]
+
+
+def test_trajectories_csr():
+    pois = np.array([[1.0, 1.0, 1.0]])
+    p, off = trajectories.random_trajectories(pois, 20, seed=5, len_range=(5, 40))
+    assert off[0] == 0 and off[-1] == len(p) and np.all(np.diff(off) >= 5) and np.all(np.diff(off) <= 40)
+    assert p.dtype == np.float32 and p.shape[1] == 7
+    assert np.allclose(np.linalg.norm(p[:, 3:], axis=1), 1.0, atol=1e-6)
+    d = np.min(np.linalg.norm(p[:, None, :3] - pois[None], axis=2), axis=1)
+    assert np.all(d > 0.3 - 1e-6) and np.all(d < 0.8 + 1e-6)
+
+
+def test_workload_presets_small():
+    w = configs.exact64()
+    assert w.grid.shape == (64, 64, 64) and w.poses.shape == (64, 7) and w.rays_per_pose == 3072
+    d = np.linalg.norm(w.poses[:, :3] - w.pois[0], axis=1)
+    assert np.allclose(d, 0.5, atol=1e-6)
