@@ -1,0 +1,342 @@
+"""Benchmark of the IG raycasting hot path on one or more GPUs.
+
+One step = one pass of the path over one batch of synthetic input: upload
+the step's dense occupancy grid (already resident in HBM) into the bricked
+map, derive the per-voxel gains, cast every ray of every perspective and
+reduce to per-perspective IG (paper Section III).  Default workload
+``prob256``: 256^3 FP32 tabletop of 200 primitives, 1024 perspectives on a
+0.3-0.8 m Fibonacci shell, 160 x 120 rays each, entropy IG until p > 0.7.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+       [--impl reference]
+With N > 1 launch under torch.distributed.run: every rank processes its own
+batch (replicas; no data-path collective), timings are reduced with a max.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IG views/sec & voxel-steps/s at 1 GB300 (exact vs surrogate-pruned, same best view)"
+L2_FLUSH_BYTES = 256 << 20
+BYTES_PER_STEP = {"f32": 4.0, "u8": 1.0, "u2": 0.25}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SOURCES = ["paper_2503_22588_gb300/csrc/nbt_raycast.cu", "paper_2503_22588_gb300/csrc/nbt_internal.cuh"]
+
+
+def describe(w) -> str:
+    return {
+        "prob256": "prob256: 256^3 FP32 tabletop (200 primitives), 1024 views on a 0.3-0.8 m Fibonacci shell, "
+                   "160x120 rays, entropy IG until p>0.7",
+        "exact64": "exact64: 64^3 uint8 states (20 boxes/spheres, half unknown), 64 views on a 0.5 m sphere, "
+                   "64x48 rays, unknown-voxel count",
+        "room512": "room512: 512^3 2-bit states (2000 primitives, 40% unknown), 8 PoIs x 4096 views, "
+                   "320x240 rays, unknown-voxel count",
+    }.get(w.name, w.name)
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per launch of the tile kernel from the committed ncu summary, if current."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    t = json.load(open(TRAFFIC_FILE)).get(workload)
+    if not t or t.get("kernel_hash") != kernel_hash():
+        return None
+    return t.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        top = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * top] or sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload(name: str, rank: int):
+    from workload import configs
+    return configs.WORKLOADS[name](seed=rank)
+
+
+def cpu_baseline(w, budget_s: float = 12.0) -> dict:
+    """The oracle as it stands (FP32 reference walk, FP64 sums) on a bounded sample of the workload."""
+    import oracle
+    threads = os.cpu_count() or 1
+    m = oracle.Map(w.grid, w.voxel_size, w.origin)
+    cam = oracle.camera_of(w.camera)
+    prm = oracle.params(w.metric)
+    n_cal = min(threads, w.n_poses)
+    t0 = time.perf_counter()
+    oracle.views_ig(m, w.poses[:n_cal], cam, prm, "f32", threads)
+    t_cal = time.perf_counter() - t0
+    n = int(min(w.n_poses, max(n_cal, n_cal * budget_s / max(t_cal, 1e-3))))
+    n = max(threads, (n // threads) * threads) if n >= threads else n
+    t0 = time.perf_counter()
+    _, st = oracle.views_ig(m, w.poses[:n], cam, prm, "f32", threads)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "views/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {n} of {w.n_poses} views of the same workload ({int(st.sum())} voxel steps)",
+            "voxel_steps_per_s": float(st.sum()) / dt}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    w = build_workload(args.workload, 0)
+    threads = os.cpu_count() or 1
+    m = oracle.Map(w.grid, w.voxel_size, w.origin)
+    cam = oracle.camera_of(w.camera)
+    prm = oracle.params(w.metric)
+    # a bounded sample per step so that warmup + steps end within a few minutes
+    t0 = time.perf_counter()
+    oracle.views_ig(m, w.poses[:threads], cam, prm, "f32", threads)
+    per_view = (time.perf_counter() - t0) / threads
+    n = int(max(threads, min(w.n_poses, 8.0 / max(per_view, 1e-6))))
+    for _ in range(args.warmup):
+        oracle.views_ig(m, w.poses[:n], cam, prm, "f32", threads)
+    times, steps = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, st = oracle.views_ig(m, w.poses[:n], cam, prm, "f32", threads)
+        times.append(time.perf_counter() - t0)
+        steps += int(st.sum())
+    total = sum(times)
+    value = n * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(w), "views_per_step": n, "parallelism": "host threads"},
+            "voxel_steps_per_s": steps / total,
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": threads, "kind": "oracle",
+                             "sample": f"first {n} of {w.n_poses} views per step"},
+            "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="prob256", choices=["prob256", "exact64", "room512"])
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_2503_22588_gb300 as nbt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    nbt.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    w = build_workload(args.workload, rank)
+    cam = nbt.camera(w.camera.width, w.camera.height, w.camera.fov_h, w.camera.fov_v, w.camera.max_range)
+    prm = nbt.ig_params(w.metric)
+    grid_dev = torch.from_numpy(np.ascontiguousarray(w.grid)).to(dev)
+    poses_dev = torch.from_numpy(w.poses).to(dev)
+    m = nbt.Map(w.n, w.n, w.n, w.voxel_size, w.origin, w.encoding)
+    ws = nbt.workspace(w.n_poses, cam, dev)
+    ig = torch.empty(w.n_poses, dtype=torch.float32, device=dev)
+    steps = torch.empty(w.n_poses, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        m.upload(grid_dev, stream)
+        nbt.views_ig(m, poses_dev, cam, prm, ig, steps, ws, stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    barrier()
+    n_steps_voxel = int(steps.sum().item())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # evict the map from L2 between timed steps (not timed)
+        a, b, c = ev[k]
+        a.record(stream)
+        m.upload(grid_dev, stream)
+        b.record(stream)
+        nbt.views_ig(m, poses_dev, cam, prm, ig, steps, ws, stream)
+        c.record(stream)
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    ig_ms = [b.elapsed_time(c) for a, b, c in ev]
+    total_ms = float(sum(step_ms))
+    ig_mean_ms = float(np.mean(ig_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through the public API with host buffers: pinned host grid and
+    # poses in, per-perspective IG out, copies inside the timed region
+    grid_host = torch.from_numpy(np.ascontiguousarray(w.grid)).pin_memory()
+    poses_host = torch.from_numpy(w.poses).pin_memory()
+    ig_host = torch.empty(w.n_poses, dtype=torch.float32).pin_memory()
+    poses_e2e = torch.empty_like(poses_dev)
+
+    def e2e_step():
+        m.upload(grid_host.numpy(), stream)
+        poses_e2e.copy_(poses_host, non_blocking=True)
+        nbt.views_ig(m, poses_e2e, cam, prm, ig, None, ws, stream, want_steps=False)
+        ig_host.copy_(ig, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, _, c = ev[k]
+        a.record(stream)
+        e2e_step()
+        c.record(stream)
+        c.synchronize()
+        e_ms.append(a.elapsed_time(c))
+    e2e_total = float(sum(e_ms))
+    if dist is not None:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    peak, peak_kind = load_peaks()
+    bps = BYTES_PER_STEP[w.encoding]
+    achieved = n_steps_voxel * bps / (ig_mean_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(args.workload)
+    views_total = world * w.n_poses * args.steps
+    line = {
+        "metric": METRIC,
+        "value": views_total / (total_ms * 1e-3),
+        "unit": "views/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": describe(w), "views_per_gpu": w.n_poses, "rays_per_view": w.rays_per_pose,
+                   "map": f"{w.n}^3 {w.encoding}", "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "step": "map upload+gain derivation + views_ig (tile kernel + reduce)"},
+        "voxel_steps_per_s": world * n_steps_voxel * args.steps / (total_ms * 1e-3),
+        "voxel_steps_per_step": n_steps_voxel,
+        "views_ig_ms": ig_mean_ms,
+        "upload_ms": float(np.mean([a.elapsed_time(b) for a, b, c in ev])),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "ig_tiles_kernel (+views_reduce)",
+                     "algorithmic": f"{bps} B per voxel step x {n_steps_voxel} steps",
+                     "peak_kind": f"{peak_kind} (hbm_gbs)"},
+        "e2e": {"value": views_total / (e2e_total * 1e-3), "unit": "views/s",
+                "h2d_bytes_per_step": int(grid_host.numel() * grid_host.element_size()
+                                          + poses_host.numel() * 4),
+                "d2h_bytes_per_step": int(ig_host.numel() * 4)},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

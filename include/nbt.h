@@ -1,0 +1,223 @@
+/*
+ * nbt.h -- C ABI of the GB300 information-gain (IG) raycasting library.
+ *
+ * The library computes the Online Local Information Distribution of the
+ * paper's Section III: for each camera perspective around a point of
+ * interest, N_E rays are cast from the perspective p_P to endpoints p_E on
+ * the far frustum plane ("Endpoint Calculation"), each ray sums the per-voxel
+ * gains g(v_i) of Eq. 2 over the voxels it crosses up to and including the
+ * first occupied voxel ("IG Calculation", N_O), and the ray IGs are reduced
+ * to one value per perspective (the sum, or the mean g_P of Section III).
+ * Trajectory IG adds the perspective IGs of each pose sequence.
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an int status: NBT_OK (0) or a negative NBT_E*
+ *     code; nbt_status_string() names it.  No C++ exception crosses the ABI.
+ *   - Arguments are validated on the host before anything is enqueued; a
+ *     call that returns an error has enqueued no work.
+ *   - "device" pointers are CUDA global-memory pointers on the device the
+ *     map was created on, which must be the current device of the calling
+ *     thread.  The caller owns every pointer it passes; the library keeps
+ *     none beyond the call, except what a map handle owns.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is asynchronous: results are valid once the stream has
+ *     reached the call.  No call synchronises the device, except
+ *     nbt_map_upload from pageable host memory (CUDA copies pageable memory
+ *     synchronously).
+ *   - A map handle may be used from several host threads; calls that read
+ *     it may overlap on different streams, but an upload must not overlap
+ *     with calls that read the same map.
+ *
+ * Geometry: voxel (x, y, z) covers [origin + x*s, origin + (x+1)*s) on x and
+ * likewise on y and z (s = voxel size).  Dense host/device grids are
+ * x-fastest: linear index (z * ny + y) * nx + x.  A pose is the camera
+ * position (world metres) and the unit quaternion (w, x, y, z) of the
+ * camera-to-world rotation; camera +z is the optical axis, +x right, +y down.
+ *
+ * Traversal: every ray is walked in FP32 by the reference operation order
+ * documented in nbt_trace_segments (bit-exact with the project's CPU
+ * reference walk); gains are accumulated in FP32 per ray, per-perspective
+ * sums in FP64, and returned as float.
+ */
+#ifndef NBT_H
+#define NBT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NBT_API_VERSION 1
+
+/* Status codes. */
+#define NBT_OK 0
+#define NBT_EINVAL (-1)          /* an argument is invalid (NULL, size, range, mismatch) */
+#define NBT_ENOMEM (-2)          /* device or host allocation failed */
+#define NBT_ECUDA (-3)           /* a CUDA runtime call or kernel launch failed */
+#define NBT_ETIMEOUT (-4)        /* a bounded device-side wait gave up */
+#define NBT_EUNSUPPORTED (-5)    /* valid but unsupported combination (e.g. Eq. 2 on a state map) */
+#define NBT_EWORKSPACE (-6)      /* workspace missing or smaller than nbt_workspace_size() */
+
+/* Map encodings (voxel payload stored on the device). */
+#define NBT_U8_STATE 0           /* uint8 state per voxel: 0 unknown, 1 free, >= 2 occupied */
+#define NBT_F32_PROB 1           /* float occupancy probability P(v) per voxel */
+#define NBT_U2_STATE 2           /* states packed 4 per byte (2 bits; 3 reads as occupied) */
+
+/* IG metrics (per-voxel gain g(v), Section III). */
+#define NBT_COUNT_UNKNOWN 0      /* g = 1 if unknown, else 0 */
+#define NBT_PAPER_EQ2 1          /* Eq. 2: 1 - P occupied, P free, 1 unknown (F32 maps only) */
+#define NBT_ENTROPY 2            /* g = H(P) in bits (F32 maps only) */
+
+#define NBT_REDUCE_SUM 0         /* per-perspective IG = sum over the N_E rays */
+#define NBT_REDUCE_MEAN 1        /* per-perspective IG = g_P = sum / N_E (Section III) */
+
+#define NBT_GRID_CORNERS 0       /* endpoint grid includes the four border rays (paper) */
+#define NBT_GRID_CENTERS 1       /* endpoint grid at pixel centres */
+
+#define NBT_RANGE_PLANAR 0       /* endpoints on the far plane at d_Cam (paper) */
+#define NBT_RANGE_SPHERICAL 1    /* every ray has length d_Cam */
+
+typedef struct nbt_map_s *nbt_map; /* opaque; owns the device copy of the map */
+
+/* Map description.  Each of nx, ny, nz in [1, 2048]; nx*ny*nz < 2^31.
+ * brick: 0 (default 8), 4 or 8 -- the edge of the cubic voxel bricks the
+ * device copy is stored in (bricks in Morton order; see nbt_map_create). */
+typedef struct {
+  int32_t nx, ny, nz;
+  float voxel_size;              /* s_Vox, metres, > 0 */
+  float origin[3];               /* world position of the map's min corner */
+  int32_t encoding;              /* NBT_U8_STATE | NBT_F32_PROB | NBT_U2_STATE */
+  int32_t brick;                 /* 0, 4 or 8 */
+} nbt_map_desc;
+
+/* Camera pose: 28 bytes, arrays of poses are tightly packed. */
+typedef struct {
+  float pos[3];                  /* p_P, world metres */
+  float quat[4];                 /* camera-to-world rotation, (w, x, y, z), unit */
+} nbt_pose;
+
+/* Camera: W x H rays per perspective (N_E = W * H), opening angles FoV_h,
+ * FoV_v and range d_Cam (Section III "Endpoint Calculation": half extents
+ * d_h = d_Cam tan(FoV_h / 2), d_v = d_Cam tan(FoV_v / 2)). */
+typedef struct {
+  int32_t width, height;         /* each in [1, 65535] */
+  float fov_h, fov_v;            /* full angles, radians, in (0, pi) */
+  float max_range;               /* d_Cam, metres, > 0 */
+  int32_t grid_mode;             /* NBT_GRID_CORNERS | NBT_GRID_CENTERS */
+  int32_t range_mode;            /* NBT_RANGE_PLANAR | NBT_RANGE_SPHERICAL */
+} nbt_camera;
+
+/* IG parameters. */
+typedef struct {
+  int32_t metric;                /* NBT_COUNT_UNKNOWN | NBT_PAPER_EQ2 | NBT_ENTROPY */
+  float occ_threshold;           /* F32 maps: occupied iff P > occ_threshold (e.g. 0.7) */
+  float free_threshold;          /* F32 maps: free iff P < free_threshold (e.g. 0.3) */
+  int32_t include_hit;           /* 1: the first occupied voxel adds its gain (sum to N_O) */
+  int32_t reduce;                /* NBT_REDUCE_SUM | NBT_REDUCE_MEAN */
+} nbt_ig_params;
+
+/* Name of a status code (static string, never NULL). */
+const char *nbt_status_string(int status);
+
+/* Library ABI version (NBT_API_VERSION) into *version. */
+int nbt_get_version(int32_t *version);
+
+/* Create a map on the current device and allocate its device storage
+ * (zero-filled: all voxels unknown / P = 0).  The grid is stored in B^3
+ * bricks (B = desc->brick), bricks in Morton (Z) order of their brick
+ * coordinates; per-axis offset tables make any voxel's address the sum of
+ * three table entries.  Ownership of the handle passes to the caller, who
+ * releases it with nbt_map_destroy.  Errors: NBT_EINVAL (desc out of range),
+ * NBT_ENOMEM, NBT_ECUDA. */
+int nbt_map_create(const nbt_map_desc *desc, nbt_map *out);
+
+/* Release a map and its device memory (synchronises the device first so no
+ * enqueued call still reads it).  NULL is accepted and ignored. */
+int nbt_map_destroy(nbt_map map);
+
+/* Upload a dense x-fastest grid (the paper's voxel map, Section III) into
+ * the map's bricked device layout.  src holds nx*ny*nz elements: uint8
+ * states for NBT_U8_STATE and NBT_U2_STATE maps, float probabilities for
+ * NBT_F32_PROB maps; bytes must equal that size.  src_on_device: 1 if src is
+ * a device pointer, 0 for host memory (copied in slabs through a staging
+ * buffer the map owns).  Asynchronous on `stream`; invalidates derived gain
+ * tables.  Errors: NBT_EINVAL, NBT_ECUDA. */
+int nbt_map_upload(nbt_map map, const void *src, int64_t bytes, int32_t src_on_device, void *stream);
+
+/* Description and device bytes held by the map (either output may be NULL). */
+int nbt_map_info(nbt_map map, nbt_map_desc *desc, int64_t *device_bytes);
+
+/* Device workspace, in bytes, that nbt_views_ig / nbt_traj_ig need for
+ * n_poses perspectives of camera `cam` (per-tile partial sums).  The caller
+ * allocates it (any device allocator) and passes it to those calls; it may
+ * be reused by calls that do not overlap on the device. */
+int nbt_workspace_size(int64_t n_poses, const nbt_camera *cam, int64_t *bytes);
+
+/* Per-perspective IG (Section III "IG Calculation"): for each of n_views
+ * poses (device array), cast the W x H rays, sum g(v_i) along each ray to
+ * the first occupied voxel, and reduce over rays (params->reduce).
+ *   ig_out:    device float[n_views], written.
+ *   steps_out: device uint64[n_views] or NULL: voxels visited per view
+ *              (the occluding voxel included).
+ *   workspace: device buffer of >= nbt_workspace_size(n_views, cam) bytes,
+ *              16-byte aligned.
+ * n_views == 0 is valid and enqueues nothing.  Errors: NBT_EINVAL,
+ * NBT_EUNSUPPORTED (Eq. 2 / entropy on a state map), NBT_EWORKSPACE,
+ * NBT_ECUDA. */
+int nbt_views_ig(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_camera *cam,
+                 const nbt_ig_params *params, float *ig_out, uint64_t *steps_out, void *workspace,
+                 int64_t workspace_bytes, void *stream);
+
+/* Trajectory IG: per trajectory t, the sum of the perspective IGs of poses
+ * offsets[t] .. offsets[t+1]-1 (device int32 CSR offsets, n_traj + 1
+ * entries, non-decreasing, offsets[0] == 0, offsets[n_traj] == n_poses).
+ * Poses of all trajectories go through one persistent launch that takes
+ * (pose, ray tile) items from a device work queue.
+ *   traj_ig_out: device float[n_traj]; pose_ig_out: device float[n_poses]
+ *   or NULL; workspace as for nbt_views_ig with n_poses perspectives.
+ * Errors as for nbt_views_ig; NBT_EINVAL also if n_poses does not match. */
+int nbt_traj_ig(nbt_map map, const nbt_pose *poses, int64_t n_poses, const int32_t *offsets, int32_t n_traj,
+                const nbt_camera *cam, const nbt_ig_params *params, float *traj_ig_out, float *pose_ig_out,
+                void *workspace, int64_t workspace_bytes, void *stream);
+
+/* Test entry point: the voxels visited by n_rays explicit segments.
+ * o, d: device float[n_rays][3], segment start and displacement in voxel
+ * units (point o + t d, t in [0, 1], relative to the map's min corner).
+ * The walk (Section III "IG Calculation": all voxels from p_P to p_E) runs
+ * in FP32 in this fixed operation order, each operation rounded on its own:
+ *   inv_a = 1 / d_a; clip t0 = (0 - o_a) inv_a, t1 = (N_a - o_a) inv_a,
+ *   t_min = max(0, near), t_max = min(1, far), no voxel unless t_min < t_max;
+ *   start p_a = o_a + t_min d_a, i_a = floor(clamp(p_a, 0, N_a - 1));
+ *   next crossing t_a = ((float)(i_a + [d_a > 0]) - o_a) inv_a, recomputed
+ *   from the index after each step; step x if t_x <= t_y and t_x <= t_z,
+ *   else y if t_y <= t_z, else z; stop when that t is not < t_max or the
+ *   index leaves the map.
+ * params: NULL walks the whole segment; otherwise the walk also stops after
+ * the first occupied voxel as the IG sum does.
+ *   idx_out: device int32[n_rays][cap], linear voxel indices in visit order
+ *            (entries past the count are left untouched);
+ *   n_out:   device int32[n_rays], the number of visited voxels (may
+ *            exceed cap; only cap are stored). */
+int nbt_trace_segments(nbt_map map, const float *o, const float *d, int32_t n_rays, const nbt_ig_params *params,
+                       int32_t *idx_out, int32_t cap, int32_t *n_out, void *stream);
+
+/* Test entry point: the ray segments (voxel units, as nbt_trace_segments
+ * takes them) that the IG kernels generate for every ray of n_views poses,
+ * ray k = j * W + i of view v at row v * W * H + k.  Endpoint grid (Section
+ * III): d_h, d_v in FP64 on the host; x_i = x_0 + i * x_step in FP32 with
+ * x_0 = -d_h, x_step = 2 d_h / (W - 1) (corners) or x_0 = -d_h + d_h / W,
+ * x_step = 2 d_h / W (centres), both rounded once to FP32; likewise y_j;
+ * camera-frame direction (x_i, y_j, d_Cam), scaled to length d_Cam in the
+ * spherical range mode; world direction R c with R from the quaternion;
+ * o = (p_P - origin) / s and d = (R c) / s, with 1/s rounded once to FP32.
+ *   o_out, d_out: device float[n_views * W * H][3]. */
+int nbt_view_segments(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_camera *cam, float *o_out,
+                      float *d_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBT_H */

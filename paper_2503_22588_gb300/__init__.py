@@ -1,0 +1,11 @@
+"""GB300-native information-gain raycasting for Next-Best-Trajectory planning.
+
+The hot path of the paper's Section III (Online Local Information
+Distribution) as hand-written sm_103a CUDA kernels behind a C ABI
+(``include/nbt.h``, ``libnbt.so``); this package is the Python binding.
+"""
+
+from ._lib import LibraryMissing, NbtError, lib  # noqa: F401
+from .api import (Map, camera, ig_params, trace_segments, traj_ig, view_segments, views_ig,  # noqa: F401
+                  workspace, workspace_size)
+from .build import LIB_PATH, build  # noqa: F401

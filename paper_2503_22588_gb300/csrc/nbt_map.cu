@@ -1,0 +1,358 @@
+// nbt_map.cu -- voxel map handle: bricked device layout, upload, derived gains.
+//
+// The paper keeps its voxel map in an octree (UfoMap) on the host and moves
+// map data to the GPU for every ID computation (Section V attributes the
+// GPU's loss at few rays to that allocation and transfer).  Here the map
+// lives on the device for its whole life: nbt_map_create allocates it once,
+// nbt_map_upload re-lays a dense grid into B^3 Morton-ordered bricks with
+// one coalesced pass, and probability maps get a derived per-voxel signed
+// gain table (|value| = g(v) of Eq. 2 / entropy / unknown indicator, sign =
+// occupied) so the traversal reads one float per voxel step.
+
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "nbt_internal.cuh"
+
+namespace nbt {
+
+namespace {
+
+constexpr int64_t kStageBytes = 64ll << 20;
+
+int ceil_log2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// Per-axis brick-index parts.  Morton: the bits of bx, by, bz are
+// interleaved from the least significant end (x, y, z at each level),
+// skipping an axis once it has no bits left.  Used when the padded Morton
+// space is at most twice the brick count; otherwise bricks are linear.
+void brick_parts(int nbx, int nby, int nbz, std::vector<int64_t> &px, std::vector<int64_t> &py,
+                 std::vector<int64_t> &pz, int64_t *slots) {
+  const int L[3] = {ceil_log2(nbx), ceil_log2(nby), ceil_log2(nbz)};
+  const int64_t morton_slots = 1ll << (L[0] + L[1] + L[2]);
+  const int64_t linear_slots = (int64_t)nbx * nby * nbz;
+  px.assign(nbx, 0);
+  py.assign(nby, 0);
+  pz.assign(nbz, 0);
+  if (morton_slots <= 2 * linear_slots) {
+    int pos = 0;
+    int64_t bitpos[3][32];
+    const int maxl = std::max(L[0], std::max(L[1], L[2]));
+    for (int k = 0; k < maxl; ++k)
+      for (int a = 0; a < 3; ++a)
+        if (k < L[a]) bitpos[a][k] = pos++;
+    std::vector<int64_t> *parts[3] = {&px, &py, &pz};
+    const int nb[3] = {nbx, nby, nbz};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < nb[a]; ++b) {
+        int64_t v = 0;
+        for (int k = 0; k < L[a]; ++k)
+          if ((b >> k) & 1) v |= 1ll << bitpos[a][k];
+        (*parts[a])[b] = v;
+      }
+    *slots = morton_slots;
+  } else {
+    for (int b = 0; b < nbx; ++b) px[b] = b;
+    for (int b = 0; b < nby; ++b) py[b] = (int64_t)b * nbx;
+    for (int b = 0; b < nbz; ++b) pz[b] = (int64_t)b * nbx * nby;
+    *slots = linear_slots;
+  }
+}
+
+__device__ __forceinline__ int32_t voxel_offset(const int32_t *tab, int nx, int ny, int x, int y, int z) {
+  return tab[x] + tab[nx + y] + tab[nx + ny + z];
+}
+
+// Dense x-fastest slab (z in [z0, z0 + nzs)) -> bricked uint8 / float.
+template <typename T>
+__global__ void scatter_bricks_kernel(const T *__restrict__ src, T *__restrict__ dst, const int32_t *__restrict__ tab,
+                                      int nx, int ny, int z0, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx);
+    const int64_t r = k / nx;
+    const int y = (int)(r % ny);
+    const int z = z0 + (int)(r / ny);
+    dst[voxel_offset(tab, nx, ny, x, y, z)] = src[k];
+  }
+}
+
+// Dense uint8 states slab -> 2-bit packed bricks.  Each thread packs four
+// x-consecutive voxels (x = 4g .. 4g+3), which are consecutive elements of
+// one brick row because B >= 4 and 4 | B; voxels past nx pack as unknown.
+__global__ void pack_u2_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                               const int32_t *__restrict__ tab, int nx, int ny, int z0, int64_t n_groups) {
+  const int gx = (nx + 3) / 4;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_groups;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(k % gx);
+    const int64_t r = k / gx;
+    const int y = (int)(r % ny);
+    const int zl = (int)(r / ny);
+    const int x0 = 4 * g;
+    const uint8_t *row = src + ((int64_t)zl * ny + y) * nx;
+    uint32_t byte = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int x = x0 + u;
+      uint32_t s = x < nx ? row[x] : 0u;
+      s = s > 2u ? 2u : s;
+      byte |= s << (2 * u);
+    }
+    const int32_t off = voxel_offset(tab, nx, ny, x0, y, z0 + zl);
+    dst[off >> 2] = (uint8_t)byte;
+  }
+}
+
+__device__ __forceinline__ float entropy_bits(float p) {
+  if (!(p > 0.0f && p < 1.0f)) return 0.0f;
+  const float q = 1.0f - p;
+  return -p * log2f(p) - q * log2f(q);
+}
+
+// Bricked probabilities -> signed gains: |g| = g(v), sign bit = occupied.
+__global__ void derive_gain_kernel(const float *__restrict__ p, float *__restrict__ g, int64_t n, int metric,
+                                   float occ_thr, float free_thr) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const float v = p[k];
+    const bool occ = v > occ_thr;
+    const bool fre = v < free_thr;
+    float gain;
+    if (metric == NBT_PAPER_EQ2) {
+      gain = occ ? 1.0f - v : (fre ? v : 1.0f);            // Eq. 2
+    } else if (metric == NBT_ENTROPY) {
+      gain = entropy_bits(v);
+    } else {
+      gain = (!occ && !fre) ? 1.0f : 0.0f;
+    }
+    g[k] = occ ? -fabsf(gain) : fabsf(gain);
+  }
+}
+
+int grid_for(int64_t n) {
+  const int64_t blocks = (n + 255) / 256;
+  return (int)std::min<int64_t>(std::max<int64_t>(blocks, 1), (int64_t)sm_count() * 16);
+}
+
+int elem_size(int encoding) { return encoding == NBT_F32_PROB ? 4 : 1; }
+
+}  // namespace
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+int check_map(nbt_map map) {
+  if (!map) return NBT_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NBT_ECUDA;
+  return dev == map->device ? NBT_OK : NBT_EINVAL;
+}
+
+int prepare_gain(nbt_map map, const nbt_ig_params *prm, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lock(map->mu);
+  if (map->gain_valid && map->gain_metric == prm->metric && map->gain_occ == prm->occ_threshold &&
+      map->gain_free == prm->free_threshold && map->gain_version == map->version)
+    return NBT_OK;
+  derive_gain_kernel<<<grid_for(map->elems), 256, 0, stream>>>((const float *)map->d_payload, map->d_gain,
+                                                               map->elems, prm->metric, prm->occ_threshold,
+                                                               prm->free_threshold);
+  NBT_CUDA_TRY(cudaGetLastError());
+  map->gain_valid = true;
+  map->gain_metric = prm->metric;
+  map->gain_occ = prm->occ_threshold;
+  map->gain_free = prm->free_threshold;
+  map->gain_version = map->version;
+  return NBT_OK;
+}
+
+int payload_kind(nbt_map map, const nbt_ig_params *prm, PayloadKind *kind, const void **payload) {
+  switch (map->desc.encoding) {
+    case NBT_U8_STATE:
+      if (prm && prm->metric != NBT_COUNT_UNKNOWN) return NBT_EUNSUPPORTED;
+      *kind = PAYLOAD_U8;
+      *payload = map->d_payload;
+      return NBT_OK;
+    case NBT_U2_STATE:
+      if (prm && prm->metric != NBT_COUNT_UNKNOWN) return NBT_EUNSUPPORTED;
+      *kind = PAYLOAD_U2;
+      *payload = map->d_payload;
+      return NBT_OK;
+    case NBT_F32_PROB:
+      *kind = PAYLOAD_GAIN_F32;
+      *payload = map->d_gain;
+      return NBT_OK;
+    default:
+      return NBT_EINVAL;
+  }
+}
+
+}  // namespace nbt
+
+using namespace nbt;
+
+extern "C" {
+
+const char *nbt_status_string(int status) {
+  switch (status) {
+    case NBT_OK: return "NBT_OK";
+    case NBT_EINVAL: return "NBT_EINVAL: invalid argument";
+    case NBT_ENOMEM: return "NBT_ENOMEM: allocation failed";
+    case NBT_ECUDA: return "NBT_ECUDA: CUDA runtime error";
+    case NBT_ETIMEOUT: return "NBT_ETIMEOUT: bounded device wait gave up";
+    case NBT_EUNSUPPORTED: return "NBT_EUNSUPPORTED: unsupported combination";
+    case NBT_EWORKSPACE: return "NBT_EWORKSPACE: workspace missing or too small";
+    default: return "unknown status";
+  }
+}
+
+int nbt_get_version(int32_t *version) {
+  if (!version) return NBT_EINVAL;
+  *version = NBT_API_VERSION;
+  return NBT_OK;
+}
+
+int nbt_map_create(const nbt_map_desc *desc, nbt_map *out) {
+  if (!desc || !out) return NBT_EINVAL;
+  *out = nullptr;
+  const nbt_map_desc &d = *desc;
+  if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nx > kMaxDim || d.ny > kMaxDim || d.nz > kMaxDim) return NBT_EINVAL;
+  if ((int64_t)d.nx * d.ny * d.nz >= (1ll << 31)) return NBT_EINVAL;
+  if (!(d.voxel_size > 0.0f) || !isfinite(d.voxel_size)) return NBT_EINVAL;
+  if (!isfinite(d.origin[0]) || !isfinite(d.origin[1]) || !isfinite(d.origin[2])) return NBT_EINVAL;
+  if (d.encoding != NBT_U8_STATE && d.encoding != NBT_F32_PROB && d.encoding != NBT_U2_STATE) return NBT_EINVAL;
+  const int brick = d.brick == 0 ? 8 : d.brick;
+  if (brick != 4 && brick != 8) return NBT_EINVAL;
+
+  nbt_map m = new (std::nothrow) nbt_map_s();
+  if (!m) return NBT_ENOMEM;
+  m->desc = d;
+  m->desc.brick = brick;
+  m->brick = brick;
+  if (cudaGetDevice(&m->device) != cudaSuccess) {
+    delete m;
+    return NBT_ECUDA;
+  }
+  const int lb = brick == 8 ? 3 : 2;
+  m->nbx = (d.nx + brick - 1) / brick;
+  m->nby = (d.ny + brick - 1) / brick;
+  m->nbz = (d.nz + brick - 1) / brick;
+  std::vector<int64_t> px, py, pz;
+  int64_t slots = 0;
+  brick_parts(m->nbx, m->nby, m->nbz, px, py, pz, &slots);
+  const int64_t b3 = (int64_t)brick * brick * brick;
+  m->elems = slots * b3;
+  if (m->elems >= (1ll << 31)) {
+    delete m;
+    return NBT_EINVAL;
+  }
+  std::vector<int32_t> tab((size_t)d.nx + d.ny + d.nz);
+  const int mask = brick - 1;
+  for (int x = 0; x < d.nx; ++x) tab[x] = (int32_t)(px[x >> lb] * b3 + (x & mask));
+  for (int y = 0; y < d.ny; ++y) tab[d.nx + y] = (int32_t)(py[y >> lb] * b3 + (int64_t)(y & mask) * brick);
+  for (int z = 0; z < d.nz; ++z)
+    tab[d.nx + d.ny + z] = (int32_t)(pz[z >> lb] * b3 + (int64_t)(z & mask) * brick * brick);
+
+  m->payload_bytes = d.encoding == NBT_F32_PROB ? m->elems * 4 : (d.encoding == NBT_U2_STATE ? m->elems / 4 : m->elems);
+  const int64_t dense_bytes = (int64_t)d.nx * d.ny * d.nz * elem_size(d.encoding);
+  m->stage_bytes = std::min(dense_bytes, std::max<int64_t>(kStageBytes, (int64_t)d.nx * d.ny * elem_size(d.encoding)));
+  int rc = NBT_OK;
+  if (cudaMalloc(&m->d_payload, (size_t)m->payload_bytes) != cudaSuccess) rc = NBT_ENOMEM;
+  if (rc == NBT_OK && d.encoding == NBT_F32_PROB &&
+      cudaMalloc((void **)&m->d_gain, (size_t)m->elems * 4) != cudaSuccess)
+    rc = NBT_ENOMEM;
+  if (rc == NBT_OK && cudaMalloc((void **)&m->d_tab, tab.size() * sizeof(int32_t)) != cudaSuccess) rc = NBT_ENOMEM;
+  if (rc == NBT_OK && cudaMalloc(&m->d_stage, (size_t)m->stage_bytes) != cudaSuccess) rc = NBT_ENOMEM;
+  if (rc == NBT_OK && cudaMemset(m->d_payload, 0, (size_t)m->payload_bytes) != cudaSuccess) rc = NBT_ECUDA;
+  if (rc == NBT_OK && cudaMemcpy(m->d_tab, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+                          cudaSuccess)
+    rc = NBT_ECUDA;
+  if (rc != NBT_OK) {
+    (void)cudaGetLastError();
+    nbt_map_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return NBT_OK;
+}
+
+int nbt_map_destroy(nbt_map map) {
+  if (!map) return NBT_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != map->device) cudaSetDevice(map->device);
+  cudaDeviceSynchronize();
+  if (map->d_payload) cudaFree(map->d_payload);
+  if (map->d_gain) cudaFree(map->d_gain);
+  if (map->d_tab) cudaFree(map->d_tab);
+  if (map->d_stage) cudaFree(map->d_stage);
+  (void)cudaGetLastError();
+  if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
+  delete map;
+  return NBT_OK;
+}
+
+int nbt_map_upload(nbt_map map, const void *src, int64_t bytes, int32_t src_on_device, void *stream_) {
+  int rc = check_map(map);
+  if (rc != NBT_OK) return rc;
+  if (!src) return NBT_EINVAL;
+  const nbt_map_desc &d = map->desc;
+  const int es = elem_size(d.encoding);
+  const int64_t plane = (int64_t)d.nx * d.ny;
+  if (bytes != plane * d.nz * es) return NBT_EINVAL;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  std::lock_guard<std::mutex> lock(map->mu);
+  const int slab = src_on_device ? d.nz : (int)std::max<int64_t>(1, map->stage_bytes / (plane * es));
+  for (int z0 = 0; z0 < d.nz; z0 += slab) {
+    const int nzs = std::min(slab, d.nz - z0);
+    const char *s = (const char *)src + (int64_t)z0 * plane * es;
+    if (!src_on_device) {
+      NBT_CUDA_TRY(cudaMemcpyAsync(map->d_stage, s, (size_t)(nzs * plane * es), cudaMemcpyHostToDevice, stream));
+      s = (const char *)map->d_stage;
+    }
+    const int64_t n = nzs * plane;
+    if (d.encoding == NBT_U8_STATE) {
+      scatter_bricks_kernel<uint8_t><<<grid_for(n), 256, 0, stream>>>((const uint8_t *)s, (uint8_t *)map->d_payload,
+                                                                      map->d_tab, d.nx, d.ny, z0, n);
+    } else if (d.encoding == NBT_F32_PROB) {
+      scatter_bricks_kernel<float><<<grid_for(n), 256, 0, stream>>>((const float *)s, (float *)map->d_payload,
+                                                                    map->d_tab, d.nx, d.ny, z0, n);
+    } else {
+      const int64_t groups = (int64_t)((d.nx + 3) / 4) * d.ny * nzs;
+      pack_u2_kernel<<<grid_for(groups), 256, 0, stream>>>((const uint8_t *)s, (uint8_t *)map->d_payload, map->d_tab,
+                                                           d.nx, d.ny, z0, groups);
+    }
+    NBT_CUDA_TRY(cudaGetLastError());
+  }
+  map->version += 1;
+  map->gain_valid = false;
+  return NBT_OK;
+}
+
+int nbt_map_info(nbt_map map, nbt_map_desc *desc, int64_t *device_bytes) {
+  if (!map) return NBT_EINVAL;
+  if (desc) *desc = map->desc;
+  if (device_bytes) {
+    int64_t b = map->payload_bytes + (int64_t)(map->desc.nx + map->desc.ny + map->desc.nz) * 4 + map->stage_bytes;
+    if (map->d_gain) b += map->elems * 4;
+    *device_bytes = b;
+  }
+  return NBT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,480 @@
+// nbt_raycast.cu -- per-perspective and per-trajectory IG by voxel raycasting.
+//
+// Section III of the paper: for each perspective, rays from p_P to the
+// endpoint grid on the far frustum plane; each ray sums g(v_i) over the
+// voxels it crosses, up to and including the first occupied one (N_O); the
+// ray IGs of a perspective are summed (or averaged, g_P).
+//
+// GPU mapping.  A work item is one (pose, 32 x 8 ray tile); a CTA of 256
+// threads takes items from a device work queue (one atomicAdd per item) and
+// casts one ray per thread.  Each warp's 32 rays form an 8 x 4 pixel packet,
+// so at any step its lanes read neighbouring voxels of the same bricks.
+// Per ray, the walk runs KAHEAD voxels ahead of the gain accumulation: the
+// voxel sequence does not depend on the map, so KAHEAD addresses are formed
+// first and their loads issued together, and only the occlusion test waits
+// on the data.  Per-ray sums go through a fixed warp-shuffle tree and a
+// fixed 8-warp sum into one 16-byte partial per item; a second kernel adds
+// the partials of each perspective (or trajectory) in a fixed order in FP64,
+// so results do not depend on scheduling.
+
+#include <math.h>
+
+#include <algorithm>
+
+#include "nbt_internal.cuh"
+
+namespace nbt {
+namespace {
+
+constexpr int kAhead = 4;
+
+bool valid_camera(const nbt_camera *c) {
+  if (!c) return false;
+  if (c->width < 1 || c->height < 1 || c->width > 65535 || c->height > 65535) return false;
+  const float pi = 3.14159265358979f;
+  if (!(c->fov_h > 0.0f && c->fov_h < pi) || !(c->fov_v > 0.0f && c->fov_v < pi)) return false;
+  if (!(c->max_range > 0.0f) || !isfinite(c->max_range)) return false;
+  if (c->grid_mode != NBT_GRID_CORNERS && c->grid_mode != NBT_GRID_CENTERS) return false;
+  if (c->range_mode != NBT_RANGE_PLANAR && c->range_mode != NBT_RANGE_SPHERICAL) return false;
+  return true;
+}
+
+bool valid_params(const nbt_ig_params *p) {
+  if (!p) return false;
+  if (p->metric != NBT_COUNT_UNKNOWN && p->metric != NBT_PAPER_EQ2 && p->metric != NBT_ENTROPY) return false;
+  if (p->reduce != NBT_REDUCE_SUM && p->reduce != NBT_REDUCE_MEAN) return false;
+  if (!isfinite(p->occ_threshold) || !isfinite(p->free_threshold)) return false;
+  return true;
+}
+
+// Section III endpoint grid: d_h = d_Cam tan(FoV_h / 2), d_v likewise, in
+// FP64 on the host; the grid start and spacing are each rounded once to FP32.
+CamConst make_cam(nbt_map map, const nbt_camera *c) {
+  CamConst cc;
+  const double dh = (double)c->max_range * tan((double)c->fov_h * 0.5);
+  const double dv = (double)c->max_range * tan((double)c->fov_v * 0.5);
+  const int w = c->width, h = c->height;
+  if (c->grid_mode == NBT_GRID_CORNERS) {
+    cc.x0 = w > 1 ? (float)(-dh) : 0.0f;
+    cc.xstep = w > 1 ? (float)(2.0 * dh / (double)(w - 1)) : 0.0f;
+    cc.y0 = h > 1 ? (float)(-dv) : 0.0f;
+    cc.ystep = h > 1 ? (float)(2.0 * dv / (double)(h - 1)) : 0.0f;
+  } else {
+    cc.x0 = (float)(-dh + dh / (double)w);
+    cc.xstep = (float)(2.0 * dh / (double)w);
+    cc.y0 = (float)(-dv + dv / (double)h);
+    cc.ystep = (float)(2.0 * dv / (double)h);
+  }
+  cc.zc = c->max_range;
+  cc.spherical = c->range_mode == NBT_RANGE_SPHERICAL;
+  cc.W = w;
+  cc.H = h;
+  cc.tiles_x = (w + kTileW - 1) / kTileW;
+  cc.tiles_per_pose = cc.tiles_x * ((h + kTileH - 1) / kTileH);
+  cc.inv_s = (float)(1.0 / (double)map->desc.voxel_size);
+  cc.ox = map->desc.origin[0];
+  cc.oy = map->desc.origin[1];
+  cc.oz = map->desc.origin[2];
+  return cc;
+}
+
+DevMap dev_map(nbt_map map, const void *payload) {
+  DevMap m;
+  m.payload = payload;
+  m.tab = map->d_tab;
+  m.nx = map->desc.nx;
+  m.ny = map->desc.ny;
+  m.nz = map->desc.nz;
+  return m;
+}
+
+int64_t workspace_bytes_for(int64_t n_items) { return 256 + n_items * (int64_t)kPartialBytes; }
+
+// Voxel payload read: gain magnitude, unknown indicator, occupied flag.
+template <int KIND>
+__device__ __forceinline__ void read_voxel(const void *payload, uint32_t off, float &g, uint32_t &unk, bool &occ) {
+  if (KIND == PAYLOAD_GAIN_F32) {
+    const float v = __ldg((const float *)payload + off);
+    occ = (__float_as_uint(v) >> 31) != 0u;
+    g = fabsf(v);
+    unk = 0u;
+  } else if (KIND == PAYLOAD_U8) {
+    const uint32_t s = __ldg((const uint8_t *)payload + off);
+    occ = s >= 2u;
+    unk = s == 0u;
+    g = 0.0f;
+  } else {
+    const uint32_t b = __ldg((const uint8_t *)payload + (off >> 2));
+    const uint32_t s = (b >> ((off & 3u) << 1)) & 3u;
+    occ = s >= 2u;
+    unk = s == 0u;
+    g = 0.0f;
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ uint32_t raw_load(const void *payload, uint32_t off) {
+  if (KIND == PAYLOAD_GAIN_F32) return __float_as_uint(__ldg((const float *)payload + off));
+  if (KIND == PAYLOAD_U8) return __ldg((const uint8_t *)payload + off);
+  return __ldg((const uint8_t *)payload + (off >> 2));
+}
+
+// IG of one ray: walk, read, accumulate, stop after the first occupied voxel.
+template <int KIND>
+__device__ __forceinline__ void ray_ig(const DevMap &m, const int32_t *tab, const float o[3], const float d[3],
+                                       bool include_hit, float &facc, uint32_t &iacc, uint32_t &steps) {
+  Walk w;
+  if (!walk_init(w, o, d, m.nx, m.ny, m.nz)) return;
+  int offx = tab[w.ix], offy = tab[m.nx + w.iy], offz = tab[m.nx + m.ny + w.iz];
+  bool live = true;
+  for (;;) {
+    uint32_t addr[kAhead];
+    bool val[kAhead];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      val[u] = live;
+      addr[u] = (uint32_t)(offx + offy + offz);
+      if (live) live = walk_step(w, m.nx, m.ny, m.nz, tab, offx, offy, offz);
+    }
+    uint32_t raw[kAhead];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) raw[u] = val[u] ? raw_load<KIND>(m.payload, addr[u]) : 0u;
+    bool stop = false;
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      if (val[u] && !stop) {
+        bool occ;
+        if (KIND == PAYLOAD_GAIN_F32) {
+          occ = (raw[u] >> 31) != 0u;
+          const float g = __uint_as_float(raw[u] & 0x7fffffffu);
+          if (!occ || include_hit) facc += g;
+        } else {
+          uint32_t s = raw[u];
+          if (KIND == PAYLOAD_U2) s = (s >> ((addr[u] & 3u) << 1)) & 3u;
+          occ = s >= 2u;
+          iacc += (s == 0u) ? 1u : 0u;  // an occupied voxel is never unknown
+        }
+        steps += 1u;
+        stop = occ;
+      }
+    }
+    if (stop || !live) break;
+  }
+}
+
+// Item = (pose, ray tile); CTA-wide partial sums into partials[item].
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) ig_tiles_kernel(DevMap m, CamConst cc, const float *__restrict__ poses,
+                                                           int64_t n_items, int include_hit,
+                                                           unsigned long long *queue, Partial *partials) {
+  extern __shared__ int32_t stab[];
+  __shared__ float s_f[kThreads / 32];
+  __shared__ uint32_t s_i[kThreads / 32], s_s[kThreads / 32];
+  __shared__ long long s_item;
+  const int ntab = m.nx + m.ny + m.nz;
+  for (int k = threadIdx.x; k < ntab; k += blockDim.x) stab[k] = m.tab[k];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pi = (warp & 3) * 8 + (lane & 7);   // 8 x 4 pixel packet per warp, 4 x 2 warps per tile
+  const int pj = (warp >> 2) * 4 + (lane >> 3);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= n_items) break;
+    const long long pose = item / cc.tiles_per_pose;
+    const int tile = (int)(item - pose * cc.tiles_per_pose);
+    const int i = (tile % cc.tiles_x) * kTileW + pi;
+    const int j = (tile / cc.tiles_x) * kTileH + pj;
+    float facc = 0.0f;
+    uint32_t iacc = 0u, steps = 0u;
+    if (i < cc.W && j < cc.H) {
+      float pz[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) pz[k] = __ldg(poses + pose * 7 + k);
+      float o[3], d[3];
+      ray_segment(cc, pz, i, j, o, d);
+      ray_ig<KIND>(m, stab, o, d, include_hit != 0, facc, iacc, steps);
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      facc += __shfl_xor_sync(0xffffffffu, facc, s);
+      iacc += __shfl_xor_sync(0xffffffffu, iacc, s);
+      steps += __shfl_xor_sync(0xffffffffu, steps, s);
+    }
+    if (lane == 0) {
+      s_f[warp] = facc;
+      s_i[warp] = iacc;
+      s_s[warp] = steps;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Partial p;
+      p.fsum = 0.0f;
+      p.isum = 0u;
+      p.steps = 0u;
+      p.pad = 0u;
+      for (int k = 0; k < kThreads / 32; ++k) {
+        p.fsum += s_f[k];
+        p.isum += s_i[k];
+        p.steps += s_s[k];
+      }
+      partials[item] = p;
+    }
+  }
+}
+
+// One warp per perspective: fixed-order FP64 sum of its tiles' partials.
+__global__ void views_reduce_kernel(const Partial *__restrict__ partials, int64_t n_views, int tiles, int mean,
+                                    double n_rays, float *__restrict__ ig_out, uint64_t *__restrict__ steps_out) {
+  const int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (v >= n_views) return;
+  double f = 0.0;
+  unsigned long long a = 0ull, b = 0ull;
+  for (int t = lane; t < tiles; t += 32) {
+    const Partial p = partials[v * tiles + t];
+    f += (double)p.fsum;
+    a += p.isum;
+    b += p.steps;
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    f += __shfl_xor_sync(0xffffffffu, f, s);
+    a += __shfl_xor_sync(0xffffffffu, a, s);
+    b += __shfl_xor_sync(0xffffffffu, b, s);
+  }
+  if (lane == 0) {
+    double total = f + (double)a;
+    if (mean) total /= n_rays;
+    ig_out[v] = (float)total;
+    if (steps_out) steps_out[v] = b;
+  }
+}
+
+// One warp per trajectory: lanes take whole poses, each pose's IG in FP64
+// (sum or mean over its tiles), then a fixed shuffle tree over lanes.
+// Offsets are clamped to [0, n_poses] so malformed CSR input cannot read
+// outside the partials; it only yields wrong sums.
+__global__ void traj_reduce_kernel(const Partial *__restrict__ partials, const int32_t *__restrict__ offsets,
+                                   int32_t n_traj, int32_t n_poses, int tiles, int mean, double n_rays,
+                                   float *__restrict__ traj_out, float *__restrict__ pose_out) {
+  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= n_traj) return;
+  const int32_t b = min(max(offsets[t], 0), n_poses);
+  const int32_t e = min(max(offsets[t + 1], b), n_poses);
+  double acc = 0.0;
+  for (int32_t p = b + lane; p < e; p += 32) {
+    double f = 0.0;
+    unsigned long long a = 0ull;
+    for (int k = 0; k < tiles; ++k) {
+      const Partial q = partials[(int64_t)p * tiles + k];
+      f += (double)q.fsum;
+      a += q.isum;
+    }
+    double pig = f + (double)a;
+    if (mean) pig /= n_rays;
+    if (pose_out) pose_out[p] = (float)pig;
+    acc += pig;
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  if (lane == 0) traj_out[t] = (float)acc;
+}
+
+__global__ void view_segments_kernel(CamConst cc, const float *__restrict__ poses, int64_t n_rays,
+                                     float *__restrict__ o_out, float *__restrict__ d_out) {
+  const int64_t n_per = (int64_t)cc.W * cc.H;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = r / n_per;
+    const int k = (int)(r - v * n_per);
+    float pz[7];
+    for (int q = 0; q < 7; ++q) pz[q] = poses[v * 7 + q];
+    float o[3], d[3];
+    ray_segment(cc, pz, k % cc.W, k / cc.W, o, d);
+    for (int a = 0; a < 3; ++a) {
+      o_out[r * 3 + a] = o[a];
+      d_out[r * 3 + a] = d[a];
+    }
+  }
+}
+
+template <int KIND>
+__global__ void trace_kernel(DevMap m, const float *__restrict__ o, const float *__restrict__ d, int n_rays,
+                             int use_occ, int32_t *__restrict__ idx_out, int cap, int32_t *__restrict__ n_out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rays) return;
+  const float oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
+  const float dd[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
+  Walk w;
+  int count = 0;
+  if (walk_init(w, oo, dd, m.nx, m.ny, m.nz)) {
+    int offx = m.tab[w.ix], offy = m.tab[m.nx + w.iy], offz = m.tab[m.nx + m.ny + w.iz];
+    for (;;) {
+      if (count < cap) idx_out[(int64_t)r * cap + count] = (w.iz * m.ny + w.iy) * m.nx + w.ix;
+      ++count;
+      if (use_occ) {
+        float g;
+        uint32_t unk;
+        bool occ;
+        read_voxel<KIND>(m.payload, (uint32_t)(offx + offy + offz), g, unk, occ);
+        if (occ) break;
+      }
+      if (!walk_step(w, m.nx, m.ny, m.nz, m.tab, offx, offy, offz)) break;
+    }
+  }
+  n_out[r] = count;
+}
+
+size_t tile_smem(nbt_map map) { return (size_t)(map->desc.nx + map->desc.ny + map->desc.nz) * sizeof(int32_t); }
+
+template <int KIND>
+int launch_tiles(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
+                 int include_hit, void *workspace, cudaStream_t stream) {
+  const size_t smem = tile_smem(map);
+  int per_sm = 0;
+  NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ig_tiles_kernel<KIND>, kThreads, smem));
+  per_sm = std::max(per_sm, 1);
+  const int64_t grid = std::min<int64_t>(n_items, (int64_t)sm_count() * per_sm);
+  unsigned long long *queue = (unsigned long long *)workspace;
+  Partial *partials = (Partial *)((char *)workspace + 256);
+  NBT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream));
+  ig_tiles_kernel<KIND><<<(unsigned)grid, kThreads, smem, stream>>>(dev_map(map, payload), cc, poses, n_items,
+                                                                   include_hit, queue, partials);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+int run_tiles(nbt_map map, const nbt_pose *poses, int64_t n_poses, const nbt_camera *cam,
+              const nbt_ig_params *params, void *workspace, int64_t workspace_bytes, cudaStream_t stream,
+              CamConst *cc_out) {
+  PayloadKind kind;
+  const void *payload = nullptr;
+  int rc = payload_kind(map, params, &kind, &payload);
+  if (rc != NBT_OK) return rc;
+  const CamConst cc = make_cam(map, cam);
+  *cc_out = cc;
+  const int64_t n_items = n_poses * cc.tiles_per_pose;
+  if (!workspace || workspace_bytes < workspace_bytes_for(n_items) || ((uintptr_t)workspace & 15u))
+    return NBT_EWORKSPACE;
+  if (kind == PAYLOAD_GAIN_F32) {
+    rc = prepare_gain(map, params, stream);
+    if (rc != NBT_OK) return rc;
+  }
+  const float *pp = (const float *)poses;
+  switch (kind) {
+    case PAYLOAD_U8:
+      return launch_tiles<PAYLOAD_U8>(map, payload, cc, pp, n_items, params->include_hit, workspace, stream);
+    case PAYLOAD_U2:
+      return launch_tiles<PAYLOAD_U2>(map, payload, cc, pp, n_items, params->include_hit, workspace, stream);
+    default:
+      return launch_tiles<PAYLOAD_GAIN_F32>(map, payload, cc, pp, n_items, params->include_hit, workspace, stream);
+  }
+}
+
+}  // namespace
+}  // namespace nbt
+
+using namespace nbt;
+
+extern "C" {
+
+int nbt_workspace_size(int64_t n_poses, const nbt_camera *cam, int64_t *bytes) {
+  if (!bytes || n_poses < 0 || !valid_camera(cam)) return NBT_EINVAL;
+  const int64_t tiles = (int64_t)((cam->width + kTileW - 1) / kTileW) * ((cam->height + kTileH - 1) / kTileH);
+  *bytes = workspace_bytes_for(n_poses * tiles);
+  return NBT_OK;
+}
+
+int nbt_views_ig(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_camera *cam,
+                 const nbt_ig_params *params, float *ig_out, uint64_t *steps_out, void *workspace,
+                 int64_t workspace_bytes, void *stream_) {
+  int rc = check_map(map);
+  if (rc != NBT_OK) return rc;
+  if (n_views < 0 || !valid_camera(cam) || !valid_params(params)) return NBT_EINVAL;
+  if (n_views == 0) return NBT_OK;
+  if (!poses || !ig_out) return NBT_EINVAL;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  CamConst cc;
+  rc = run_tiles(map, poses, n_views, cam, params, workspace, workspace_bytes, stream, &cc);
+  if (rc != NBT_OK) return rc;
+  const Partial *partials = (const Partial *)((const char *)workspace + 256);
+  const int64_t threads = n_views * 32;
+  views_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
+      partials, n_views, cc.tiles_per_pose, params->reduce == NBT_REDUCE_MEAN, (double)cc.W * cc.H, ig_out, steps_out);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+int nbt_traj_ig(nbt_map map, const nbt_pose *poses, int64_t n_poses, const int32_t *offsets, int32_t n_traj,
+                const nbt_camera *cam, const nbt_ig_params *params, float *traj_ig_out, float *pose_ig_out,
+                void *workspace, int64_t workspace_bytes, void *stream_) {
+  int rc = check_map(map);
+  if (rc != NBT_OK) return rc;
+  if (n_poses < 0 || n_traj < 0 || !valid_camera(cam) || !valid_params(params)) return NBT_EINVAL;
+  if (n_traj == 0) return n_poses == 0 ? NBT_OK : NBT_EINVAL;
+  if (!offsets || !traj_ig_out || (n_poses > 0 && !poses)) return NBT_EINVAL;
+  if (n_poses > INT32_MAX) return NBT_EINVAL;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  CamConst cc = make_cam(map, cam);
+  if (n_poses > 0) {
+    rc = run_tiles(map, poses, n_poses, cam, params, workspace, workspace_bytes, stream, &cc);
+    if (rc != NBT_OK) return rc;
+  } else if (!workspace || workspace_bytes < workspace_bytes_for(0)) {
+    return NBT_EWORKSPACE;
+  }
+  const Partial *partials = (const Partial *)((const char *)workspace + 256);
+  const int64_t threads = (int64_t)n_traj * 32;
+  traj_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
+      partials, offsets, n_traj, (int32_t)n_poses, cc.tiles_per_pose, params->reduce == NBT_REDUCE_MEAN,
+      (double)cc.W * cc.H, traj_ig_out, pose_ig_out);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+int nbt_trace_segments(nbt_map map, const float *o, const float *d, int32_t n_rays, const nbt_ig_params *params,
+                       int32_t *idx_out, int32_t cap, int32_t *n_out, void *stream_) {
+  int rc = check_map(map);
+  if (rc != NBT_OK) return rc;
+  if (n_rays < 0 || cap < 0 || (params && !valid_params(params))) return NBT_EINVAL;
+  if (n_rays == 0) return NBT_OK;
+  if (!o || !d || !n_out || (cap > 0 && !idx_out)) return NBT_EINVAL;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  PayloadKind kind = PAYLOAD_U8;
+  const void *payload = map->d_payload;
+  if (params) {
+    rc = payload_kind(map, params, &kind, &payload);
+    if (rc != NBT_OK) return rc;
+    if (kind == PAYLOAD_GAIN_F32) {
+      rc = prepare_gain(map, params, stream);
+      if (rc != NBT_OK) return rc;
+    }
+  }
+  const DevMap m = dev_map(map, payload);
+  const unsigned grid = (unsigned)((n_rays + 127) / 128);
+  const int use_occ = params != nullptr;
+  switch (kind) {
+    case PAYLOAD_U8: trace_kernel<PAYLOAD_U8><<<grid, 128, 0, stream>>>(m, o, d, n_rays, use_occ, idx_out, cap, n_out); break;
+    case PAYLOAD_U2: trace_kernel<PAYLOAD_U2><<<grid, 128, 0, stream>>>(m, o, d, n_rays, use_occ, idx_out, cap, n_out); break;
+    default: trace_kernel<PAYLOAD_GAIN_F32><<<grid, 128, 0, stream>>>(m, o, d, n_rays, use_occ, idx_out, cap, n_out); break;
+  }
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+int nbt_view_segments(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_camera *cam, float *o_out,
+                      float *d_out, void *stream_) {
+  int rc = check_map(map);
+  if (rc != NBT_OK) return rc;
+  if (n_views < 0 || !valid_camera(cam)) return NBT_EINVAL;
+  if (n_views == 0) return NBT_OK;
+  if (!poses || !o_out || !d_out) return NBT_EINVAL;
+  const CamConst cc = make_cam(map, cam);
+  const int64_t n_rays = n_views * cam->width * (int64_t)cam->height;
+  const unsigned grid = (unsigned)std::min<int64_t>((n_rays + 255) / 256, (int64_t)sm_count() * 32);
+  view_segments_kernel<<<grid, 256, 0, (cudaStream_t)stream_>>>(cc, (const float *)poses, n_rays, o_out, d_out);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+"""The C ABI library loads and exports every symbol include/nbt.h declares (no GPU)."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "nbt.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(nbt_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def libnbt():
+    import paper_2503_22588_gb300 as nbt
+    try:
+        nbt.build()
+    except (RuntimeError, FileNotFoundError) as e:  # no nvcc on this machine
+        if not os.path.exists(nbt.LIB_PATH):
+            pytest.skip(f"cannot build libnbt.so here: {e}")
+    return nbt
+
+
+def test_every_declared_symbol_is_exported_and_bound(libnbt):
+    from paper_2503_22588_gb300 import _lib
+    names = declared_functions()
+    assert len(names) >= 11
+    raw = C.CDLL(libnbt.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), n
+        assert n in _lib.SIGNATURES, n
+    assert set(_lib.SIGNATURES) == set(names)
+
+
+def test_host_only_entry_points(libnbt):
+    from paper_2503_22588_gb300 import _lib
+    L = _lib.lib()
+    v = C.c_int32()
+    assert L.nbt_get_version(C.byref(v)) == 0 and v.value == 1
+    assert L.nbt_get_version(None) == -1
+    assert L.nbt_status_string(-6).startswith(b"NBT_EWORKSPACE")
+    assert L.nbt_map_create(None, None) == -1
+    assert L.nbt_map_destroy(None) == 0
+    cam = libnbt.camera(160, 120, 1.0, 0.8, 1.0)
+    b = C.c_int64()
+    assert L.nbt_workspace_size(1024, C.byref(cam), C.byref(b)) == 0
+    assert b.value == 256 + 1024 * 5 * 15 * 16
+    assert L.nbt_workspace_size(-1, C.byref(cam), C.byref(b)) == -1
+    bad = libnbt.camera(0, 120, 1.0, 0.8, 1.0)
+    assert L.nbt_workspace_size(4, C.byref(bad), C.byref(b)) == -1
+
+
+def test_structs_match_header_sizes():
+    from paper_2503_22588_gb300 import _lib
+    assert C.sizeof(_lib.MapDesc) == 36
+    assert C.sizeof(_lib.Camera) == 28
+    assert C.sizeof(_lib.IgParams) == 20
+
+
+def test_product_package_does_not_touch_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2503_22588_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                for bad in ("import oracle", "from oracle", "liborc", "nbt_oracle"):
+                    assert bad not in text, (f, bad)

@@ -1,0 +1,285 @@
+"""Parity of the CUDA path with the CPU oracle (GPU required).
+
+Bars: ray segments and voxel sequences bit-exact with the oracle's FP32
+reference walk; voxel-step counts exact; unknown-voxel counts exact;
+floating-point IG within a relative 1e-5 of the FP64 oracle, both along the
+FP32 reference walk and along the exact FP64 walk.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2503_22588_gb300 as nbt
+from gpu_util import RTOL, gpu_camera, gpu_map, oracle_camera, oracle_map, rel_err, views_gpu
+from workload import configs, poses, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    nbt.build()
+    oracle.build()
+
+
+def _segments(rng, dims, n, max_len):
+    dims = np.asarray(dims, np.float64)
+    o = np.where(rng.random((n, 1)) < 0.5, rng.random((n, 3)) * dims, rng.uniform(-0.5, 1.5, (n, 3)) * dims)
+    v = rng.standard_normal((n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return o.astype(np.float32), (v * rng.uniform(0.1, max_len, (n, 1))).astype(np.float32)
+
+
+def _edge_segments(dims):
+    nx, ny, nz = dims
+    rows = [
+        ([0.5, 0.5, 0.5], [nx + 5.0, 0.0, 0.0]),            # axis-aligned, through the whole map
+        ([nx - 0.5, 1.25, 1.75], [-(nx + 3.0), 0.0, 0.0]),  # axis-aligned, negative
+        ([1.3, 1.7, 0.2], [0.0, 0.0, nz * 2.0]),             # along z
+        ([2.0, 2.0, 2.0], [3.0, 3.0, 3.0]),                  # starts on a corner, exact diagonal
+        ([0.0, 0.0, 0.0], [1.0, 0.0, 0.0]),                  # starts on the min corner
+        ([1.5, 1.5, 1.5], [0.0, 0.0, 0.0]),                  # zero length
+        ([-1.0, -1.0, -1.0], [-2.0, -3.0, -1.0]),            # outside, pointing away
+        ([-5.0, 1.5, 1.5], [nx + 10.0, 0.0, 0.0]),           # enters through the x = 0 face
+        ([1.5, float(ny), 1.5], [1.0, 0.0, 0.0]),            # on the y = N face (outside)
+        ([1.5, 1.0, 1.5], [2.0, 0.0, 0.3]),                  # in the y = 1 plane
+        ([float("nan"), 1.0, 1.0], [1.0, 1.0, 1.0]),         # NaN start
+        ([1.0, 1.0, 1.0], [float("inf"), 0.0, 0.0]),         # infinite displacement
+        ([nx / 2.0, ny / 2.0, nz / 2.0], [1e-30, 1e-30, 1e-30]),  # tiny displacement
+        ([0.5, 0.5, 0.5], [3e6, 2e6, 1e6]),                  # huge segment
+    ]
+    o = np.array([r[0] for r in rows], np.float32)
+    d = np.array([r[1] for r in rows], np.float32)
+    return o, d
+
+
+@pytest.mark.parametrize("grid_mode", ["corners", "centers"])
+@pytest.mark.parametrize("range_mode", ["planar", "spherical"])
+@pytest.mark.parametrize("wh", [(64, 48), (33, 9), (1, 1), (7, 1)])
+def test_view_segments_bitexact(grid_mode, range_mode, wh):
+    w = configs.exact64(seed=1, n_views=5)
+    cam = configs.Camera(wh[0], wh[1], grid_mode=grid_mode, range_mode=range_mode)
+    gm = gpu_map(w)
+    o, d = nbt.view_segments(gm, torch.from_numpy(w.poses).cuda(), gpu_camera(cam))
+    o = o.cpu().numpy()
+    d = d.cpu().numpy()
+    om = oracle_map(w)
+    n = wh[0] * wh[1]
+    for v in range(len(w.poses)):
+        ro, rd = oracle.view_rays(om, oracle_camera(cam), w.poses[v])
+        assert np.array_equal(o[v * n:(v + 1) * n].view(np.uint32), ro.view(np.uint32))
+        assert np.array_equal(d[v * n:(v + 1) * n].view(np.uint32), rd.view(np.uint32))
+
+
+@pytest.mark.parametrize("dims", [(16, 16, 16), (37, 20, 50), (256, 256, 256), (1, 1, 1), (5, 64, 3)])
+@pytest.mark.parametrize("brick", [4, 8])
+def test_trace_segments_bitexact(dims, brick):
+    rng = np.random.default_rng(dims[0] * 7 + brick)
+    o, d = _segments(rng, dims, 3000, max_len=1.5 * max(dims))
+    eo, ed = _edge_segments(dims)
+    o = np.concatenate([o, eo])
+    d = np.concatenate([d, ed])
+    grid = np.zeros(dims[::-1], np.uint8)
+    gm = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01, (0.0, 0.0, 0.0), "u8", brick)
+    idx, cnt = nbt.trace_segments(gm, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+    idx = idx.cpu().numpy()
+    cnt = cnt.cpu().numpy()
+    for k in range(len(o)):
+        ref = oracle.trace(dims, o[k], d[k], "f32")
+        assert cnt[k] == len(ref), k
+        assert np.array_equal(idx[k, :cnt[k]], ref), k
+
+
+@pytest.mark.parametrize("encoding", ["u8", "u2"])
+@pytest.mark.parametrize("brick", [4, 8])
+def test_trace_views_occluded_bitexact(encoding, brick):
+    w = configs.exact64(seed=4, n_views=6)
+    gm = gpu_map(w, brick, encoding)
+    cam = gpu_camera(w.camera)
+    o, d = nbt.view_segments(gm, torch.from_numpy(w.poses).cuda(), cam)
+    prm = nbt.ig_params("count")
+    idx, cnt = nbt.trace_segments(gm, o, d, prm)
+    idx = idx.cpu().numpy()
+    cnt = cnt.cpu().numpy()
+    o = o.cpu().numpy()
+    d = d.cpu().numpy()
+    om = oracle_map(w)
+    op = oracle.params("count")
+    for k in range(len(o)):
+        ref = oracle.trace_occluded(om, o[k], d[k], op, "f32")
+        assert cnt[k] == len(ref) and np.array_equal(idx[k, :cnt[k]], ref), k
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("encoding,brick", [("u8", 8), ("u8", 4), ("u2", 8), ("u2", 4)])
+def test_views_ig_count_exact(seed, encoding, brick):
+    """64^3 states, 64 views, 64 x 48 rays: unknown counts and steps equal the oracle's exactly."""
+    w = configs.exact64(seed=seed)
+    gm = gpu_map(w, brick, encoding)
+    ig, st = views_gpu(gm, w.poses, gpu_camera(w.camera), nbt.ig_params("count"))
+    rig, rst = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(w.camera), oracle.params("count"), "f32", 8)
+    assert np.array_equal(st, rst)
+    assert np.array_equal(ig, rig)
+    xig, _ = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(w.camera), oracle.params("count"), "f64", 8)
+    assert np.all(rel_err(ig, xig) <= RTOL)
+
+
+@pytest.mark.parametrize("metric", ["entropy", "eq2", "count"])
+@pytest.mark.parametrize("brick", [8, 4])
+def test_views_ig_probability_map(metric, brick):
+    """Reduced tabletop (96^3 FP32), 24 views of 80 x 60 rays."""
+    w = configs.prob256(seed=3, n_views=24, n=96, n_prims=40)
+    w.camera = configs.Camera(80, 60)
+    gm = gpu_map(w, brick)
+    ig, st = views_gpu(gm, w.poses, gpu_camera(w.camera), nbt.ig_params(metric))
+    om = oracle_map(w)
+    rig, rst = oracle.views_ig(om, w.poses, oracle_camera(w.camera), oracle.params(metric), "f32", 8)
+    assert np.array_equal(st, rst)
+    assert np.all(rel_err(ig, rig) <= RTOL), rel_err(ig, rig).max()
+    xig, xst = oracle.views_ig(om, w.poses, oracle_camera(w.camera), oracle.params(metric), "f64", 8)
+    assert np.all(rel_err(ig, xig) <= RTOL), rel_err(ig, xig).max()
+    assert np.all(np.abs(st - xst) <= 0.001 * xst + 2)
+
+
+def test_views_ig_mean_and_include_hit():
+    w = configs.prob256(seed=5, n_views=8, n=64, n_prims=20)
+    w.camera = configs.Camera(40, 30)
+    gm = gpu_map(w)
+    om = oracle_map(w)
+    for prm_kw in ({"reduce": "mean"}, {"include_hit": False}, {"include_hit": False, "reduce": "mean"},
+                   {"occ_threshold": 0.6, "free_threshold": 0.35}):
+        ig, st = views_gpu(gm, w.poses, gpu_camera(w.camera), nbt.ig_params("eq2", **prm_kw))
+        rig, rst = oracle.views_ig(om, w.poses, oracle_camera(w.camera), oracle.params("eq2", **prm_kw), "f32", 4)
+        assert np.array_equal(st, rst), prm_kw
+        assert np.all(rel_err(ig, rig) <= RTOL), prm_kw
+
+
+@pytest.mark.parametrize("wh", [(33, 9), (1, 1), (31, 7), (200, 3)])
+def test_views_ig_ragged_tiles(wh):
+    w = configs.exact64(seed=6, n_views=9)
+    cam = configs.Camera(*wh)
+    gm = gpu_map(w)
+    ig, st = views_gpu(gm, w.poses, gpu_camera(cam), nbt.ig_params("count"))
+    rig, rst = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(cam), oracle.params("count"), "f32", 4)
+    assert np.array_equal(st, rst) and np.array_equal(ig, rig)
+
+
+def test_views_ig_degenerate_maps_and_poses():
+    # 1 x 1 x 1 map; non-cubic map; cameras outside looking away; empty view list
+    for dims in ((1, 1, 1), (37, 20, 50)):
+        grid = scenes.random_states(dims[::-1], 0.4, 0.1, seed=3)
+        w = configs.Workload("t", 0, "u8", "count", configs.Camera(16, 12), grid, None, None)
+        poi = np.array(dims, np.float64) * 0.005
+        pos = poi + np.array([[0.3, 0.0, 0.0], [0.0, -0.25, 0.1], [0.0, 0.0, 0.4], [0.01, 0.02, 0.03]])
+        p = poses.look_at_poses(pos, poi)
+        away = poses.look_at_poses(poi + np.array([[0.5, 0.5, 0.5]]), poi + np.array([1.0, 1.0, 1.0]))
+        w.poses = np.concatenate([p, away])
+        gm = gpu_map(w)
+        ig, st = views_gpu(gm, w.poses, gpu_camera(w.camera), nbt.ig_params("count"))
+        rig, rst = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(w.camera), oracle.params("count"))
+        assert np.array_equal(st, rst) and np.array_equal(ig, rig)
+        assert ig[-1] == 0 and st[-1] == 0
+    out, steps = nbt.views_ig(gm, torch.zeros((0, 7), dtype=torch.float32, device="cuda"), gpu_camera(w.camera),
+                              nbt.ig_params("count"))
+    assert out.numel() == 0
+
+
+def test_closed_forms_on_gpu():
+    """All-free map: IG 0; all-occupied: one step per ray that meets the map."""
+    cam = configs.Camera(24, 18)
+    poi = np.array([0.16, 0.16, 0.16])
+    p = poses.sphere_views(poi, 10, 0.1)  # inside the 32^3 map
+    for state, expect_steps in ((1, None), (2, 24 * 18)):
+        grid = scenes.uniform_states((32, 32, 32), state)
+        gm = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01)
+        ig, st = views_gpu(gm, p, gpu_camera(cam), nbt.ig_params("count"))
+        assert np.all(ig == 0)
+        if expect_steps:
+            assert np.all(st == expect_steps)
+
+
+def test_traj_ig_matches_oracle():
+    w = configs.traj256(seed=2, n_traj=24, n=96, len_range=(1, 9))
+    w.camera = configs.Camera(48, 36)
+    gm = gpu_map(w)
+    off = torch.from_numpy(w.offsets).cuda()
+    pz = torch.from_numpy(w.poses).cuda()
+    pose_out = torch.empty(len(w.poses), dtype=torch.float32, device="cuda")
+    tig = nbt.traj_ig(gm, pz, off, gpu_camera(w.camera), nbt.ig_params("count"), pose_out=pose_out)
+    torch.cuda.synchronize()
+    rig, _ = oracle.traj_ig(oracle_map(w), w.poses, w.offsets, oracle_camera(w.camera), oracle.params("count"),
+                            "f32", 8)
+    assert np.array_equal(tig.cpu().numpy().astype(np.float64), rig)
+    vig, _ = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(w.camera), oracle.params("count"), "f32", 8)
+    assert np.array_equal(pose_out.cpu().numpy().astype(np.float64), vig)
+
+
+def test_traj_ig_empty_and_uneven():
+    w = configs.exact64(seed=8, n_views=10)
+    gm = gpu_map(w)
+    offsets = np.array([0, 0, 4, 4, 5, 10, 10], np.int32)
+    tig = nbt.traj_ig(gm, torch.from_numpy(w.poses).cuda(), torch.from_numpy(offsets).cuda(),
+                      gpu_camera(w.camera), nbt.ig_params("count", reduce="mean"))
+    rig, _ = oracle.traj_ig(oracle_map(w), w.poses, offsets, oracle_camera(w.camera),
+                            oracle.params("count", reduce="mean"))
+    assert np.all(rel_err(tig.cpu().numpy(), rig) <= 1e-6)
+    assert tig[0].item() == 0 and tig[2].item() == 0 and tig[5].item() == 0
+
+
+def test_deterministic_results():
+    w = configs.prob256(seed=1, n_views=32, n=64, n_prims=20)
+    w.camera = configs.Camera(64, 48)
+    gm = gpu_map(w)
+    a = views_gpu(gm, w.poses, gpu_camera(w.camera), nbt.ig_params("entropy"))
+    b = views_gpu(gm, w.poses, gpu_camera(w.camera), nbt.ig_params("entropy"))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_invalid_arguments_are_rejected():
+    w = configs.exact64(seed=0, n_views=2)
+    gm = gpu_map(w)
+    p = torch.from_numpy(w.poses).cuda()
+    with pytest.raises(nbt.NbtError) as e:
+        nbt.views_ig(gm, p, gpu_camera(w.camera), nbt.ig_params("entropy"))   # entropy on a state map
+    assert e.value.status == -5
+    with pytest.raises(nbt.NbtError) as e:
+        nbt.views_ig(gm, p, nbt.camera(0, 4, 1.0, 1.0, 1.0), nbt.ig_params("count"))
+    assert e.value.status == -1
+    with pytest.raises(nbt.NbtError) as e:
+        nbt.views_ig(gm, p, nbt.camera(8, 4, 4.0, 1.0, 1.0), nbt.ig_params("count"))  # fov >= pi
+    assert e.value.status == -1
+    small = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(nbt.NbtError) as e:
+        nbt.views_ig(gm, p, gpu_camera(w.camera), nbt.ig_params("count"), ws=small)
+    assert e.value.status == -6
+    with pytest.raises(nbt.NbtError):
+        nbt.Map(0, 4, 4, 0.01)
+    with pytest.raises(nbt.NbtError):
+        nbt.Map(4, 4, 4, 0.01, brick=5)
+    with pytest.raises(nbt.NbtError):
+        nbt.Map(4, 4, 4, -1.0)
+    with pytest.raises(TypeError):
+        gm.upload(np.zeros((64, 64, 64), np.float32))
+
+
+def test_host_upload_matches_device_upload():
+    w = configs.prob256(seed=2, n_views=6, n=64, n_prims=10)
+    w.camera = configs.Camera(32, 24)
+    a = nbt.Map.from_grid(w.grid, w.voxel_size)                       # host numpy source
+    b = nbt.Map.from_grid(torch.from_numpy(w.grid).cuda(), w.voxel_size)  # device source
+    ra = views_gpu(a, w.poses, gpu_camera(w.camera), nbt.ig_params("entropy"))
+    rb = views_gpu(b, w.poses, gpu_camera(w.camera), nbt.ig_params("entropy"))
+    assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
+    # re-upload invalidates the derived gains
+    g2 = w.grid.copy()
+    g2[:, :, :32] = 0.5
+    a.upload(g2)
+    rc = views_gpu(a, w.poses, gpu_camera(w.camera), nbt.ig_params("entropy"))
+    rig, _ = oracle.views_ig(oracle.Map(g2), w.poses, oracle_camera(w.camera), oracle.params("entropy"))
+    assert np.all(rel_err(rc[0], rig) <= RTOL)
