@@ -161,7 +161,8 @@ def run_reference(args) -> None:
     t0 = time.perf_counter()
     oracle.views_ig(m, w.poses[:threads], cam, prm, "f32", threads)
     per_view = (time.perf_counter() - t0) / threads
-    n = int(max(threads, min(w.n_poses, 8.0 / max(per_view, 1e-6))))
+    per_step_s = min(8.0, 120.0 / max(1, args.steps + args.warmup))
+    n = int(max(threads, min(w.n_poses, per_step_s / max(per_view, 1e-6))))
     for _ in range(args.warmup):
         oracle.views_ig(m, w.poses[:n], cam, prm, "f32", threads)
     times, steps = [], 0
@@ -186,8 +187,8 @@ def run_reference(args) -> None:
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default="prob256", choices=["prob256", "exact64", "room512"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -253,6 +254,7 @@ def main() -> None:
     clk = clocks.stop()
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     ig_ms = [b.elapsed_time(c) for a, b, c in ev]
+    upload_ms = float(np.mean([a.elapsed_time(b) for a, b, c in ev]))
     total_ms = float(sum(step_ms))
     ig_mean_ms = float(np.mean(ig_ms))
     if dist is not None:
@@ -316,7 +318,7 @@ def main() -> None:
         "voxel_steps_per_s": world * n_steps_voxel * args.steps / (total_ms * 1e-3),
         "voxel_steps_per_step": n_steps_voxel,
         "views_ig_ms": ig_mean_ms,
-        "upload_ms": float(np.mean([a.elapsed_time(b) for a, b, c in ev])),
+        "upload_ms": upload_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "ig_tiles_kernel (+views_reduce)",
                      "algorithmic": f"{bps} B per voxel step x {n_steps_voxel} steps",
