@@ -59,6 +59,7 @@ extern "C" {
 #define NBT_ETIMEOUT (-4)        /* a bounded device-side wait gave up */
 #define NBT_EUNSUPPORTED (-5)    /* valid but unsupported combination (e.g. Eq. 2 on a state map) */
 #define NBT_EWORKSPACE (-6)      /* workspace missing or smaller than nbt_workspace_size() */
+#define NBT_ESCRATCH (-7)        /* request larger than the fixed scratch of nbt_views_ig_noalloc */
 
 /* Map encodings (voxel payload stored on the device). */
 #define NBT_U8_STATE 0           /* uint8 state per voxel: 0 unknown, 1 free, >= 2 occupied */
@@ -215,6 +216,41 @@ int nbt_trace_segments(nbt_map map, const float *o, const float *d, int32_t n_ra
  *   o_out, d_out: device float[n_views * W * H][3]. */
 int nbt_view_segments(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_camera *cam, float *o_out,
                       float *d_out, void *stream);
+
+/* Size of the fixed device scratch array behind nbt_views_ig_noalloc. */
+#define NBT_NOALLOC_SCRATCH_BYTES (4 << 20)
+
+/* nbt_views_ig without any device allocation, for callers that cannot
+ * allocate.  The paper has no counterpart; this is a deployment variant.
+ *
+ * Who needs it: code that must never call cudaMalloc -- a real-time
+ * planning loop (the planner of the paper runs at 10 Hz) where a
+ * cudaMalloc can synchronise the device and stall for milliseconds, a
+ * host process whose device memory is already reserved by another
+ * allocator or capped by a budget, or a plugin that is not allowed to
+ * allocate inside its callbacks.  Such a caller cannot create the
+ * workspace nbt_views_ig takes, so this entry point uses a file-scope
+ * __device__ array of NBT_NOALLOC_SCRATCH_BYTES instead.  That array exists
+ * on every device that loads the library and stays there until the
+ * process exits.
+ *
+ * Arguments and results are those of nbt_views_ig, without the workspace
+ * (the map, the poses and the outputs are still the caller's).  The request
+ * must fit the array: n_views * ceil(W / 32) * ceil(H / 8) tiles, 16 bytes
+ * each, plus a 256-byte header, at most NBT_NOALLOC_SCRATCH_BYTES (262,128
+ * tiles, e.g. 3,495 views of 160 x 120 rays); larger requests return
+ * NBT_ESCRATCH before anything is enqueued -- split them into several
+ * calls.
+ *
+ * The first call on a device looks up the array's device address there
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array
+ * and clears the part that must start at zero itself; calls whose work
+ * overlaps on the GPU (different streams, no ordering between them) race
+ * on the array and give wrong results, so order them on one stream or with
+ * events.  Errors as for nbt_views_ig, plus NBT_ESCRATCH. */
+int nbt_views_ig_noalloc(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_camera *cam,
+                         const nbt_ig_params *params, float *ig_out, uint64_t *steps_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -7,5 +7,5 @@ Distribution) as hand-written sm_103a CUDA kernels behind a C ABI
 
 from ._lib import LibraryMissing, NbtError, lib  # noqa: F401
 from .api import (Map, camera, ig_params, trace_segments, traj_ig, view_segments, views_ig,  # noqa: F401
-                  workspace, workspace_size)
+                  views_ig_noalloc, workspace, workspace_size)
 from .build import LIB_PATH, build  # noqa: F401

@@ -9,7 +9,7 @@ from .build import LIB_PATH
 
 NBT_OK = 0
 STATUS = {0: "NBT_OK", -1: "NBT_EINVAL", -2: "NBT_ENOMEM", -3: "NBT_ECUDA", -4: "NBT_ETIMEOUT",
-          -5: "NBT_EUNSUPPORTED", -6: "NBT_EWORKSPACE"}
+          -5: "NBT_EUNSUPPORTED", -6: "NBT_EWORKSPACE", -7: "NBT_ESCRATCH"}
 ENCODINGS = {"u8": 0, "f32": 1, "u2": 2}
 METRICS = {"count": 0, "eq2": 1, "entropy": 2}
 REDUCE = {"sum": 0, "mean": 1}
@@ -57,6 +57,7 @@ SIGNATURES = {
     "nbt_traj_ig": (C.c_int, [_vp, _vp, _i64, _vp, _i32, P(Camera), P(IgParams), _vp, _vp, _vp, _i64, _vp]),
     "nbt_trace_segments": (C.c_int, [_vp, _vp, _vp, _i32, P(IgParams), _vp, _i32, _vp, _vp]),
     "nbt_view_segments": (C.c_int, [_vp, _vp, _i64, P(Camera), _vp, _vp, _vp]),
+    "nbt_views_ig_noalloc": (C.c_int, [_vp, _vp, _i64, P(Camera), P(IgParams), _vp, _vp, _vp]),
 }
 
 _lib = None

@@ -181,3 +181,20 @@ def view_segments(m: Map, poses: torch.Tensor, cam: Camera, stream=None):
     check(lib().nbt_view_segments(m.handle, _dev(poses, torch.float32, "poses", (7,)), poses.shape[0],
                                   C.byref(cam), o.data_ptr(), d.data_ptr(), _stream(stream)), "nbt_view_segments")
     return o, d
+
+
+def views_ig_noalloc(m: Map, poses: torch.Tensor, cam: Camera, params: IgParams, out: torch.Tensor,
+                     steps: torch.Tensor | None = None, stream=None):
+    """nbt_views_ig_noalloc: nbt_views_ig with its scratch in the library's fixed device array.
+
+    For callers that must not allocate device memory (a real-time planning
+    loop, a process whose device memory belongs to another allocator): the
+    outputs are preallocated by the caller and the call allocates nothing.
+    Calls that overlap on the GPU race on the shared array.
+    """
+    n = poses.shape[0]
+    sp = _dev(steps, torch.int64, "steps") if steps is not None else None
+    check(lib().nbt_views_ig_noalloc(m.handle, _dev(poses, torch.float32, "poses", (7,)), n, C.byref(cam),
+                                     C.byref(params), _dev(out, torch.float32, "out"), sp, _stream(stream)),
+          "nbt_views_ig_noalloc")
+    return out, steps

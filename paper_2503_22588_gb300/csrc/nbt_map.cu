@@ -217,6 +217,7 @@ const char *nbt_status_string(int status) {
     case NBT_ETIMEOUT: return "NBT_ETIMEOUT: bounded device wait gave up";
     case NBT_EUNSUPPORTED: return "NBT_EUNSUPPORTED: unsupported combination";
     case NBT_EWORKSPACE: return "NBT_EWORKSPACE: workspace missing or too small";
+    case NBT_ESCRATCH: return "NBT_ESCRATCH: request exceeds the fixed scratch of nbt_views_ig_noalloc";
     default: return "unknown status";
   }
 }

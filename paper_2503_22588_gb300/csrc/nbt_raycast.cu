@@ -478,3 +478,68 @@ int nbt_view_segments(nbt_map map, const nbt_pose *poses, int64_t n_views, const
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// nbt_views_ig_noalloc: the per-perspective IG path with its scratch (work
+// queue counter + per-tile partials) in a fixed device array instead of a
+// caller workspace, for callers that may not allocate device memory (see
+// include/nbt.h).  The array is file-scope, so every device that loads the
+// library holds it until the process exits.  Host code only ever uses the
+// device address looked up below; the array's name is a host-side stand-in.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char nbt_noalloc_scratch[NBT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on `device` (the current device),
+// looked up once per device.
+int noalloc_scratch(int device, void **ptr) {
+  if (device < 0 || device >= kNoallocMaxDevices) return NBT_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, nbt_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      (void)cudaGetLastError();
+      return NBT_ECUDA;
+    }
+    g_noalloc_ptr[device] = p;
+  }
+  *ptr = g_noalloc_ptr[device];
+  return NBT_OK;
+}
+
+}  // namespace
+
+extern "C" int nbt_views_ig_noalloc(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_camera *cam,
+                                    const nbt_ig_params *params, float *ig_out, uint64_t *steps_out,
+                                    void *stream_) {
+  int rc = check_map(map);
+  if (rc != NBT_OK) return rc;
+  if (n_views < 0 || !valid_camera(cam) || !valid_params(params)) return NBT_EINVAL;
+  if (n_views == 0) return NBT_OK;
+  if (!poses || !ig_out) return NBT_EINVAL;
+  int64_t need = 0;
+  rc = nbt_workspace_size(n_views, cam, &need);
+  if (rc != NBT_OK) return rc;
+  if (need > (int64_t)NBT_NOALLOC_SCRATCH_BYTES) return NBT_ESCRATCH;
+  void *scratch = nullptr;
+  rc = noalloc_scratch(map->device, &scratch);
+  if (rc != NBT_OK) return rc;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  // run_tiles zeroes the queue counter on the stream before the tile
+  // kernel; the tile kernel writes every partial the reduce kernel reads.
+  CamConst cc;
+  rc = run_tiles(map, poses, n_views, cam, params, scratch, (int64_t)NBT_NOALLOC_SCRATCH_BYTES, stream, &cc);
+  if (rc != NBT_OK) return rc;
+  const Partial *partials = (const Partial *)((const char *)scratch + 256);
+  const int64_t threads = n_views * 32;
+  views_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
+      partials, n_views, cc.tiles_per_pose, params->reduce == NBT_REDUCE_MEAN, (double)cc.W * cc.H, ig_out, steps_out);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
