@@ -83,14 +83,15 @@ extern "C" {
 typedef struct nbt_map_s *nbt_map; /* opaque; owns the device copy of the map */
 
 /* Map description.  Each of nx, ny, nz in [1, 2048]; nx*ny*nz < 2^31.
- * brick: 0 (default 8), 4 or 8 -- the edge of the cubic voxel bricks the
- * device copy is stored in (bricks in Morton order; see nbt_map_create). */
+ * brick: the device layout -- 1 (linear x-fastest, the default; 0 selects
+ * it too) or 4 / 8 (cubic bricks of that edge in Morton order; see
+ * nbt_map_create). */
 typedef struct {
   int32_t nx, ny, nz;
   float voxel_size;              /* s_Vox, metres, > 0 */
   float origin[3];               /* world position of the map's min corner */
   int32_t encoding;              /* NBT_U8_STATE | NBT_F32_PROB | NBT_U2_STATE */
-  int32_t brick;                 /* 0, 4 or 8 */
+  int32_t brick;                 /* 0 or 1 (linear), 4 or 8 (Morton bricks) */
 } nbt_map_desc;
 
 /* Camera pose: 28 bytes, arrays of poses are tightly packed. */
@@ -126,12 +127,14 @@ const char *nbt_status_string(int status);
 int nbt_get_version(int32_t *version);
 
 /* Create a map on the current device and allocate its device storage
- * (zero-filled: all voxels unknown / P = 0).  The grid is stored in B^3
- * bricks (B = desc->brick), bricks in Morton (Z) order of their brick
- * coordinates; per-axis offset tables make any voxel's address the sum of
- * three table entries.  Ownership of the handle passes to the caller, who
- * releases it with nbt_map_destroy.  Errors: NBT_EINVAL (desc out of range),
- * NBT_ENOMEM, NBT_ECUDA. */
+ * (zero-filled: all voxels unknown / P = 0).  Layout: linear x-fastest
+ * (brick 1; a voxel step adds a fixed stride -- the fastest layout on GB300
+ * because the whole map stays L2-resident), or B^3 bricks (B = 4 or 8) in
+ * Morton (Z) order of their brick coordinates, addressed through per-axis
+ * offset tables (a voxel's offset is the sum of three table entries).
+ * Ownership of the handle passes to the caller, who releases it with
+ * nbt_map_destroy.  Errors: NBT_EINVAL (desc out of range), NBT_ENOMEM,
+ * NBT_ECUDA. */
 int nbt_map_create(const nbt_map_desc *desc, nbt_map *out);
 
 /* Release a map and its device memory (synchronises the device first so no
@@ -216,6 +219,21 @@ int nbt_trace_segments(nbt_map map, const float *o, const float *d, int32_t n_ra
  *   o_out, d_out: device float[n_views * W * H][3]. */
 int nbt_view_segments(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_camera *cam, float *o_out,
                       float *d_out, void *stream);
+
+/* Launch tuning of the IG kernels for one map (chosen by the autotuner in
+ * the Python package).  packet_w: width of a warp's ray packet in pixels,
+ * 4, 8, 16 or 32 (height 32 / packet_w; 0 = default 8).  brick: read-only
+ * in nbt_map_get_tuning (the brick edge is fixed at nbt_map_create).  Only
+ * speed changes: every setting visits the same voxels and returns the same
+ * per-ray sums (per-perspective sums may differ in FP32 rounding order). */
+typedef struct {
+  int32_t packet_w;
+  int32_t brick;
+} nbt_tuning;
+
+/* Set / read a map's kernel tuning.  Errors: NBT_EINVAL. */
+int nbt_map_set_tuning(nbt_map map, const nbt_tuning *tuning);
+int nbt_map_get_tuning(nbt_map map, nbt_tuning *tuning);
 
 /* Size of the fixed device scratch array behind nbt_views_ig_noalloc. */
 #define NBT_NOALLOC_SCRATCH_BYTES (4 << 20)

@@ -37,6 +37,10 @@ class Camera(C.Structure):
                 ("max_range", C.c_float), ("grid_mode", C.c_int32), ("range_mode", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("packet_w", C.c_int32), ("brick", C.c_int32)]
+
+
 class IgParams(C.Structure):
     _fields_ = [("metric", C.c_int32), ("occ_threshold", C.c_float), ("free_threshold", C.c_float),
                 ("include_hit", C.c_int32), ("reduce", C.c_int32)]
@@ -58,6 +62,8 @@ SIGNATURES = {
     "nbt_trace_segments": (C.c_int, [_vp, _vp, _vp, _i32, P(IgParams), _vp, _i32, _vp, _vp]),
     "nbt_view_segments": (C.c_int, [_vp, _vp, _i64, P(Camera), _vp, _vp, _vp]),
     "nbt_views_ig_noalloc": (C.c_int, [_vp, _vp, _i64, P(Camera), P(IgParams), _vp, _vp, _vp]),
+    "nbt_map_set_tuning": (C.c_int, [_vp, P(Tuning)]),
+    "nbt_map_get_tuning": (C.c_int, [_vp, P(Tuning)]),
 }
 
 _lib = None

@@ -12,7 +12,7 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import ENCODINGS, GRID, METRICS, RANGE, REDUCE, Camera, IgParams, MapDesc, check, lib
+from ._lib import ENCODINGS, GRID, METRICS, RANGE, REDUCE, Camera, IgParams, MapDesc, Tuning, check, lib
 
 
 def _stream(stream) -> int:
@@ -100,6 +100,15 @@ class Map:
         nbytes = C.c_int64()
         check(lib().nbt_map_info(self.handle, C.byref(desc), C.byref(nbytes)), "nbt_map_info")
         return desc, nbytes.value
+
+    def set_tuning(self, packet_w: int = 8) -> None:
+        """nbt_map_set_tuning: warp ray-packet width (4, 8, 16 or 32 pixels)."""
+        check(lib().nbt_map_set_tuning(self.handle, C.byref(Tuning(int(packet_w), 0))), "nbt_map_set_tuning")
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        check(lib().nbt_map_get_tuning(self.handle, C.byref(t)), "nbt_map_get_tuning")
+        return {"packet_w": t.packet_w, "brick": t.brick}
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:

@@ -2,17 +2,19 @@
 //
 // Layout of a map on the device
 // -----------------------------
-// The grid is stored in cubic bricks of B^3 voxels (B = 4 or 8), the voxels
-// of a brick x-fastest, the bricks in Morton (Z) order of their brick
-// coordinates (bit-interleaved x, y, z, with axes that run out of bits
-// skipped).  Because the Morton bits of different axes and the in-brick bits
-// of different axes never overlap, the element offset of voxel (x, y, z) is
+// Two layouts.  Linear (brick = 1, the default): x-fastest, element index
+// (z * ny + y) * nx + x; a DDA step adds a fixed per-axis stride.  Bricked
+// (brick = 4 or 8): cubic bricks of B^3 voxels, x-fastest inside a brick,
+// bricks in Morton (Z) order of their brick coordinates (bit-interleaved x, y,
+// z, axes that run out of bits skipped).  Because the Morton bits of
+// different axes and the in-brick bits of different axes never overlap, the
+// element offset of voxel (x, y, z) is
 //     tab[x] + tab[nx + y] + tab[nx + ny + z]
-// with one per-axis table (int32, nx + ny + nz entries).  The kernels keep
-// the three partial offsets in registers and refresh only the one of the
-// axis a DDA step moves along, so any brick layout costs one table read per
-// step.  Element = one byte (uint8 states), one float (gains), or 2 bits
-// (packed states: byte offset >> 2, shift 2 * (offset & 3)).
+// with one per-axis table (int32, nx + ny + nz entries; built for both
+// layouts).  The bricked kernel keeps the three partial offsets in registers
+// and re-reads them from a shared-memory copy of the tables every step.
+// Element = one byte (uint8 states), one float (gains), or 2 bits (packed
+// states: byte offset >> 2, shift 2 * (offset & 3)).
 
 #pragma once
 
@@ -29,9 +31,9 @@ namespace nbt {
 enum PayloadKind : int { PAYLOAD_U8 = 0, PAYLOAD_GAIN_F32 = 1, PAYLOAD_U2 = 2 };
 
 constexpr int kMaxDim = 2048;
-constexpr int kTileW = 32;          // ray tile: 32 x 8 pixels, 8 warps of 8 x 4 pixels
+constexpr int kTileW = 32;          // ray tile: 32 x 8 pixels = 8 warp packets of 32 rays
 constexpr int kTileH = 8;
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;          // 8 warps, each working on its own tiles
 constexpr int kPartialBytes = 16;   // one per (pose, tile) item
 
 struct Partial {                    // per-tile partial sums (16 bytes)
@@ -47,6 +49,7 @@ struct nbt_map_s {
   nbt_map_desc desc;
   int device = 0;
   int brick = 8;
+  int packet_w = 8;                  // warp ray packet width (nbt_map_set_tuning)
   int nbx = 0, nby = 0, nbz = 0;     // bricks per axis
   int64_t elems = 0;                 // padded element count of the bricked payload
   int64_t payload_bytes = 0;
@@ -79,6 +82,7 @@ struct CamConst {
   int spherical;
   int W, H;
   int tiles_x, tiles_per_pose;
+  int packet_w;                      // warp ray packet: packet_w x (32 / packet_w) pixels
   float inv_s;
   float ox, oy, oz;                  // map origin, world metres
 };
@@ -129,13 +133,29 @@ __device__ __forceinline__ void ray_segment(const CamConst &cc, const float *pos
 
 // ---------------------------------------------------------------------------
 // The FP32 voxel walk (reference operation order documented in nbt.h).
+//
+// State per axis a: the parameter t_a of the next plane crossing, the
+// coordinate b_a of that plane as an integer-valued float (b_a = i_a + [s_a >
+// 0], exact below 2^24), the step s_a, o_a, 1/d_a, and the byte offset of
+// voxel index i_a in the axis' offset table.  A step advances b_a by s_a
+// (exact) and recomputes t_a = (b_a - o_a) * (1/d_a): the same two rounded
+// operations as ((float)(i_a + [s_a > 0]) - o_a) * (1/d_a), so the sequence
+// is bit-identical to the reference walk.  A step is branch-free (see
+// walk_advance), so the lanes of a warp never diverge inside it.
+//
+// No index range check is needed per step: the plane that would take axis
+// a out of the map has b_a = N_a (or 0), whose t is computed by exactly the
+// expression of the clip value on that axis, which is >= t_max; the t_max
+// test therefore always ends the walk first.
 // ---------------------------------------------------------------------------
 struct Walk {
-  int ix, iy, iz;
-  int sx, sy, sz;
-  float tx, ty, tz;
-  float invx, invy, invz;
-  float ox, oy, oz;
+  float tx, ty, tz;        // next crossing parameter (+inf: no crossing on that axis)
+  float bx, by, bz;        // next crossing plane, integer-valued
+  float sx, sy, sz;        // step: +1, -1 or 0
+  float ox, oy, oz;        // segment start
+  float vx, vy, vz;        // 1 / d
+  int px, py, pz;          // byte offset of the current voxel's entry in each axis table
+  int qx, qy, qz;          // byte step of those offsets: 4 * s
   float tmax;
 };
 
@@ -143,8 +163,15 @@ __device__ __forceinline__ bool finite3(const float v[3]) {
   return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
 }
 
-// Clip the segment to the map box and find the first voxel.  Returns false
-// if the segment visits no voxel.
+__device__ __forceinline__ bool step_of(float s) { return s != 0.0f; }
+
+__device__ __forceinline__ int tab_at(const int32_t *tab, int byte_off) {
+  return *(const int32_t *)((const char *)tab + byte_off);
+}
+
+// Clip the segment to the map box and find the first voxel.  Table offsets
+// are relative to each axis' table (x at 0, y at 4 nx, z at 4 (nx + ny)).
+// Returns false if the segment visits no voxel.
 __device__ __forceinline__ bool walk_init(Walk &w, const float o[3], const float d[3], int nx, int ny, int nz) {
   if (!finite3(o) || !finite3(d)) return false;
   const int dims[3] = {nx, ny, nz};
@@ -167,52 +194,121 @@ __device__ __forceinline__ bool walk_init(Walk &w, const float o[3], const float
     }
   }
   if (!ok || !(tmin < tmax)) return false;
-  int idx[3], step[3];
-  float tn[3];
+  float b[3], t[3], s[3];
+  int p[3], q[3];
+  const int base[3] = {0, nx, nx + ny};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    float p = fadd(o[a], fmul(tmin, d[a]));
+    float pa = fadd(o[a], fmul(tmin, d[a]));
     const float hi = (float)(dims[a] - 1);
-    p = p < 0.0f ? 0.0f : p;
-    p = p > hi ? hi : p;
-    idx[a] = (int)floorf(p);
-    step[a] = d[a] > 0.0f ? 1 : (d[a] < 0.0f ? -1 : 0);
-    tn[a] = step[a] != 0 ? fmul(fsub((float)(idx[a] + (step[a] > 0)), o[a]), inv[a]) : __int_as_float(0x7f800000);
+    pa = pa < 0.0f ? 0.0f : pa;
+    pa = pa > hi ? hi : pa;
+    const int idx = (int)floorf(pa);
+    const int step = d[a] > 0.0f ? 1 : (d[a] < 0.0f ? -1 : 0);
+    b[a] = (float)(idx + (step > 0));
+    t[a] = step != 0 ? fmul(fsub(b[a], o[a]), inv[a]) : __int_as_float(0x7f800000);
+    s[a] = (float)step;
+    p[a] = 4 * (base[a] + idx);
+    q[a] = 4 * step;
   }
-  w.ix = idx[0]; w.iy = idx[1]; w.iz = idx[2];
-  w.sx = step[0]; w.sy = step[1]; w.sz = step[2];
-  w.tx = tn[0]; w.ty = tn[1]; w.tz = tn[2];
-  w.invx = inv[0]; w.invy = inv[1]; w.invz = inv[2];
-  w.ox = o[0]; w.oy = o[1]; w.oz = o[2];
+  w.tx = t[0]; w.ty = t[1]; w.tz = t[2];
+  w.bx = b[0]; w.by = b[1]; w.bz = b[2];
+  w.sx = s[0]; w.sy = s[1]; w.sz = s[2];
+  // An axis without a step (d_a = 0) must keep t_a = +inf when walk_advance
+  // recomputes it: o_a = -inf and 1/d_a = 1 give (b_a - o_a) * 1 = +inf.
+  const float ninf = -__int_as_float(0x7f800000);
+  w.ox = step_of(s[0]) ? o[0] : ninf; w.oy = step_of(s[1]) ? o[1] : ninf; w.oz = step_of(s[2]) ? o[2] : ninf;
+  w.vx = step_of(s[0]) ? inv[0] : 1.0f; w.vy = step_of(s[1]) ? inv[1] : 1.0f; w.vz = step_of(s[2]) ? inv[2] : 1.0f;
+  w.px = p[0]; w.py = p[1]; w.pz = p[2];
+  w.qx = q[0]; w.qy = q[1]; w.qz = q[2];
   w.tmax = tmax;
   return true;
 }
 
-// One step of the walk; refreshes the partial offset of the moved axis from
-// the offset table.  Returns false when the walk has ended (the current
-// voxel was the last one).
-__device__ __forceinline__ bool walk_step(Walk &w, int nx, int ny, int nz, const int32_t *tab, int &offx,
-                                          int &offy, int &offz) {
-  if (w.tx <= w.ty && w.tx <= w.tz) {
-    if (!(w.tx < w.tmax)) return false;
-    w.ix += w.sx;
-    if ((unsigned)w.ix >= (unsigned)nx) return false;
-    w.tx = fmul(fsub((float)(w.ix + (w.sx > 0)), w.ox), w.invx);
-    offx = tab[w.ix];
-  } else if (w.ty <= w.tz) {
-    if (!(w.ty < w.tmax)) return false;
-    w.iy += w.sy;
-    if ((unsigned)w.iy >= (unsigned)ny) return false;
-    w.ty = fmul(fsub((float)(w.iy + (w.sy > 0)), w.oy), w.invy);
-    offy = tab[nx + w.iy];
-  } else {
-    if (!(w.tz < w.tmax)) return false;
-    w.iz += w.sz;
-    if ((unsigned)w.iz >= (unsigned)nz) return false;
-    w.tz = fmul(fsub((float)(w.iz + (w.sz > 0)), w.oz), w.invz);
-    offz = tab[nx + ny + w.iz];
-  }
+// Voxel index of the current position on one axis.
+__device__ __forceinline__ int walk_index(float b, float s) { return (int)b - (s > 0.0f ? 1 : 0); }
+
+// One step of the walk: x if t_x <= t_y and t_x <= t_z, else y if t_y <=
+// t_z, else z; false (and no change) when that crossing is not before t_max.
+// Branch-free: the chosen axis' plane moves by its step (the others by 0,
+// exact), all three crossing parameters are recomputed (unchanged planes
+// give bit-identical values), and all three table entries are re-read.
+__device__ __forceinline__ bool walk_advance(Walk &w, const int32_t *tab, int &offx, int &offy, int &offz) {
+  const bool mx = (w.tx <= w.ty) & (w.tx <= w.tz);
+  const bool my = !mx & (w.ty <= w.tz);
+  const bool mz = !mx & !my;
+  const float tsel = mx ? w.tx : (my ? w.ty : w.tz);
+  if (!(tsel < w.tmax)) return false;
+  w.bx = fadd(w.bx, mx ? w.sx : 0.0f);
+  w.by = fadd(w.by, my ? w.sy : 0.0f);
+  w.bz = fadd(w.bz, mz ? w.sz : 0.0f);
+  w.tx = fmul(fsub(w.bx, w.ox), w.vx);
+  w.ty = fmul(fsub(w.by, w.oy), w.vy);
+  w.tz = fmul(fsub(w.bz, w.oz), w.vz);
+  w.px += mx ? w.qx : 0;
+  w.py += my ? w.qy : 0;
+  w.pz += mz ? w.qz : 0;
+  offx = tab_at(tab, w.px);
+  offy = tab_at(tab, w.py);
+  offz = tab_at(tab, w.pz);
   return true;
+}
+
+// Linear x-fastest layout: the element index moves by a fixed step per axis
+// (+-1, +-nx, +-nx ny), so a step needs no table read.  Same walk, same
+// reference operation order as walk_advance.
+__device__ __forceinline__ void walk_linear_steps(Walk &w, int nx, int ny) {
+  w.qx = w.sx > 0.0f ? 1 : (w.sx < 0.0f ? -1 : 0);
+  w.qy = w.sy > 0.0f ? nx : (w.sy < 0.0f ? -nx : 0);
+  w.qz = w.sz > 0.0f ? nx * ny : (w.sz < 0.0f ? -nx * ny : 0);
+}
+
+__device__ __forceinline__ int walk_linear_index(const Walk &w, int nx, int ny) {
+  return (walk_index(w.bz, w.sz) * ny + walk_index(w.by, w.sy)) * nx + walk_index(w.bx, w.sx);
+}
+
+// One step of the walk on the linear layout, as predicated PTX: the axis
+// predicates px / py / pz select the x / y / z crossing (same order and
+// tie-break as walk_advance), and only the chosen axis' plane, crossing
+// parameter and element index are updated, each operation rounded on its
+// own.  The state advances on every call; the return value says whether the
+// crossing was before t_max, i.e. whether the new voxel is part of the walk
+// (callers stop at the first false and ignore the advanced state).  Because
+// exactly one axis moves per call, the number of calls made while walking a
+// ray equals the number of planes crossed, which ray_ig uses to count steps.
+// Crossing parameters are never NaN (b - o has the sign of d and is nonzero,
+// axes without a step hold +inf), so the three-input min equals the
+// reference walk's selected parameter.
+__device__ __forceinline__ bool walk_advance_lin(Walk &w, int &addr) {
+  unsigned int end;
+  asm("{\n\t"
+      ".reg .pred px, py, pz, pe, pt;\n\t"
+      ".reg .f32 ts, u;\n\t"
+      "setp.le.f32 px, %0, %1;\n\t"          // x: t_x <= t_y and t_x <= t_z
+      "setp.le.and.f32 px, %0, %2, px;\n\t"
+      "setp.le.and.f32 py, %1, %2, !px;\n\t" // y: not x and t_y <= t_z
+      "or.pred pt, px, py;\n\t"
+      "not.pred pz, pt;\n\t"                  // z: neither
+      "min.f32 ts, %0, %1, %2;\n\t"           // the chosen crossing
+      "setp.geu.f32 pe, ts, %17;\n\t"         // not before t_max: the walk ends
+      "selp.u32 %7, 1, 0, pe;\n\t"
+      "@px add.rn.f32 %3, %3, %8;\n\t"        // b_x += s_x
+      "@px sub.rn.f32 u, %3, %11;\n\t"        // t_x = (b_x - o_x) * (1 / d_x)
+      "@px mul.rn.f32 %0, u, %14;\n\t"
+      "@px add.s32 %6, %6, %18;\n\t"          // index += x stride
+      "@py add.rn.f32 %4, %4, %9;\n\t"
+      "@py sub.rn.f32 u, %4, %12;\n\t"
+      "@py mul.rn.f32 %1, u, %15;\n\t"
+      "@py add.s32 %6, %6, %19;\n\t"
+      "@pz add.rn.f32 %5, %5, %10;\n\t"
+      "@pz sub.rn.f32 u, %5, %13;\n\t"
+      "@pz mul.rn.f32 %2, u, %16;\n\t"
+      "@pz add.s32 %6, %6, %20;\n\t"
+      "}"
+      : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(addr), "=r"(end)
+      : "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy), "f"(w.vz),
+        "f"(w.tmax), "r"(w.qx), "r"(w.qy), "r"(w.qz));
+  return end == 0u;
 }
 
 // Host helpers (defined in nbt_map.cu).

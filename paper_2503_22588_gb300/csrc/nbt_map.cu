@@ -4,10 +4,11 @@
 // map data to the GPU for every ID computation (Section V attributes the
 // GPU's loss at few rays to that allocation and transfer).  Here the map
 // lives on the device for its whole life: nbt_map_create allocates it once,
-// nbt_map_upload re-lays a dense grid into B^3 Morton-ordered bricks with
-// one coalesced pass, and probability maps get a derived per-voxel signed
-// gain table (|value| = g(v) of Eq. 2 / entropy / unknown indicator, sign =
-// occupied) so the traversal reads one float per voxel step.
+// nbt_map_upload lays a dense grid out on the device (linear x-fastest, the
+// default, or B^3 Morton-ordered bricks) with one coalesced pass, and
+// probability maps get a derived per-voxel signed gain table (|value| = g(v)
+// of Eq. 2 / entropy / unknown indicator, sign = occupied) so the traversal
+// reads one float per voxel step.
 
 #include <math.h>
 #include <string.h>
@@ -108,6 +109,25 @@ __global__ void pack_u2_kernel(const uint8_t *__restrict__ src, uint8_t *__restr
     }
     const int32_t off = voxel_offset(tab, nx, ny, x0, y, z0 + zl);
     dst[off >> 2] = (uint8_t)byte;
+  }
+}
+
+// Dense uint8 states (voxels [v0, v0 + n) of the linear order) -> 2-bit
+// elements of the linear layout: byte k holds voxels 4k .. 4k+3.  v0 is a
+// multiple of 4, so every byte is written by exactly one thread.
+__global__ void pack_u2_linear_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst, int64_t v0,
+                                      int64_t n) {
+  const int64_t n_bytes = (n + 3) / 4;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_bytes; k += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t byte = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t v = 4 * k + u;
+      uint32_t s = v < n ? src[v] : 0u;
+      s = s > 2u ? 2u : s;
+      byte |= s << (2 * u);
+    }
+    dst[v0 / 4 + k] = (uint8_t)byte;
   }
 }
 
@@ -237,8 +257,8 @@ int nbt_map_create(const nbt_map_desc *desc, nbt_map *out) {
   if (!(d.voxel_size > 0.0f) || !isfinite(d.voxel_size)) return NBT_EINVAL;
   if (!isfinite(d.origin[0]) || !isfinite(d.origin[1]) || !isfinite(d.origin[2])) return NBT_EINVAL;
   if (d.encoding != NBT_U8_STATE && d.encoding != NBT_F32_PROB && d.encoding != NBT_U2_STATE) return NBT_EINVAL;
-  const int brick = d.brick == 0 ? 8 : d.brick;
-  if (brick != 4 && brick != 8) return NBT_EINVAL;
+  const int brick = d.brick == 0 ? 1 : d.brick;
+  if (brick != 1 && brick != 4 && brick != 8) return NBT_EINVAL;
 
   nbt_map m = new (std::nothrow) nbt_map_s();
   if (!m) return NBT_ENOMEM;
@@ -249,15 +269,26 @@ int nbt_map_create(const nbt_map_desc *desc, nbt_map *out) {
     delete m;
     return NBT_ECUDA;
   }
-  const int lb = brick == 8 ? 3 : 2;
+  const int lb = brick == 8 ? 3 : (brick == 4 ? 2 : 0);
   m->nbx = (d.nx + brick - 1) / brick;
   m->nby = (d.ny + brick - 1) / brick;
   m->nbz = (d.nz + brick - 1) / brick;
   std::vector<int64_t> px, py, pz;
   int64_t slots = 0;
-  brick_parts(m->nbx, m->nby, m->nbz, px, py, pz, &slots);
   const int64_t b3 = (int64_t)brick * brick * brick;
-  m->elems = slots * b3;
+  if (brick == 1) {  // linear x-fastest layout: element index = (z * ny + y) * nx + x
+    px.resize(m->nbx);
+    py.resize(m->nby);
+    pz.resize(m->nbz);
+    for (int b = 0; b < m->nbx; ++b) px[b] = b;
+    for (int b = 0; b < m->nby; ++b) py[b] = (int64_t)b * m->nbx;
+    for (int b = 0; b < m->nbz; ++b) pz[b] = (int64_t)b * m->nbx * m->nby;
+    slots = (int64_t)m->nbx * m->nby * m->nbz;
+    m->elems = (slots + 3) / 4 * 4;  // whole bytes of 2-bit elements
+  } else {
+    brick_parts(m->nbx, m->nby, m->nbz, px, py, pz, &slots);
+    m->elems = slots * b3;
+  }
   if (m->elems >= (1ll << 31)) {
     delete m;
     return NBT_EINVAL;
@@ -318,7 +349,9 @@ int nbt_map_upload(nbt_map map, const void *src, int64_t bytes, int32_t src_on_d
   if (bytes != plane * d.nz * es) return NBT_EINVAL;
   cudaStream_t stream = (cudaStream_t)stream_;
   std::lock_guard<std::mutex> lock(map->mu);
-  const int slab = src_on_device ? d.nz : (int)std::max<int64_t>(1, map->stage_bytes / (plane * es));
+  int slab = src_on_device ? d.nz : (int)std::max<int64_t>(1, map->stage_bytes / (plane * es));
+  // linear 2-bit maps: slab starts must fall on whole bytes (4 voxels)
+  if (d.encoding == NBT_U2_STATE && map->brick == 1 && slab < d.nz) slab = std::max(4, slab / 4 * 4);
   for (int z0 = 0; z0 < d.nz; z0 += slab) {
     const int nzs = std::min(slab, d.nz - z0);
     const char *s = (const char *)src + (int64_t)z0 * plane * es;
@@ -333,6 +366,9 @@ int nbt_map_upload(nbt_map map, const void *src, int64_t bytes, int32_t src_on_d
     } else if (d.encoding == NBT_F32_PROB) {
       scatter_bricks_kernel<float><<<grid_for(n), 256, 0, stream>>>((const float *)s, (float *)map->d_payload,
                                                                     map->d_tab, d.nx, d.ny, z0, n);
+    } else if (map->brick == 1) {
+      pack_u2_linear_kernel<<<grid_for((n + 3) / 4), 256, 0, stream>>>((const uint8_t *)s, (uint8_t *)map->d_payload,
+                                                                      (int64_t)z0 * plane, n);
     } else {
       const int64_t groups = (int64_t)((d.nx + 3) / 4) * d.ny * nzs;
       pack_u2_kernel<<<grid_for(groups), 256, 0, stream>>>((const uint8_t *)s, (uint8_t *)map->d_payload, map->d_tab,

@@ -5,17 +5,18 @@
 // voxels it crosses, up to and including the first occupied one (N_O); the
 // ray IGs of a perspective are summed (or averaged, g_P).
 //
-// GPU mapping.  A work item is one (pose, 32 x 8 ray tile); a CTA of 256
-// threads takes items from a device work queue (one atomicAdd per item) and
-// casts one ray per thread.  Each warp's 32 rays form an 8 x 4 pixel packet,
-// so at any step its lanes read neighbouring voxels of the same bricks.
-// Per ray, the walk runs KAHEAD voxels ahead of the gain accumulation: the
-// voxel sequence does not depend on the map, so KAHEAD addresses are formed
-// first and their loads issued together, and only the occlusion test waits
-// on the data.  Per-ray sums go through a fixed warp-shuffle tree and a
-// fixed 8-warp sum into one 16-byte partial per item; a second kernel adds
-// the partials of each perspective (or trajectory) in a fixed order in FP64,
-// so results do not depend on scheduling.
+// GPU mapping.  A work item is one (pose, 32 x 8 ray tile).  A CTA of 8
+// warps takes items from a device work queue (one atomicAdd per item); each
+// warp casts one 32-ray packet of the tile (packet_w x 32/packet_w pixels),
+// one ray per lane, so the 256 rays a CTA walks at once start at the same
+// camera and stay close, and their loads share L1 lines.  Each ray's walk is
+// branch-free (see Walk), and the payload element of the next voxel is
+// loaded before the current one is accumulated (the voxel sequence does not
+// depend on the map, only the occlusion test does).  Per-ray sums go
+// through a fixed warp-shuffle tree and a fixed 8-warp sum into one 16-byte
+// partial per item; a second kernel adds the partials of each perspective
+// (or trajectory) in a fixed order in FP64, so results do not depend on
+// scheduling.
 
 #include <math.h>
 
@@ -25,8 +26,6 @@
 
 namespace nbt {
 namespace {
-
-constexpr int kAhead = 4;
 
 bool valid_camera(const nbt_camera *c) {
   if (!c) return false;
@@ -71,6 +70,7 @@ CamConst make_cam(nbt_map map, const nbt_camera *c) {
   cc.H = h;
   cc.tiles_x = (w + kTileW - 1) / kTileW;
   cc.tiles_per_pose = cc.tiles_x * ((h + kTileH - 1) / kTileH);
+  cc.packet_w = map->packet_w;
   cc.inv_s = (float)(1.0 / (double)map->desc.voxel_size);
   cc.ox = map->desc.origin[0];
   cc.oy = map->desc.origin[1];
@@ -120,80 +120,102 @@ __device__ __forceinline__ uint32_t raw_load(const void *payload, uint32_t off) 
 }
 
 // IG of one ray: walk, read, accumulate, stop after the first occupied voxel.
-template <int KIND>
-__device__ __forceinline__ void ray_ig(const DevMap &m, const int32_t *tab, const float o[3], const float d[3],
-                                       bool include_hit, float &facc, uint32_t &iacc, uint32_t &steps) {
+// HIT: the occupied voxel adds its gain (the Section III sum runs to N_O).
+// LINEAR: linear layout with stride steps; else bricked with table reads.
+// Every payload read uses min(index, addr_max), a safety net that keeps
+// reads inside the payload (the walk itself never leaves the map).
+template <int KIND, bool HIT, bool LINEAR>
+__device__ __forceinline__ void ray_ig(const void *payload, const int32_t *tab, uint32_t addr_max, int nx, int ny,
+                                       int nz, const float o[3], const float d[3], float &facc, uint32_t &iacc,
+                                       uint32_t &steps) {
   Walk w;
-  if (!walk_init(w, o, d, m.nx, m.ny, m.nz)) return;
-  int offx = tab[w.ix], offy = tab[m.nx + w.iy], offz = tab[m.nx + m.ny + w.iz];
-  bool live = true;
-  for (;;) {
-    uint32_t addr[kAhead];
-    bool val[kAhead];
-#pragma unroll
-    for (int u = 0; u < kAhead; ++u) {
-      val[u] = live;
-      addr[u] = (uint32_t)(offx + offy + offz);
-      if (live) live = walk_step(w, m.nx, m.ny, m.nz, tab, offx, offy, offz);
-    }
-    uint32_t raw[kAhead];
-#pragma unroll
-    for (int u = 0; u < kAhead; ++u) raw[u] = val[u] ? raw_load<KIND>(m.payload, addr[u]) : 0u;
-    bool stop = false;
-#pragma unroll
-    for (int u = 0; u < kAhead; ++u) {
-      if (val[u] && !stop) {
-        bool occ;
-        if (KIND == PAYLOAD_GAIN_F32) {
-          occ = (raw[u] >> 31) != 0u;
-          const float g = __uint_as_float(raw[u] & 0x7fffffffu);
-          if (!occ || include_hit) facc += g;
-        } else {
-          uint32_t s = raw[u];
-          if (KIND == PAYLOAD_U2) s = (s >> ((addr[u] & 3u) << 1)) & 3u;
-          occ = s >= 2u;
-          iacc += (s == 0u) ? 1u : 0u;  // an occupied voxel is never unknown
-        }
-        steps += 1u;
-        stop = occ;
-      }
-    }
-    if (stop || !live) break;
+  if (!walk_init(w, o, d, nx, ny, nz)) return;
+  int offx = 0, offy = 0, offz = 0, lin = 0;
+  if (LINEAR) {
+    walk_linear_steps(w, nx, ny);
+    lin = walk_linear_index(w, nx, ny);
+  } else {
+    offx = tab_at(tab, w.px);
+    offy = tab_at(tab, w.py);
+    offz = tab_at(tab, w.pz);
   }
+  uint32_t addr = min(LINEAR ? (uint32_t)lin : (uint32_t)(offx + offy + offz), addr_max);
+  uint32_t raw = raw_load<KIND>(payload, addr);
+  const float bx0 = w.bx, by0 = w.by, bz0 = w.bz;
+  for (;;) {
+    bool more;
+    if (LINEAR) {
+      more = walk_advance_lin(w, lin);
+    } else {
+      more = walk_advance(w, tab, offx, offy, offz);
+      steps += 1u;
+    }
+    const uint32_t naddr = min(LINEAR ? (uint32_t)lin : (uint32_t)(offx + offy + offz), addr_max);
+    const uint32_t nraw = more ? raw_load<KIND>(payload, naddr) : 0u;
+    bool occ;
+    if (KIND == PAYLOAD_GAIN_F32) {
+      occ = (int32_t)raw < 0;
+      const float g = fabsf(__uint_as_float(raw));
+      if (HIT || !occ) facc += g;
+    } else {
+      uint32_t st = raw;
+      if (KIND == PAYLOAD_U2) st = (st >> ((addr & 3u) << 1)) & 3u;
+      occ = st >= 2u;
+      iacc += st == 0u ? 1u : 0u;  // an occupied voxel is never unknown
+    }
+    if (occ || !more) break;
+    raw = nraw;
+    addr = naddr;
+  }
+  // Linear walk: one call of walk_advance_lin per visited voxel, each moving
+  // one plane by one, so the visited count is the plane travel (exact
+  // integer-valued floats).
+  if (LINEAR) steps += (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
 }
 
-// Item = (pose, ray tile); CTA-wide partial sums into partials[item].
-template <int KIND>
-__global__ void __launch_bounds__(kThreads) ig_tiles_kernel(DevMap m, CamConst cc, const float *__restrict__ poses,
-                                                           int64_t n_items, int include_hit,
-                                                           unsigned long long *queue, Partial *partials) {
+// Items = (pose, 32 x 8 ray tile).  A CTA takes one item at a time; warp w
+// casts packet w of the tile; the 8 packet sums are added in warp order
+// into partials[item].
+template <int KIND, bool HIT, bool LINEAR>
+__global__ void __launch_bounds__(kThreads, LINEAR ? 6 : 5)
+    ig_tiles_kernel(DevMap m, CamConst cc, const float *__restrict__ poses, int64_t n_items, uint32_t addr_max,
+                    unsigned long long *queue, Partial *partials) {
   extern __shared__ int32_t stab[];
+  __shared__ float s_pose[8];
   __shared__ float s_f[kThreads / 32];
   __shared__ uint32_t s_i[kThreads / 32], s_s[kThreads / 32];
   __shared__ long long s_item;
-  const int ntab = m.nx + m.ny + m.nz;
-  for (int k = threadIdx.x; k < ntab; k += blockDim.x) stab[k] = m.tab[k];
+  if (!LINEAR) {
+    const int ntab = m.nx + m.ny + m.nz;
+    for (int k = threadIdx.x; k < ntab; k += blockDim.x) stab[k] = m.tab[k];
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int pi = (warp & 3) * 8 + (lane & 7);   // 8 x 4 pixel packet per warp, 4 x 2 warps per tile
-  const int pj = (warp >> 2) * 4 + (lane >> 3);
+  const int pw = cc.packet_w, ph = 32 / pw, across = 32 / pw;
+  const int di = (warp % across) * pw + lane % pw;  // pixel of this lane within the tile
+  const int dj = (warp / across) * ph + lane / pw;
   for (;;) {
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(queue, 1ull);
+      s_item = it;
+      if (it < n_items) {
+        const long long pose = it / cc.tiles_per_pose;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s_pose[k] = __ldg(poses + pose * 7 + k);
+      }
+    }
     __syncthreads();
     const long long item = s_item;
     if (item >= n_items) break;
     const long long pose = item / cc.tiles_per_pose;
     const int tile = (int)(item - pose * cc.tiles_per_pose);
-    const int i = (tile % cc.tiles_x) * kTileW + pi;
-    const int j = (tile / cc.tiles_x) * kTileH + pj;
+    const int i = (tile % cc.tiles_x) * kTileW + di;
+    const int j = (tile / cc.tiles_x) * kTileH + dj;
     float facc = 0.0f;
     uint32_t iacc = 0u, steps = 0u;
     if (i < cc.W && j < cc.H) {
-      float pz[7];
-#pragma unroll
-      for (int k = 0; k < 7; ++k) pz[k] = __ldg(poses + pose * 7 + k);
       float o[3], d[3];
-      ray_segment(cc, pz, i, j, o, d);
-      ray_ig<KIND>(m, stab, o, d, include_hit != 0, facc, iacc, steps);
+      ray_segment(cc, s_pose, i, j, o, d);
+      ray_ig<KIND, HIT, LINEAR>(m.payload, stab, addr_max, m.nx, m.ny, m.nz, o, d, facc, iacc, steps);
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
@@ -299,50 +321,95 @@ __global__ void view_segments_kernel(CamConst cc, const float *__restrict__ pose
   }
 }
 
-template <int KIND>
+// Test kernel: the voxel sequence of each segment, walked by the same step
+// function as the IG kernel for the map's layout.
+template <int KIND, bool LINEAR>
 __global__ void trace_kernel(DevMap m, const float *__restrict__ o, const float *__restrict__ d, int n_rays,
-                             int use_occ, int32_t *__restrict__ idx_out, int cap, int32_t *__restrict__ n_out) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_rays) return;
-  const float oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
-  const float dd[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
-  Walk w;
-  int count = 0;
-  if (walk_init(w, oo, dd, m.nx, m.ny, m.nz)) {
-    int offx = m.tab[w.ix], offy = m.tab[m.nx + w.iy], offz = m.tab[m.nx + m.ny + w.iz];
-    for (;;) {
-      if (count < cap) idx_out[(int64_t)r * cap + count] = (w.iz * m.ny + w.iy) * m.nx + w.ix;
-      ++count;
-      if (use_occ) {
-        float g;
-        uint32_t unk;
-        bool occ;
-        read_voxel<KIND>(m.payload, (uint32_t)(offx + offy + offz), g, unk, occ);
-        if (occ) break;
+                             int use_occ, uint32_t addr_max, int32_t *__restrict__ idx_out, int cap,
+                             int32_t *__restrict__ n_out) {
+  extern __shared__ int32_t stab[];
+  const int ntab = m.nx + m.ny + m.nz;
+  if (!LINEAR)
+    for (int k = threadIdx.x; k < ntab; k += blockDim.x) stab[k] = m.tab[k];
+  __syncthreads();
+  const int limit = ntab + 2;  // a walk visits at most nx + ny + nz - 2 voxels
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rays; r += gridDim.x * blockDim.x) {
+    const float oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
+    const float dd[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
+    Walk w;
+    int count = 0;
+    if (walk_init(w, oo, dd, m.nx, m.ny, m.nz)) {
+      int offx = 0, offy = 0, offz = 0, lin = 0;
+      if (LINEAR) {
+        walk_linear_steps(w, m.nx, m.ny);
+        lin = walk_linear_index(w, m.nx, m.ny);
+      } else {
+        offx = tab_at(stab, w.px);
+        offy = tab_at(stab, w.py);
+        offz = tab_at(stab, w.pz);
       }
-      if (!walk_step(w, m.nx, m.ny, m.nz, m.tab, offx, offy, offz)) break;
+      while (count < limit) {
+        const int ix = walk_index(w.bx, w.sx), iy = walk_index(w.by, w.sy), iz = walk_index(w.bz, w.sz);
+        if (count < cap) idx_out[(int64_t)r * cap + count] = (iz * m.ny + iy) * m.nx + ix;
+        ++count;
+        if (use_occ) {
+          float g;
+          uint32_t unk;
+          bool occ;
+          const uint32_t a = min(LINEAR ? (uint32_t)lin : (uint32_t)(offx + offy + offz), addr_max);
+          read_voxel<KIND>(m.payload, a, g, unk, occ);
+          if (occ) break;
+        }
+        const bool more = LINEAR ? walk_advance_lin(w, lin) : walk_advance(w, stab, offx, offy, offz);
+        if (!more) break;
+      }
     }
+    n_out[r] = count;
   }
-  n_out[r] = count;
 }
 
 size_t tile_smem(nbt_map map) { return (size_t)(map->desc.nx + map->desc.ny + map->desc.nz) * sizeof(int32_t); }
 
-template <int KIND>
-int launch_tiles(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
-                 int include_hit, void *workspace, cudaStream_t stream) {
-  const size_t smem = tile_smem(map);
+uint32_t addr_max_of(nbt_map map) { return (uint32_t)(map->elems - 1); }
+
+template <int KIND, bool HIT, bool LINEAR>
+int launch_tiles_t(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
+                   void *workspace, cudaStream_t stream) {
+  const size_t smem = LINEAR ? 0 : tile_smem(map);
   int per_sm = 0;
-  NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ig_tiles_kernel<KIND>, kThreads, smem));
+  NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ig_tiles_kernel<KIND, HIT, LINEAR>, kThreads,
+                                                             smem));
   per_sm = std::max(per_sm, 1);
   const int64_t grid = std::min<int64_t>(n_items, (int64_t)sm_count() * per_sm);
   unsigned long long *queue = (unsigned long long *)workspace;
   Partial *partials = (Partial *)((char *)workspace + 256);
   NBT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream));
-  ig_tiles_kernel<KIND><<<(unsigned)grid, kThreads, smem, stream>>>(dev_map(map, payload), cc, poses, n_items,
-                                                                   include_hit, queue, partials);
+  ig_tiles_kernel<KIND, HIT, LINEAR><<<(unsigned)grid, kThreads, smem, stream>>>(
+      dev_map(map, payload), cc, poses, n_items, addr_max_of(map), queue, partials);
   NBT_CUDA_TRY(cudaGetLastError());
   return NBT_OK;
+}
+
+template <int KIND>
+int launch_tiles(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
+                 int include_hit, void *workspace, cudaStream_t stream) {
+  const bool lin = map->brick == 1;
+  if (include_hit)
+    return lin ? launch_tiles_t<KIND, true, true>(map, payload, cc, poses, n_items, workspace, stream)
+               : launch_tiles_t<KIND, true, false>(map, payload, cc, poses, n_items, workspace, stream);
+  return lin ? launch_tiles_t<KIND, false, true>(map, payload, cc, poses, n_items, workspace, stream)
+             : launch_tiles_t<KIND, false, false>(map, payload, cc, poses, n_items, workspace, stream);
+}
+
+template <int KIND>
+void launch_trace(nbt_map map, const DevMap &m, unsigned grid, cudaStream_t stream, const float *o, const float *d,
+                  int n_rays, int use_occ, int32_t *idx_out, int cap, int32_t *n_out) {
+  const size_t smem = tile_smem(map);
+  const uint32_t amax = addr_max_of(map);
+  if (map->brick == 1)
+    trace_kernel<KIND, true><<<grid, 128, 0, stream>>>(m, o, d, n_rays, use_occ, amax, idx_out, cap, n_out);
+  else
+    trace_kernel<KIND, false><<<grid, 128, smem, stream>>>(m, o, d, n_rays, use_occ, amax, idx_out, cap, n_out);
 }
 
 int run_tiles(nbt_map map, const nbt_pose *poses, int64_t n_poses, const nbt_camera *cam,
@@ -451,12 +518,12 @@ int nbt_trace_segments(nbt_map map, const float *o, const float *d, int32_t n_ra
     }
   }
   const DevMap m = dev_map(map, payload);
-  const unsigned grid = (unsigned)((n_rays + 127) / 128);
+  const unsigned grid = (unsigned)std::min<int64_t>((n_rays + 127) / 128, (int64_t)sm_count() * 8);
   const int use_occ = params != nullptr;
   switch (kind) {
-    case PAYLOAD_U8: trace_kernel<PAYLOAD_U8><<<grid, 128, 0, stream>>>(m, o, d, n_rays, use_occ, idx_out, cap, n_out); break;
-    case PAYLOAD_U2: trace_kernel<PAYLOAD_U2><<<grid, 128, 0, stream>>>(m, o, d, n_rays, use_occ, idx_out, cap, n_out); break;
-    default: trace_kernel<PAYLOAD_GAIN_F32><<<grid, 128, 0, stream>>>(m, o, d, n_rays, use_occ, idx_out, cap, n_out); break;
+    case PAYLOAD_U8: launch_trace<PAYLOAD_U8>(map, m, grid, stream, o, d, n_rays, use_occ, idx_out, cap, n_out); break;
+    case PAYLOAD_U2: launch_trace<PAYLOAD_U2>(map, m, grid, stream, o, d, n_rays, use_occ, idx_out, cap, n_out); break;
+    default: launch_trace<PAYLOAD_GAIN_F32>(map, m, grid, stream, o, d, n_rays, use_occ, idx_out, cap, n_out); break;
   }
   NBT_CUDA_TRY(cudaGetLastError());
   return NBT_OK;
@@ -541,5 +608,20 @@ extern "C" int nbt_views_ig_noalloc(nbt_map map, const nbt_pose *poses, int64_t 
   views_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
       partials, n_views, cc.tiles_per_pose, params->reduce == NBT_REDUCE_MEAN, (double)cc.W * cc.H, ig_out, steps_out);
   NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+extern "C" int nbt_map_set_tuning(nbt_map map, const nbt_tuning *tuning) {
+  if (!map || !tuning) return NBT_EINVAL;
+  const int pw = tuning->packet_w == 0 ? 8 : tuning->packet_w;
+  if (pw != 4 && pw != 8 && pw != 16 && pw != 32) return NBT_EINVAL;
+  map->packet_w = pw;
+  return NBT_OK;
+}
+
+extern "C" int nbt_map_get_tuning(nbt_map map, nbt_tuning *tuning) {
+  if (!map || !tuning) return NBT_EINVAL;
+  tuning->packet_w = map->packet_w;
+  tuning->brick = map->brick;
   return NBT_OK;
 }

@@ -59,6 +59,7 @@ def test_structs_match_header_sizes():
     assert C.sizeof(_lib.MapDesc) == 36
     assert C.sizeof(_lib.Camera) == 28
     assert C.sizeof(_lib.IgParams) == 20
+    assert C.sizeof(_lib.Tuning) == 8
 
 
 def test_product_package_does_not_touch_the_oracle():

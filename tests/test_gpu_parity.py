@@ -78,7 +78,7 @@ def test_view_segments_bitexact(grid_mode, range_mode, wh):
 
 
 @pytest.mark.parametrize("dims", [(16, 16, 16), (37, 20, 50), (256, 256, 256), (1, 1, 1), (5, 64, 3)])
-@pytest.mark.parametrize("brick", [4, 8])
+@pytest.mark.parametrize("brick", [1, 4, 8])
 def test_trace_segments_bitexact(dims, brick):
     rng = np.random.default_rng(dims[0] * 7 + brick)
     o, d = _segments(rng, dims, 3000, max_len=1.5 * max(dims))
@@ -97,7 +97,7 @@ def test_trace_segments_bitexact(dims, brick):
 
 
 @pytest.mark.parametrize("encoding", ["u8", "u2"])
-@pytest.mark.parametrize("brick", [4, 8])
+@pytest.mark.parametrize("brick", [1, 4, 8])
 def test_trace_views_occluded_bitexact(encoding, brick):
     w = configs.exact64(seed=4, n_views=6)
     gm = gpu_map(w, brick, encoding)
@@ -117,7 +117,7 @@ def test_trace_views_occluded_bitexact(encoding, brick):
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-@pytest.mark.parametrize("encoding,brick", [("u8", 8), ("u8", 4), ("u2", 8), ("u2", 4)])
+@pytest.mark.parametrize("encoding,brick", [("u8", 1), ("u8", 8), ("u8", 4), ("u2", 1), ("u2", 8), ("u2", 4)])
 def test_views_ig_count_exact(seed, encoding, brick):
     """64^3 states, 64 views, 64 x 48 rays: unknown counts and steps equal the oracle's exactly."""
     w = configs.exact64(seed=seed)
@@ -131,7 +131,7 @@ def test_views_ig_count_exact(seed, encoding, brick):
 
 
 @pytest.mark.parametrize("metric", ["entropy", "eq2", "count"])
-@pytest.mark.parametrize("brick", [8, 4])
+@pytest.mark.parametrize("brick", [1, 8, 4])
 def test_views_ig_probability_map(metric, brick):
     """Reduced tabletop (96^3 FP32), 24 views of 80 x 60 rays."""
     w = configs.prob256(seed=3, n_views=24, n=96, n_prims=40)
@@ -283,3 +283,49 @@ def test_host_upload_matches_device_upload():
     rc = views_gpu(a, w.poses, gpu_camera(w.camera), nbt.ig_params("entropy"))
     rig, _ = oracle.views_ig(oracle.Map(g2), w.poses, oracle_camera(w.camera), oracle.params("entropy"))
     assert np.all(rel_err(rc[0], rig) <= RTOL)
+
+
+@pytest.mark.parametrize("brick", [1, 4, 8])
+def test_odd_dims_two_bit_upload_and_walk(brick):
+    """Non-multiple-of-4 dims: 2-bit bytes straddle rows in the linear layout."""
+    dims = (37, 21, 19)
+    grid = scenes.random_states(dims[::-1], 0.35, 0.08, seed=11)
+    w = configs.Workload("t", 0, "u2", "count", configs.Camera(40, 30), grid, None, None)
+    poi = np.array(dims, np.float64) * 0.005
+    w.poses = poses.sphere_views(poi, 12, 0.25)
+    for src in ("host", "device"):
+        g = grid if src == "host" else torch.from_numpy(grid).cuda()
+        gm = nbt.Map.from_grid(g, 0.01, (0.0, 0.0, 0.0), "u2", brick)
+        ig, st = views_gpu(gm, w.poses, gpu_camera(w.camera), nbt.ig_params("count"))
+        rig, rst = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(w.camera), oracle.params("count"))
+        assert np.array_equal(st, rst) and np.array_equal(ig, rig), (src, brick)
+
+
+@pytest.mark.parametrize("packet_w", [4, 8, 16, 32])
+def test_packet_shapes_same_results(packet_w):
+    w = configs.exact64(seed=9, n_views=16)
+    gm = gpu_map(w)
+    gm.set_tuning(packet_w)
+    assert gm.tuning() == {"packet_w": packet_w, "brick": 1}
+    ig, st = views_gpu(gm, w.poses, gpu_camera(w.camera), nbt.ig_params("count"))
+    rig, rst = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(w.camera), oracle.params("count"))
+    assert np.array_equal(st, rst) and np.array_equal(ig, rig)
+    with pytest.raises(nbt.NbtError):
+        gm.set_tuning(6)
+
+
+def test_large_host_upload_in_slabs():
+    """A host upload larger than the 64 MiB staging buffer goes through several slabs."""
+    n = 416  # 416^3 bytes = 72 MB of uint8 states
+    grid = scenes.random_states((n, n, n), 0.3, 0.02, seed=4)
+    for enc, brick in (("u8", 1), ("u2", 1), ("u2", 8)):
+        a = nbt.Map.from_grid(grid, 0.01, (0.0, 0.0, 0.0), enc, brick)
+        b = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01, (0.0, 0.0, 0.0), enc, brick)
+        poi = np.full(3, n * 0.005)
+        p = poses.sphere_views(poi, 8, 0.6)
+        cam = nbt.camera(32, 24, 1.0, 0.8, 1.2)
+        ra = views_gpu(a, p, cam, nbt.ig_params("count"))
+        rb = views_gpu(b, p, cam, nbt.ig_params("count"))
+        assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1]), (enc, brick)
+        a.close()
+        b.close()
