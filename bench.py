@@ -43,6 +43,8 @@ def describe(w) -> str:
                    "64x48 rays, unknown-voxel count",
         "room512": "room512: 512^3 2-bit states (2000 primitives, 40% unknown), 8 PoIs x 4096 views, "
                    "320x240 rays, unknown-voxel count",
+        "traj256": "traj256: 256^3 uint8 tabletop, 512 trajectories of 5-40 poses around 4 PoIs, 128x96 rays, "
+                   "trajectory IG = sum of per-pose unknown counts, one CUDA-graph replay per step",
     }.get(w.name, w.name)
 
 
@@ -147,6 +149,28 @@ def cpu_baseline(w, budget_s: float = 12.0) -> dict:
             "voxel_steps_per_s": float(st.sum()) / dt}
 
 
+def traj_cpu_baseline(w, budget_s: float = 12.0) -> dict:
+    """The oracle on a bounded sample of trajectories (all their poses)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    m = oracle.Map(w.grid, w.voxel_size, w.origin)
+    cam = oracle.camera_of(w.camera)
+    prm = oracle.params(w.metric)
+    t0 = time.perf_counter()
+    oracle.views_ig(m, w.poses[:threads], cam, prm, "f32", threads)
+    per_pose = (time.perf_counter() - t0) / threads
+    n_traj, n_poses = 0, 0
+    while n_traj < len(w.offsets) - 1 and (n_poses + 1) * per_pose < budget_s:
+        n_traj += 1
+        n_poses = int(w.offsets[n_traj])
+    t0 = time.perf_counter()
+    _, st = oracle.traj_ig(m, w.poses[:n_poses], w.offsets[:n_traj + 1], cam, prm, "f32", threads)
+    dt = time.perf_counter() - t0
+    return {"value": n_poses / dt, "unit": "views/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {n_traj} of {len(w.offsets) - 1} trajectories ({n_poses} poses, {int(st.sum())} "
+                      f"voxel steps)", "voxel_steps_per_s": float(st.sum()) / dt}
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -189,7 +213,7 @@ def main() -> None:
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--workload", default="prob256", choices=["prob256", "exact64", "room512"])
+    ap.add_argument("--workload", default="prob256", choices=["prob256", "exact64", "room512", "traj256"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -213,6 +237,9 @@ def main() -> None:
     stream = torch.cuda.current_stream(dev)
 
     w = build_workload(args.workload, rank)
+    if w.offsets is not None:
+        run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist)
+        return
     cam = nbt.camera(w.camera.width, w.camera.height, w.camera.fov_h, w.camera.fov_v, w.camera.max_range)
     prm = nbt.ig_params(w.metric)
     grid_dev = torch.from_numpy(np.ascontiguousarray(w.grid)).to(dev)
@@ -338,6 +365,100 @@ def main() -> None:
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist) -> None:
+    """Trajectory workload: autotuned map + one CUDA-graph replay of nbt_traj_ig per step."""
+    cam = nbt.camera(w.camera.width, w.camera.height, w.camera.fov_h, w.camera.fov_v, w.camera.max_range)
+    prm = nbt.ig_params(w.metric)
+    grid_dev = torch.from_numpy(np.ascontiguousarray(w.grid)).to(dev)
+    poses_dev = torch.from_numpy(w.poses).to(dev)
+    off_dev = torch.from_numpy(w.offsets).to(dev)
+    m, tuned, _ = nbt.autotune(grid_dev, w.voxel_size, w.origin, w.encoding, poses_dev, cam, prm, offsets=off_dev,
+                               reps=2)
+    _, st = nbt.views_ig(m, poses_dev, cam, prm)
+    n_steps_voxel = int(st.sum().item())
+    plan = nbt.TrajPlan(m, poses_dev, off_dev, cam, prm)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        m.upload(grid_dev, stream)
+        plan.launch(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, b, c = ev[k]
+        a.record(stream)
+        m.upload(grid_dev, stream)
+        b.record(stream)
+        plan.launch(stream)
+        c.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = float(sum(a.elapsed_time(c) for a, b, c in ev))
+    ig_ms = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # end to end: host grid, poses and offsets in, trajectory IG out
+    grid_host = torch.from_numpy(np.ascontiguousarray(w.grid)).pin_memory()
+    poses_host = torch.from_numpy(w.poses).pin_memory()
+    off_host = torch.from_numpy(w.offsets).pin_memory()
+    out_host = torch.empty(len(w.offsets) - 1, dtype=torch.float32).pin_memory()
+    e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, _, c = ev[k]
+        a.record(stream)
+        m.upload(grid_host.numpy(), stream)
+        poses_dev.copy_(poses_host, non_blocking=True)
+        off_dev.copy_(off_host, non_blocking=True)
+        out_host.copy_(plan.launch(stream), non_blocking=True)
+        c.record(stream)
+        c.synchronize()
+        e_ms.append(a.elapsed_time(c))
+    e2e_total = float(sum(e_ms))
+    peak, peak_kind = load_peaks()
+    bps = BYTES_PER_STEP[w.encoding]
+    poses_total = world * w.n_poses * args.steps
+    line = {
+        "metric": METRIC, "value": poses_total / (total_ms * 1e-3), "unit": "views/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": describe(w), "poses_per_gpu": w.n_poses, "trajectories": len(w.offsets) - 1,
+                   "rays_per_pose": w.rays_per_pose, "map": f"{w.n}^3 {w.encoding}", "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB write)", "tuned": tuned,
+                   "step": "map upload + CUDA-graph replay of nbt_traj_ig"},
+        "voxel_steps_per_s": world * n_steps_voxel * args.steps / (total_ms * 1e-3),
+        "voxel_steps_per_step": n_steps_voxel, "traj_ig_ms": ig_ms,
+        "roofline": {"bound": "hbm", "achieved": n_steps_voxel * bps / (ig_ms * 1e-3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": n_steps_voxel * bps / (ig_ms * 1e-3) / 1e9 / peak,
+                     "traffic": ncu_traffic(args.workload), "kernel": "ig_tiles_kernel (+traj_reduce)",
+                     "algorithmic": f"{bps} B per voxel step x {n_steps_voxel} steps",
+                     "peak_kind": f"{peak_kind} (hbm_gbs)"},
+        "e2e": {"value": poses_total / (e2e_total * 1e-3), "unit": "views/s",
+                "h2d_bytes_per_step": int(grid_host.numel() + poses_host.numel() * 4 + off_host.numel() * 4),
+                "d2h_bytes_per_step": int(out_host.numel() * 4)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = traj_cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    m.close()
 
 
 if __name__ == "__main__":

@@ -220,6 +220,25 @@ int nbt_trace_segments(nbt_map map, const float *o, const float *d, int32_t n_ra
 int nbt_view_segments(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_camera *cam, float *o_out,
                       float *d_out, void *stream);
 
+/* CUDA-graph executor for repeated trajectory IG (the Section IV planner
+ * re-scores candidate trajectories every cycle with unchanged shapes).
+ * nbt_plan_create_traj captures one nbt_traj_ig call with exactly these
+ * arguments (work-queue reset, the persistent tile kernel, the per-
+ * trajectory reduction) into a CUDA graph; nbt_plan_launch replays it on
+ * `stream`.  The graph keeps the pointers: every buffer passed here must
+ * stay allocated until nbt_plan_destroy, and the caller may change the
+ * contents of poses, offsets and the map between launches (not n_poses,
+ * n_traj, the camera or the params).  A probability map's derived gains
+ * are refreshed outside the graph when the map was re-uploaded.  Creating
+ * a plan synchronises an internal stream; launching does not synchronise.
+ * Errors: as nbt_traj_ig, plus NBT_ECUDA if capture fails. */
+typedef struct nbt_plan_s *nbt_plan;
+int nbt_plan_create_traj(nbt_map map, const nbt_pose *poses, int64_t n_poses, const int32_t *offsets, int32_t n_traj,
+                         const nbt_camera *cam, const nbt_ig_params *params, float *traj_ig_out, float *pose_ig_out,
+                         void *workspace, int64_t workspace_bytes, nbt_plan *out);
+int nbt_plan_launch(nbt_plan plan, void *stream);
+int nbt_plan_destroy(nbt_plan plan);
+
 /* Launch tuning of the IG kernels for one map (chosen by the autotuner in
  * the Python package).  packet_w: width of a warp's ray packet in pixels,
  * 4, 8, 16 or 32 (height 32 / packet_w; 0 = default 8).  brick: read-only

@@ -63,6 +63,10 @@ SIGNATURES = {
     "nbt_view_segments": (C.c_int, [_vp, _vp, _i64, P(Camera), _vp, _vp, _vp]),
     "nbt_views_ig_noalloc": (C.c_int, [_vp, _vp, _i64, P(Camera), P(IgParams), _vp, _vp, _vp]),
     "nbt_map_set_tuning": (C.c_int, [_vp, P(Tuning)]),
+    "nbt_plan_create_traj": (C.c_int, [_vp, _vp, _i64, _vp, _i32, P(Camera), P(IgParams), _vp, _vp, _vp, _i64,
+                                       P(_vp)]),
+    "nbt_plan_launch": (C.c_int, [_vp, _vp]),
+    "nbt_plan_destroy": (C.c_int, [_vp]),
     "nbt_map_get_tuning": (C.c_int, [_vp, P(Tuning)]),
 }
 

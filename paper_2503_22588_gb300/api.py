@@ -207,3 +207,44 @@ def views_ig_noalloc(m: Map, poses: torch.Tensor, cam: Camera, params: IgParams,
                                      C.byref(params), _dev(out, torch.float32, "out"), sp, _stream(stream)),
           "nbt_views_ig_noalloc")
     return out, steps
+
+
+class TrajPlan:
+    """nbt_plan: one nbt_traj_ig call captured in a CUDA graph, replayed per planning cycle.
+
+    The tensors passed here are kept alive by the plan; refill ``poses`` and
+    ``offsets`` in place between launches.
+    """
+
+    def __init__(self, m: Map, poses: torch.Tensor, offsets: torch.Tensor, cam: Camera, params: IgParams,
+                 out: torch.Tensor | None = None, pose_out: torch.Tensor | None = None):
+        n = poses.shape[0]
+        nt = offsets.shape[0] - 1
+        self.map, self.poses, self.offsets = m, poses, offsets
+        self.out = out if out is not None else torch.empty(max(nt, 0), dtype=torch.float32, device=offsets.device)
+        self.pose_out = pose_out
+        self.ws = workspace(n, cam, offsets.device)
+        self._cam, self._params = cam, params
+        h = C.c_void_p()
+        po = _dev(pose_out, torch.float32, "pose_out") if pose_out is not None else None
+        check(lib().nbt_plan_create_traj(m.handle, _dev(poses, torch.float32, "poses", (7,)) if n else None, n,
+                                         _dev(offsets, torch.int32, "offsets"), nt, C.byref(cam), C.byref(params),
+                                         _dev(self.out, torch.float32, "out") if nt > 0 else None, po,
+                                         _dev(self.ws, torch.uint8, "workspace"), self.ws.numel(), C.byref(h)),
+              "nbt_plan_create_traj")
+        self._h = h
+
+    def launch(self, stream=None) -> torch.Tensor:
+        check(lib().nbt_plan_launch(self._h, _stream(stream)), "nbt_plan_launch")
+        return self.out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            lib().nbt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
