@@ -254,6 +254,20 @@ typedef struct {
 int nbt_map_set_tuning(nbt_map map, const nbt_tuning *tuning);
 int nbt_map_get_tuning(nbt_map map, nbt_tuning *tuning);
 
+/* Tensor-core GEMM behind the learned IG surrogate (the paper has no
+ * learned component; the surrogate prunes candidate perspectives before the
+ * exact Section III raycast re-scores them).  Test entry point:
+ * c[m][n] = sum_k a[m][k] * b[n][k] with BF16 a (m x k) and b (n x k),
+ * row-major, 16-byte aligned, k % 8 == 0, 1 <= n <= 256; FP32 c (m x n,
+ * row-major), accumulated in FP32 by tcgen05 MMAs.  Device pointers.
+ * Errors: NBT_EINVAL, NBT_ECUDA. */
+int nbt_tc_gemm(const void *a, const void *b, float *c, int32_t m, int32_t n, int32_t k, void *stream);
+
+/* The tensor-core kernels' device error word on the current device: 1 if a
+ * bounded device-side wait gave up since the last read (then the results
+ * of that launch are invalid).  Synchronises; reading clears the word. */
+int nbt_tc_error(int32_t *flag);
+
 /* Size of the fixed device scratch array behind nbt_views_ig_noalloc. */
 #define NBT_NOALLOC_SCRATCH_BYTES (4 << 20)
 

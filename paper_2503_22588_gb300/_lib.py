@@ -67,6 +67,8 @@ SIGNATURES = {
                                        P(_vp)]),
     "nbt_plan_launch": (C.c_int, [_vp, _vp]),
     "nbt_plan_destroy": (C.c_int, [_vp]),
+    "nbt_tc_gemm": (C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp]),
+    "nbt_tc_error": (C.c_int, [P(C.c_int32)]),
     "nbt_map_get_tuning": (C.c_int, [_vp, P(Tuning)]),
 }
 
