@@ -268,6 +268,57 @@ int nbt_tc_gemm(const void *a, const void *b, float *c, int32_t m, int32_t n, in
  * of that launch are invalid).  Synchronises; reading clears the word. */
 int nbt_tc_error(int32_t *flag);
 
+/* The learned IG surrogate (no counterpart in the paper; it prunes
+ * candidate perspectives before the exact Section III raycast re-scores
+ * them).  Input per perspective: a view-aligned crop -- 32 x 32 x 32
+ * samples on the rays through the pixel centres of a 32 x 32 image of the
+ * field of view, at depth fractions (k + 1/2) / 32 of d_Cam, each the
+ * one-hot class (unknown / free / occupied in channels 0 / 1 / 2 of 8,
+ * zero outside the map) of the voxel holding it, BF16 NDHWC [n][32][32][32]
+ * [8] -- and 8 BF16 pose features ((position - origin) / map extent, the
+ * quaternion, 1).  Output: the predicted mean ray IG (the training target
+ * the caller chooses, e.g. g_P / 100).  Network: 3^3 convolutions 8->16
+ * (stride 1), 16->32, 32->64, 64->64 (stride 2), ReLU; 4096 + 8 -> 128
+ * (ReLU) -> 1; BF16 weights and activations, FP32 accumulation on tcgen05
+ * tensor cores, FP32 master weights, MSE loss, Adam. */
+typedef struct nbt_surrogate_s *nbt_surrogate;
+
+/* Number of FP32 parameters (the layout of set/get_params: per conv layer
+ * W [C_out][27 C_in] (tap (dz*3+dy)*3+dx, then C_in) and b [C_out]; then
+ * F1 [128][4104], g1 [128], f2 [128], g2 [1]). */
+int nbt_surrogate_param_count(int64_t *n);
+
+/* Create a network on the current device with activation buffers for up
+ * to max_batch (1 .. 4096) samples per pass; parameters start at zero.
+ * Errors: NBT_EINVAL, NBT_ENOMEM, NBT_ECUDA. */
+int nbt_surrogate_create(int32_t max_batch, nbt_surrogate *out);
+int nbt_surrogate_destroy(nbt_surrogate net);
+
+/* Copy all parameters from / to host memory (n must equal the count);
+ * set_params also resets the Adam state.  Synchronous. */
+int nbt_surrogate_set_params(nbt_surrogate net, const float *host, int64_t n);
+int nbt_surrogate_get_params(nbt_surrogate net, float *host, int64_t n);
+
+/* Crops and pose features of n poses (device arrays as described above;
+ * crops 16-byte aligned).  params supplies the occupancy thresholds of
+ * probability maps.  Asynchronous on stream. */
+int nbt_surrogate_crops(nbt_map map, const nbt_pose *poses, int64_t n, const nbt_camera *cam,
+                        const nbt_ig_params *params, void *crops, void *feats, void *stream);
+
+/* Predictions (device float[n]) for n crops, in passes of max_batch. */
+int nbt_surrogate_forward(nbt_surrogate net, const void *crops, const void *feats, int64_t n, float *pred,
+                          void *stream);
+
+/* Loss (mean squared error against targets) and its gradient w.r.t. every
+ * parameter for one batch (n <= max_batch, n <= 1024), without updating.
+ * grads_out: device float[count] or NULL; loss_out: device float or NULL. */
+int nbt_surrogate_backward(nbt_surrogate net, const void *crops, const void *feats, const float *targets, int32_t n,
+                           float *grads_out, float *loss_out, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on one batch. */
+int nbt_surrogate_train_step(nbt_surrogate net, const void *crops, const void *feats, const float *targets, int32_t n,
+                             float lr, float *loss_out, void *stream);
+
 /* Size of the fixed device scratch array behind nbt_views_ig_noalloc. */
 #define NBT_NOALLOC_SCRATCH_BYTES (4 << 20)
 

@@ -69,6 +69,15 @@ SIGNATURES = {
     "nbt_plan_destroy": (C.c_int, [_vp]),
     "nbt_tc_gemm": (C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp]),
     "nbt_tc_error": (C.c_int, [P(C.c_int32)]),
+    "nbt_surrogate_param_count": (C.c_int, [P(C.c_int64)]),
+    "nbt_surrogate_create": (C.c_int, [_i32, P(_vp)]),
+    "nbt_surrogate_destroy": (C.c_int, [_vp]),
+    "nbt_surrogate_set_params": (C.c_int, [_vp, _vp, _i64]),
+    "nbt_surrogate_get_params": (C.c_int, [_vp, _vp, _i64]),
+    "nbt_surrogate_crops": (C.c_int, [_vp, _vp, _i64, P(Camera), P(IgParams), _vp, _vp, _vp]),
+    "nbt_surrogate_forward": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
+    "nbt_surrogate_backward": (C.c_int, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "nbt_surrogate_train_step": (C.c_int, [_vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp]),
     "nbt_map_get_tuning": (C.c_int, [_vp, P(Tuning)]),
 }
 

@@ -1,14 +1,27 @@
-// nbt_surrogate.cu -- tensor-core kernels of the learned IG surrogate.
+// nbt_surrogate.cu -- the learned IG surrogate: crops, network, training.
 //
-// This file holds the operand loaders and epilogues that turn the tcgen05
-// GEMM of nbt_tc.cuh into the surrogate's layers, and their C-ABI entry
-// points.  The paper has no learned component; the surrogate prunes
-// candidate perspectives before exact raycasting (the exact IG of Section
-// III re-scores the survivors).
+// The paper has no learned component.  The surrogate predicts the mean ray
+// IG of a perspective (Section III's g_P, scaled) from a view-aligned
+// occupancy crop and the pose, so that only the most promising candidates
+// are raycast exactly.
+//
+// Network (all layers on the tcgen05 GEMM of nbt_tc.cuh, BF16 operands and
+// activations, FP32 accumulation and FP32 master weights):
+//   crop 32^3 x 8 (one-hot unknown / free / occupied in channels 0..2)
+//   conv 3^3 8->16 s1, conv 16->32 s2, conv 32->64 s2, conv 64->64 s2 (ReLU)
+//   flatten 4^3 x 64 = 4096 | 8 pose features -> fc 4104->128 (ReLU) -> fc 128->1
+// Convolutions are implicit GEMMs: a loader gathers the im2col tile of the
+// stage straight from the NDHWC activations into shared memory (nothing is
+// materialised in HBM).  Backward: input gradients are GEMMs over a
+// transposed-convolution loader (ReLU mask fused in the epilogue); weight
+// gradients are split-K GEMMs whose loaders transpose 16-byte activation
+// vectors into K-major stage rows, reduced over the splits in a fixed order.
 
 #include <cuda_bf16.h>
+#include <math.h>
 
 #include <algorithm>
+#include <new>
 
 #include "nbt_internal.cuh"
 #include "nbt_tc.cuh"
@@ -18,29 +31,484 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-// Row-major K-major BF16 matrix [rows, K] with row stride ld elements
-// (ld % 8 == 0, base 16-byte aligned, K % 8 == 0).
+constexpr int kCrop = 32;
+constexpr int kC0 = 8;
+constexpr int kFeat = 8;
+constexpr int kFlat = 4096;
+constexpr int kFcIn = kFlat + kFeat;  // 4104
+constexpr int kHid = 128;
+constexpr int kLayers = 4;
+struct LayerDims {
+  int cin, cout, stride, din, dout;
+};
+constexpr LayerDims kL[kLayers] = {{8, 16, 1, 32, 32}, {16, 32, 2, 32, 16}, {32, 64, 2, 16, 8}, {64, 64, 2, 8, 4}};
+// (the device-side weight copy kernel repeats these channel counts as literals)
+constexpr int kSplitBytes = 64 << 20;  // weight-gradient split-K partials
+
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+
+// Parameter vector (FP32): per conv layer W [cout][27 cin], b [cout]; then
+// F1 [128][4104], g1 [128], f2 [128], g2 [1].
+struct ParamLayout {
+  int64_t w[kLayers], b[kLayers], f1, g1, f2, g2, total;
+};
+constexpr ParamLayout make_layout() {
+  ParamLayout p{};
+  int64_t o = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    p.w[l] = o;
+    o += (int64_t)kL[l].cout * 27 * kL[l].cin;
+    p.b[l] = o;
+    o += kL[l].cout;
+  }
+  p.f1 = o;
+  o += (int64_t)kHid * kFcIn;
+  p.g1 = o;
+  o += kHid;
+  p.f2 = o;
+  o += kHid;
+  p.g2 = o;
+  o += 1;
+  p.total = o;
+  return p;
+}
+constexpr ParamLayout kP = make_layout();
+// scalar copies for device code (arrays of a host constexpr are not visible there)
+constexpr int64_t kW0 = kP.w[0], kW1 = kP.w[1], kW2 = kP.w[2], kW3 = kP.w[3];
+
+__device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
+
+// ---------------------------------------------------------------------------
+// Loaders
+// ---------------------------------------------------------------------------
+
+// Row-major K-major BF16 matrix [rows, K], row stride ld elements.
 struct MatLoader {
   const bf16 *p;
   int rows, K, ld;
   __device__ __forceinline__ uint4 chunk(int r, int kc) const {
     const int k = kc * 8;
-    if (r >= rows || k >= K) return make_uint4(0u, 0u, 0u, 0u);
+    if (r >= rows || k >= K) return zero4();
     return __ldg((const uint4 *)(p + (size_t)r * ld + k));
+  }
+  template <int ROWS>
+  __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
+    tc::fill_chunks<ROWS>(*this, s, row0, kc0, tid);
   }
 };
 
-// FP32 row-major store of C[m, n] for n < N.
-struct StoreF32 {
-  float *c;
-  int N, ldc;
-  __device__ __forceinline__ void row(int m, int n0, const float v[16]) const {
-    float *dst = c + (size_t)m * ldc + n0;
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if (n0 + i < N) dst[i] = v[i];
+// Implicit im2col of a 3^3 convolution (padding 1): row m = output voxel
+// (b, oz, oy, ox), K index = tap * cin + ci with tap = (dz*3 + dy)*3 + dx.
+struct ConvFwdLoader {
+  const bf16 *x;
+  int M, D, stride, sh_do, sh_cg, cin;
+  __device__ __forceinline__ uint4 chunk(int m, int kc) const {
+    if (m >= M) return zero4();
+    const int tap = kc >> sh_cg;
+    if (tap >= 27) return zero4();
+    const int cg = kc & ((1 << sh_cg) - 1);
+    const int dmask = (1 << sh_do) - 1;
+    const int ox = m & dmask, oy = (m >> sh_do) & dmask, oz = (m >> (2 * sh_do)) & dmask, b = m >> (3 * sh_do);
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+    const int iz = oz * stride + dz - 1, iy = oy * stride + dy - 1, ix = ox * stride + dx - 1;
+    if ((unsigned)iz >= (unsigned)D || (unsigned)iy >= (unsigned)D || (unsigned)ix >= (unsigned)D) return zero4();
+    return __ldg((const uint4 *)(x + ((((size_t)b * D + iz) * D + iy) * D + ix) * cin + cg * 8));
+  }
+  template <int ROWS>
+  __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
+    tc::fill_chunks<ROWS>(*this, s, row0, kc0, tid);
   }
 };
+
+// Implicit im2col of the transposed convolution giving the input gradient:
+// row m = input voxel i, K index = tap * cout + co; the output voxel that
+// tap d reads i from is o = (i + 1 - d) / s when that is integral and in
+// range (forward: i = o*s + d - 1).
+struct ConvBwdDataLoader {
+  const bf16 *dy;
+  int M, Di, Do, sh_s, sh_di, sh_cg, cout;
+  __device__ __forceinline__ uint4 chunk(int m, int kc) const {
+    if (m >= M) return zero4();
+    const int tap = kc >> sh_cg;
+    if (tap >= 27) return zero4();
+    const int cg = kc & ((1 << sh_cg) - 1);
+    const int dmask = (1 << sh_di) - 1;
+    const int ix = m & dmask, iy = (m >> sh_di) & dmask, iz = (m >> (2 * sh_di)) & dmask, b = m >> (3 * sh_di);
+    const int dz = tap / 9, dy_ = (tap / 3) % 3, dx = tap % 3;
+    const int tz = iz + 1 - dz, ty = iy + 1 - dy_, tx = ix + 1 - dx;
+    const int smask = (1 << sh_s) - 1;
+    if (tz < 0 || ty < 0 || tx < 0 || (tz & smask) || (ty & smask) || (tx & smask)) return zero4();
+    const int oz = tz >> sh_s, oy = ty >> sh_s, ox = tx >> sh_s;
+    if (oz >= Do || oy >= Do || ox >= Do) return zero4();
+    return __ldg((const uint4 *)(dy + ((((size_t)b * Do + oz) * Do + oy) * Do + ox) * cout + cg * 8));
+  }
+  template <int ROWS>
+  __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
+    tc::fill_chunks<ROWS>(*this, s, row0, kc0, tid);
+  }
+};
+
+// Weight gradient, operand A: rows = (tap, ci) (27 cin of them), K = output
+// voxels m.  Each thread loads the 8 channels of one input voxel (16 bytes)
+// and writes them transposed into 8 stage rows at K position m.
+struct WgradColLoader {
+  const bf16 *x;
+  int Mout, D, stride, sh_do, cin;
+  template <int ROWS>
+  __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
+    const int groups = ROWS / 8;  // 8-channel groups in the tile: (tap_local, cg)
+    const int cgn = cin / 8;
+    const int dmask = (1 << sh_do) - 1;
+    for (int it = tid; it < 64 * groups; it += tc::kThreads) {
+      const int mm = it & 63, g = it >> 6;
+      const int r = g * 8;  // first stage row of this group
+      const int row = row0 + r;
+      const int tap = row / cin, cg = (row % cin) >> 3;
+      const int m = kc0 * 8 + mm;
+      uint4 v = zero4();
+      if (tap < 27 && m < Mout) {
+        const int ox = m & dmask, oy = (m >> sh_do) & dmask, oz = (m >> (2 * sh_do)) & dmask, b = m >> (3 * sh_do);
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        const int iz = oz * stride + dz - 1, iy = oy * stride + dy - 1, ix = ox * stride + dx - 1;
+        if ((unsigned)iz < (unsigned)D && (unsigned)iy < (unsigned)D && (unsigned)ix < (unsigned)D)
+          v = __ldg((const uint4 *)(x + ((((size_t)b * D + iz) * D + iy) * D + ix) * cin + cg * 8));
+      }
+      (void)cgn;
+      const uint16_t *e = (const uint16_t *)&v;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        *(uint16_t *)(s + tc::stage_off(r + k, mm >> 3, ROWS) + (mm & 7) * 2) = e[k];
+    }
+  }
+};
+
+// Weight gradient, operand B: rows = output channels co, K = output voxels
+// m, from the NDHWC output gradient (16-byte vectors transposed into rows).
+struct WgradDyLoader {
+  const bf16 *dy;
+  int Mout, cout;
+  template <int ROWS>
+  __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
+    const int groups = ROWS / 8;
+    for (int it = tid; it < 64 * groups; it += tc::kThreads) {
+      const int mm = it & 63, g = it >> 6;
+      const int r = g * 8;
+      const int co = row0 + r;
+      const int m = kc0 * 8 + mm;
+      uint4 v = zero4();
+      if (co < cout && m < Mout) v = __ldg((const uint4 *)(dy + (size_t)m * cout + co));
+      const uint16_t *e = (const uint16_t *)&v;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        *(uint16_t *)(s + tc::stage_off(r + k, mm >> 3, ROWS) + (mm & 7) * 2) = e[k];
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Epilogues
+// ---------------------------------------------------------------------------
+
+// out[m * ld + n] = bf16(max(v + bias[n], 0)) for n < N.
+struct EpiBiasRelu {
+  bf16 *out;
+  const float *bias;
+  int N, ld;
+  __device__ __forceinline__ void row(int m, int n, const float v[16], int) const {
+    bf16 *d = out + (size_t)m * ld + n;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (n + i < N) d[i] = __float2bfloat16_rn(fmaxf(v[i] + bias[n + i], 0.0f));
+  }
+};
+
+// Last conv layer: its 64 output voxels of sample b = m / 64 go to the
+// first 4096 columns of row b of the fully connected input X.
+struct EpiConvToFlat {
+  bf16 *x;
+  const float *bias;
+  __device__ __forceinline__ void row(int m, int n, const float v[16], int) const {
+    bf16 *d = x + (size_t)(m >> 6) * kFcIn + (m & 63) * 64 + n;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) d[i] = __float2bfloat16_rn(fmaxf(v[i] + bias[n + i], 0.0f));
+  }
+};
+
+// FP32 store (split-K partials use plane z of size planes).
+struct EpiF32 {
+  float *out;
+  int N, ld;
+  int64_t plane;
+  __device__ __forceinline__ void row(int m, int n, const float v[16], int z) const {
+    float *d = out + z * plane + (size_t)m * ld + n;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (n + i < N) d[i] = v[i];
+  }
+};
+
+// Input gradient with the ReLU mask of the layer input fused:
+// out[m * ld + n] = bf16(v * [act[m * lda + n] > 0]) for n < N.
+struct EpiMaskRelu {
+  bf16 *out;
+  const bf16 *act;
+  int N, ld, lda;
+  __device__ __forceinline__ void row(int m, int n, const float v[16], int) const {
+    bf16 *d = out + (size_t)m * ld + n;
+    const bf16 *a = act + (size_t)m * lda + n;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (n + i < N) d[i] = __float2bfloat16_rn(__bfloat162float(a[i]) > 0.0f ? v[i] : 0.0f);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Small kernels
+// ---------------------------------------------------------------------------
+
+// Frustum crop (same FP32 operation order as the reference): sample (i, j,
+// k) on the ray through pixel centre (i, j) of a 32 x 32 image of the field
+// of view, at depth fraction (k + 1/2) / 32; one-hot class of the voxel that
+// holds it, zero outside the map.  One thread per sample.
+struct CropConst {
+  float x0, xs, y0, ys, zc, inv_s, ox, oy, oz, ext_x, ext_y, ext_z;
+  float occ_thr, free_thr;
+};
+
+template <int KIND>
+__global__ void crop_kernel(DevMap m, CropConst cc, const float *__restrict__ poses, int64_t n, bf16 *__restrict__ crops,
+                            bf16 *__restrict__ feats) {
+  const int64_t total = n * (int64_t)kCrop * kCrop * kCrop;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = t >> 15;
+    const int cell = (int)(t & 32767);
+    const int i = cell & 31, j = (cell >> 5) & 31, k = cell >> 10;
+    float pz[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) pz[q] = __ldg(poses + v * 7 + q);
+    const float qw = pz[3], qx = pz[4], qy = pz[5], qz = pz[6];
+    const float xx = fmul(qx, qx), yy = fmul(qy, qy), zz = fmul(qz, qz);
+    const float xy = fmul(qx, qy), xz = fmul(qx, qz), yz = fmul(qy, qz);
+    const float wx = fmul(qw, qx), wy = fmul(qw, qy), wz = fmul(qw, qz);
+    float r[9];
+    r[0] = fsub(1.0f, fmul(2.0f, fadd(yy, zz)));
+    r[1] = fmul(2.0f, fsub(xy, wz));
+    r[2] = fmul(2.0f, fadd(xz, wy));
+    r[3] = fmul(2.0f, fadd(xy, wz));
+    r[4] = fsub(1.0f, fmul(2.0f, fadd(xx, zz)));
+    r[5] = fmul(2.0f, fsub(yz, wx));
+    r[6] = fmul(2.0f, fsub(xz, wy));
+    r[7] = fmul(2.0f, fadd(yz, wx));
+    r[8] = fsub(1.0f, fmul(2.0f, fadd(xx, yy)));
+    const float fr = __fdiv_rn((float)k + 0.5f, 32.0f);
+    const float cx = fadd(cc.x0, fmul((float)i, cc.xs));
+    const float cy = fadd(cc.y0, fmul((float)j, cc.ys));
+    const float p[3] = {fmul(cx, fr), fmul(cy, fr), fmul(cc.zc, fr)};
+    const float org[3] = {cc.ox, cc.oy, cc.oz};
+    const int dims[3] = {m.nx, m.ny, m.nz};
+    int idx[3];
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float w = fadd(fadd(fmul(r[3 * a], p[0]), fmul(r[3 * a + 1], p[1])), fmul(r[3 * a + 2], p[2]));
+      const float o = fmul(fsub(pz[a], org[a]), cc.inv_s);
+      const float q = fadd(o, fmul(w, cc.inv_s));
+      const float fl = floorf(q);
+      inside = inside && fl >= 0.0f && fl < (float)dims[a];
+      idx[a] = inside ? (int)fl : 0;
+    }
+    uint32_t cls = 3u;  // 3 = outside: no channel set
+    if (inside) {
+      const int32_t off = m.tab[idx[0]] + m.tab[m.nx + idx[1]] + m.tab[m.nx + m.ny + idx[2]];
+      if (KIND == PAYLOAD_GAIN_F32) {
+        const float pv = __ldg((const float *)m.payload + off);
+        cls = pv > cc.occ_thr ? 2u : (pv < cc.free_thr ? 1u : 0u);
+      } else if (KIND == PAYLOAD_U8) {
+        const uint32_t st = __ldg((const uint8_t *)m.payload + off);
+        cls = st >= 2u ? 2u : st;
+      } else {
+        const uint32_t byte = __ldg((const uint8_t *)m.payload + (off >> 2));
+        const uint32_t st = (byte >> ((off & 3) << 1)) & 3u;
+        cls = st >= 2u ? 2u : st;
+      }
+    }
+    // BF16 1.0 (0x3F80) in channel cls of the first four, nothing for outside
+    const unsigned long long bits = cls < 3u ? (0x3F80ull << (16u * cls)) : 0ull;
+    uint4 onehot;
+    onehot.x = (uint32_t)bits;
+    onehot.y = (uint32_t)(bits >> 32);
+    onehot.z = 0u;
+    onehot.w = 0u;
+    *(uint4 *)(crops + (size_t)t * kC0) = onehot;
+    if (cell == 0) {
+      const float ext[3] = {cc.ext_x, cc.ext_y, cc.ext_z};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) feats[v * kFeat + a] = __float2bfloat16_rn(__fdiv_rn(fsub(pz[a], org[a]), ext[a]));
+#pragma unroll
+      for (int a = 0; a < 4; ++a) feats[v * kFeat + 3 + a] = __float2bfloat16_rn(pz[3 + a]);
+      feats[v * kFeat + 7] = __float2bfloat16_rn(1.0f);
+    }
+  }
+}
+
+// X[:, 4096:4104] = feats.
+__global__ void put_feats_kernel(const bf16 *__restrict__ feats, bf16 *__restrict__ x, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n * kFeat) x[(size_t)(t / kFeat) * kFcIn + kFlat + t % kFeat] = feats[t];
+}
+
+// y[b] = h1[b] . f2 + g2 (one warp per sample, fixed shuffle tree).
+__global__ void fc2_forward_kernel(const bf16 *__restrict__ h1, const float *__restrict__ params, int n,
+                                   float *__restrict__ y) {
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (b >= n) return;
+  const float *f2 = params + kP.f2;
+  float acc = 0.0f;
+  for (int j = lane; j < kHid; j += 32) acc += __bfloat162float(h1[(size_t)b * kHid + j]) * f2[j];
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  if (lane == 0) y[b] = acc + params[kP.g2];
+}
+
+// Loss head (one block of 256 threads): loss = mean (y - t)^2, dy = 2 (y - t) / n;
+// grads of f2 and g2; dh1 = dy f2 [h1 > 0] (BF16, and transposed to [128][ldn]).
+__global__ void head_backward_kernel(const float *__restrict__ y, const float *__restrict__ t, const bf16 *__restrict__ h1,
+                                     const float *__restrict__ params, int n, int ldn, float *__restrict__ grads,
+                                     float *__restrict__ loss, bf16 *__restrict__ dh1, bf16 *__restrict__ dh1t) {
+  __shared__ float red[256];
+  __shared__ float s_dy[1024];
+  const int tid = threadIdx.x;
+  float l = 0.0f, gb = 0.0f;
+  for (int b = tid; b < n; b += 256) {
+    const float e = y[b] - t[b];
+    l += e * e;
+    const float d = 2.0f * e / (float)n;
+    gb += d;
+    if (b < 1024) s_dy[b] = d;
+  }
+  red[tid] = l;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (tid < s) red[tid] += red[tid + s];
+    __syncthreads();
+  }
+  if (tid == 0) *loss = red[0] / (float)n;
+  __syncthreads();
+  red[tid] = gb;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (tid < s) red[tid] += red[tid + s];
+    __syncthreads();
+  }
+  if (tid == 0) grads[kP.g2] = red[0];
+  __syncthreads();
+  const float *f2 = params + kP.f2;
+  for (int j = tid; j < kHid; j += 256) {
+    float acc = 0.0f;
+    for (int b = 0; b < n; ++b) acc += s_dy[b] * __bfloat162float(h1[(size_t)b * kHid + j]);
+    grads[kP.f2 + j] = acc;
+  }
+  for (int e = tid; e < kHid * ldn; e += 256) {
+    const int j = e / ldn, b = e % ldn;
+    float d = 0.0f;
+    if (b < n && __bfloat162float(h1[(size_t)b * kHid + j]) > 0.0f) d = s_dy[b] * f2[j];
+    const bf16 v = __float2bfloat16_rn(d);
+    dh1t[(size_t)j * ldn + b] = v;
+    if (b < n) dh1[(size_t)b * kHid + j] = v;
+  }
+}
+
+// out[c][r] = in[r][c] for r < rows (rows padded with zeros up to ldo), c < cols.
+__global__ void transpose_kernel(const bf16 *__restrict__ in, int rows, int cols, int ldi, bf16 *__restrict__ out,
+                                 int ldo) {
+  __shared__ bf16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    tile[k][threadIdx.x] = (r < rows && c < cols) ? in[(size_t)r * ldi + c] : __float2bfloat16_rn(0.0f);
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (c < cols && r < ldo) out[(size_t)c * ldo + r] = tile[threadIdx.x][k];
+  }
+}
+
+// Column sums of a BF16 matrix [rows][cols] (bias gradients), one warp per
+// column, fixed order.
+__global__ void colsum_kernel(const bf16 *__restrict__ a, int64_t rows, int cols, float *__restrict__ out) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (c >= cols) return;
+  float acc = 0.0f;
+  for (int64_t r = lane; r < rows; r += 32) acc += __bfloat162float(a[r * cols + c]);
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  if (lane == 0) out[c] = acc;
+}
+
+// Split-K weight gradients: dW[co][k] = sum_z part[z][k][co], fixed z order.
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, int krows, int cout,
+                                    float *__restrict__ dw) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= krows * cout) return;
+  const int k = e / cout, co = e % cout;
+  float acc = 0.0f;
+  for (int z = 0; z < splits; ++z) acc += part[(size_t)z * krows * cout + (size_t)k * cout + co];
+  dw[(size_t)co * krows + k] = acc;
+}
+
+// Adam on the FP32 master parameters.
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// BF16 operand copies of the weights: W_l [cout][27 cin] (forward B), WT_l
+// [cin][27 cout] (input-gradient B), F1 [128][4104], F1T [4104][128].
+__global__ void sync_weights_kernel(const float *__restrict__ p, bf16 *__restrict__ wb, bf16 *__restrict__ wtb,
+                                    bf16 *__restrict__ f1b, bf16 *__restrict__ f1tb) {
+  const int64_t total = kP.f1 + (int64_t)kHid * kFcIn;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < kP.f1) {
+      // layer of this entry; every table access below uses a literal index
+      const int l = e < kW1 ? 0 : (e < kW2 ? 1 : (e < kW3 ? 2 : 3));
+      int cin, cout;
+      int64_t wbase;
+      switch (l) {
+        case 0: cin = 8; cout = 16; wbase = kW0; break;
+        case 1: cin = 16; cout = 32; wbase = kW1; break;
+        case 2: cin = 32; cout = 64; wbase = kW2; break;
+        default: cin = 64; cout = 64; wbase = kW3; break;
+      }
+      const int64_t o = e - wbase;
+      const int kk = 27 * cin;
+      if (o >= (int64_t)cout * kk) continue;  // bias entries
+      const int co = (int)(o / kk), k = (int)(o % kk);
+      const int tap = k / cin, ci = k % cin;
+      const bf16 v = __float2bfloat16_rn(p[e]);
+      wb[wbase + o] = v;
+      wtb[wbase + (int64_t)ci * 27 * cout + tap * cout + co] = v;
+    } else {
+      const int64_t o = e - kP.f1;
+      const int j = (int)(o / kFcIn), c = (int)(o % kFcIn);
+      const bf16 v = __float2bfloat16_rn(p[e]);
+      f1b[o] = v;
+      f1tb[(int64_t)c * kHid + j] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
 
 int *g_err[64] = {nullptr};
 
@@ -58,17 +526,35 @@ int dev_err_word(int **out) {
 }
 
 template <int BN, class LA, class LB, class EP>
-int launch_gemm(const LA &la, const LB &lb, const EP &ep, int M, int K, cudaStream_t stream) {
+int launch_gemm(const LA &la, const LB &lb, const EP &ep, int M, int N, int K, int splits, cudaStream_t stream) {
   int *err = nullptr;
   int rc = dev_err_word(&err);
   if (rc != NBT_OK) return rc;
   const size_t smem = tc::gemm_smem_bytes(BN);
   auto kern = tc::gemm_kernel<BN, LA, LB, EP>;
   NBT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const unsigned grid = (unsigned)((M + tc::kBM - 1) / tc::kBM);
-  kern<<<grid, tc::kThreads, smem, stream>>>(la, lb, ep, M, K, err);
+  const int kt_all = (K + tc::kBK - 1) / tc::kBK;
+  splits = std::max(1, std::min(splits, kt_all));
+  const int kt_split = (kt_all + splits - 1) / splits;
+  splits = (kt_all + kt_split - 1) / kt_split;
+  const dim3 grid((unsigned)((M + tc::kBM - 1) / tc::kBM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
+  kern<<<grid, tc::kThreads, smem, stream>>>(la, lb, ep, M, K, kt_split, err);
   NBT_CUDA_TRY(cudaGetLastError());
   return NBT_OK;
+}
+
+// BN for N columns (smallest supported tile >= N, at most 256 per tile).
+template <class LA, class LB, class EP>
+int gemm(const LA &la, const LB &lb, const EP &ep, int M, int N, int K, int splits, cudaStream_t s) {
+  if (N <= 16) return launch_gemm<16>(la, lb, ep, M, N, K, splits, s);
+  if (N <= 32) return launch_gemm<32>(la, lb, ep, M, N, K, splits, s);
+  if (N <= 64) return launch_gemm<64>(la, lb, ep, M, N, K, splits, s);
+  if (N <= 128) return launch_gemm<128>(la, lb, ep, M, N, K, splits, s);
+  return launch_gemm<256>(la, lb, ep, M, N, K, splits, s);
+}
+
+int grid_1d(int64_t n, int threads = 256) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, (int64_t)sm_count() * 32));
 }
 
 }  // namespace
@@ -76,26 +562,155 @@ int launch_gemm(const LA &la, const LB &lb, const EP &ep, int M, int K, cudaStre
 
 using namespace nbt;
 
+struct nbt_surrogate_s {
+  int device = 0;
+  int max_batch = 0, ldn = 0;  // ldn: batch padded to a multiple of 8
+  float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  bf16 *wb = nullptr, *wtb = nullptr, *f1b = nullptr, *f1tb = nullptr;
+  bf16 *act[kLayers] = {nullptr};   // outputs of conv layers 0..2 (layer 3 writes into x)
+  bf16 *dact[kLayers] = {nullptr};  // gradients w.r.t. the outputs of conv layers 0..3
+  bf16 *x = nullptr, *xt = nullptr, *h1 = nullptr, *dh1 = nullptr, *dh1t = nullptr;
+  float *y = nullptr, *loss = nullptr, *part = nullptr;
+  int64_t step = 0;
+};
+
+namespace {
+
+void free_net(nbt_surrogate n) {
+  void *ptrs[] = {n->params, n->grads, n->adam_m, n->adam_v, n->wb, n->wtb, n->f1b, n->f1tb, n->x, n->xt, n->h1,
+                  n->dh1, n->dh1t, n->y, n->loss, n->part};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (int l = 0; l < kLayers; ++l) {
+    if (n->act[l]) cudaFree(n->act[l]);
+    if (n->dact[l]) cudaFree(n->dact[l]);
+  }
+  (void)cudaGetLastError();
+  delete n;
+}
+
+int check_net(nbt_surrogate n) {
+  if (!n) return NBT_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NBT_ECUDA;
+  return dev == n->device ? NBT_OK : NBT_EINVAL;
+}
+
+// Forward pass of n <= max_batch samples: crops [n, 32^3, 8], feats [n, 8].
+int forward_batch(nbt_surrogate net, const bf16 *crops, const bf16 *feats, int n, float *pred, cudaStream_t s) {
+  const bf16 *in = crops;
+  for (int l = 0; l < kLayers; ++l) {
+    const LayerDims &L = kL[l];
+    const int M = n * L.dout * L.dout * L.dout;
+    const ConvFwdLoader la{in, M, L.din, L.stride, ilog2(L.dout), ilog2(L.cin / 8), L.cin};
+    const MatLoader lb{net->wb + kP.w[l], L.cout, 27 * L.cin, 27 * L.cin};
+    int rc;
+    if (l + 1 < kLayers) {
+      const EpiBiasRelu ep{net->act[l], net->params + kP.b[l], L.cout, L.cout};
+      rc = gemm(la, lb, ep, M, L.cout, 27 * L.cin, 1, s);
+      in = net->act[l];
+    } else {
+      const EpiConvToFlat ep{net->x, net->params + kP.b[l]};
+      rc = gemm(la, lb, ep, M, L.cout, 27 * L.cin, 1, s);
+    }
+    if (rc != NBT_OK) return rc;
+  }
+  put_feats_kernel<<<(n * kFeat + 255) / 256, 256, 0, s>>>(feats, net->x, n);
+  NBT_CUDA_TRY(cudaGetLastError());
+  const MatLoader la{net->x, n, kFcIn, kFcIn};
+  const MatLoader lb{net->f1b, kHid, kFcIn, kFcIn};
+  const EpiBiasRelu ep{net->h1, net->params + kP.g1, kHid, kHid};
+  int rc = gemm(la, lb, ep, n, kHid, kFcIn, 1, s);
+  if (rc != NBT_OK) return rc;
+  fc2_forward_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(net->h1, net->params, n, pred ? pred : net->y);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+int sync_weights(nbt_surrogate net, cudaStream_t s) {
+  sync_weights_kernel<<<grid_1d(kP.f1 + (int64_t)kHid * kFcIn), 256, 0, s>>>(net->params, net->wb, net->wtb, net->f1b,
+                                                                             net->f1tb);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+// Forward + backward of one batch; gradients into net->grads, loss into net->loss.
+int backward_batch(nbt_surrogate net, const bf16 *crops, const bf16 *feats, const float *targets, int n,
+                   cudaStream_t s) {
+  int rc = forward_batch(net, crops, feats, n, net->y, s);
+  if (rc != NBT_OK) return rc;
+  const int ldn = net->ldn;
+  head_backward_kernel<<<1, 256, 0, s>>>(net->y, targets, net->h1, net->params, n, ldn, net->grads, net->loss,
+                                         net->dh1, net->dh1t);
+  NBT_CUDA_TRY(cudaGetLastError());
+  // fc1: dW1 = dh1^T X, db1 = colsum(dh1), dX = dh1 F1 (ReLU mask of the flattened conv output)
+  {
+    const dim3 tb(32, 8), tg((kFcIn + 31) / 32, (ldn + 31) / 32);
+    transpose_kernel<<<tg, tb, 0, s>>>(net->x, n, kFcIn, kFcIn, net->xt, ldn);
+    NBT_CUDA_TRY(cudaGetLastError());
+    const MatLoader la{net->dh1t, kHid, n, ldn};
+    const MatLoader lb{net->xt, kFcIn, n, ldn};
+    const EpiF32 ep{net->grads + kP.f1, kFcIn, kFcIn, 0};
+    rc = gemm(la, lb, ep, kHid, kFcIn, n, 1, s);
+    if (rc != NBT_OK) return rc;
+    colsum_kernel<<<(kHid * 32 + 255) / 256, 256, 0, s>>>(net->dh1, n, kHid, net->grads + kP.g1);
+    NBT_CUDA_TRY(cudaGetLastError());
+    const MatLoader la2{net->dh1, n, kHid, kHid};
+    const MatLoader lb2{net->f1tb, kFlat, kHid, kHid};
+    const EpiMaskRelu ep2{net->dact[kLayers - 1], net->x, kFlat, kFlat, kFcIn};
+    rc = gemm(la2, lb2, ep2, n, kFlat, kHid, 1, s);
+    if (rc != NBT_OK) return rc;
+  }
+  for (int l = kLayers - 1; l >= 0; --l) {
+    const LayerDims &L = kL[l];
+    const int Mout = n * L.dout * L.dout * L.dout;
+    const bf16 *in = l == 0 ? crops : net->act[l - 1];
+    const bf16 *dy = net->dact[l];
+    // bias gradient
+    colsum_kernel<<<(L.cout * 32 + 255) / 256, 256, 0, s>>>(dy, Mout, L.cout, net->grads + kP.b[l]);
+    NBT_CUDA_TRY(cudaGetLastError());
+    // weight gradient: split-K over output voxels, then a fixed-order reduction
+    const int krows = 27 * L.cin;
+    const int mtiles = (krows + tc::kBM - 1) / tc::kBM;
+    const int kt_all = (Mout + tc::kBK - 1) / tc::kBK;
+    int splits = std::max(1, std::min(kt_all, 4 * sm_count() / mtiles));
+    splits = std::min<int>(splits, (int)(kSplitBytes / ((int64_t)krows * L.cout * 4)));
+    const int kt_split = (kt_all + splits - 1) / splits;
+    splits = (kt_all + kt_split - 1) / kt_split;
+    const WgradColLoader la{in, Mout, L.din, L.stride, ilog2(L.dout), L.cin};
+    const WgradDyLoader lb{dy, Mout, L.cout};
+    const EpiF32 ep{net->part, L.cout, L.cout, (int64_t)krows * L.cout};
+    rc = gemm(la, lb, ep, krows, L.cout, Mout, splits, s);
+    if (rc != NBT_OK) return rc;
+    wgrad_reduce_kernel<<<(krows * L.cout + 255) / 256, 256, 0, s>>>(net->part, splits, krows, L.cout,
+                                                                     net->grads + kP.w[l]);
+    NBT_CUDA_TRY(cudaGetLastError());
+    // input gradient (not needed for the crop)
+    if (l > 0) {
+      const int Min = n * L.din * L.din * L.din;
+      const ConvBwdDataLoader la2{dy, Min, L.din, L.dout, ilog2(L.stride), ilog2(L.din), ilog2(L.cout / 8), L.cout};
+      const MatLoader lb2{net->wtb + kP.w[l], L.cin, 27 * L.cout, 27 * L.cout};
+      const EpiMaskRelu ep2{net->dact[l - 1], net->act[l - 1], L.cin, L.cin, L.cin};
+      rc = gemm(la2, lb2, ep2, Min, L.cin, 27 * L.cout, 1, s);
+      if (rc != NBT_OK) return rc;
+    }
+  }
+  return NBT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
-// Test entry point: C[M, N] (FP32, row stride N) = A[M, K] * B[N, K]^T with
-// BF16 row-major A and B (row strides K).  N in [1, 256]; K % 8 == 0.
 int nbt_tc_gemm(const void *a, const void *b, float *c, int32_t m, int32_t n, int32_t k, void *stream) {
   if (!a || !b || !c || m < 1 || n < 1 || n > 256 || k < 8 || (k % 8) != 0) return NBT_EINVAL;
   if (((uintptr_t)a & 15u) || ((uintptr_t)b & 15u)) return NBT_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
   const MatLoader la{(const bf16 *)a, m, k, k};
   const MatLoader lb{(const bf16 *)b, n, k, k};
-  const StoreF32 ep{c, n, n};
-  if (n <= 16) return launch_gemm<16>(la, lb, ep, m, k, s);
-  if (n <= 32) return launch_gemm<32>(la, lb, ep, m, k, s);
-  if (n <= 64) return launch_gemm<64>(la, lb, ep, m, k, s);
-  if (n <= 128) return launch_gemm<128>(la, lb, ep, m, k, s);
-  return launch_gemm<256>(la, lb, ep, m, k, s);
+  const EpiF32 ep{c, n, n, 0};
+  return gemm(la, lb, ep, m, n, k, 1, (cudaStream_t)stream);
 }
 
-// Device error word of the tensor-core kernels on the current device: 1
-// after a bounded wait gave up.  Reading clears it.
 int nbt_tc_error(int32_t *flag) {
   if (!flag) return NBT_EINVAL;
   int *err = nullptr;
@@ -106,6 +721,182 @@ int nbt_tc_error(int32_t *flag) {
   if (v) NBT_CUDA_TRY(cudaMemset(err, 0, sizeof(int)));
   *flag = v;
   return NBT_OK;
+}
+
+int nbt_surrogate_param_count(int64_t *n) {
+  if (!n) return NBT_EINVAL;
+  *n = kP.total;
+  return NBT_OK;
+}
+
+int nbt_surrogate_create(int32_t max_batch, nbt_surrogate *out) {
+  if (!out || max_batch < 1 || max_batch > 4096) return NBT_EINVAL;
+  *out = nullptr;
+  nbt_surrogate n = new (std::nothrow) nbt_surrogate_s();
+  if (!n) return NBT_ENOMEM;
+  if (cudaGetDevice(&n->device) != cudaSuccess) {
+    delete n;
+    return NBT_ECUDA;
+  }
+  n->max_batch = max_batch;
+  n->ldn = (max_batch + 7) / 8 * 8;
+  const int64_t B = n->ldn;
+  bool ok = true;
+  auto alloc = [&](void **p, int64_t bytes) {
+    if (ok && cudaMalloc(p, (size_t)bytes) != cudaSuccess) ok = false;
+    if (ok && cudaMemset(*p, 0, (size_t)bytes) != cudaSuccess) ok = false;
+  };
+  alloc((void **)&n->params, kP.total * 4);
+  alloc((void **)&n->grads, kP.total * 4);
+  alloc((void **)&n->adam_m, kP.total * 4);
+  alloc((void **)&n->adam_v, kP.total * 4);
+  alloc((void **)&n->wb, kP.f1 * 2);
+  alloc((void **)&n->wtb, kP.f1 * 2);
+  alloc((void **)&n->f1b, (int64_t)kHid * kFcIn * 2);
+  alloc((void **)&n->f1tb, (int64_t)kHid * kFcIn * 2);
+  for (int l = 0; l < kLayers; ++l) {
+    const int64_t vox = B * kL[l].dout * kL[l].dout * kL[l].dout * kL[l].cout;
+    if (l + 1 < kLayers) alloc((void **)&n->act[l], vox * 2);
+    alloc((void **)&n->dact[l], vox * 2);
+  }
+  alloc((void **)&n->x, B * kFcIn * 2);
+  alloc((void **)&n->xt, B * kFcIn * 2);
+  alloc((void **)&n->h1, B * kHid * 2);
+  alloc((void **)&n->dh1, B * kHid * 2);
+  alloc((void **)&n->dh1t, B * kHid * 2);
+  alloc((void **)&n->y, B * 4);
+  alloc((void **)&n->loss, 4);
+  alloc((void **)&n->part, kSplitBytes);
+  if (!ok) {
+    free_net(n);
+    return NBT_ENOMEM;
+  }
+  *out = n;
+  return NBT_OK;
+}
+
+int nbt_surrogate_destroy(nbt_surrogate net) {
+  if (!net) return NBT_OK;
+  cudaDeviceSynchronize();
+  free_net(net);
+  return NBT_OK;
+}
+
+int nbt_surrogate_set_params(nbt_surrogate net, const float *host, int64_t n) {
+  int rc = check_net(net);
+  if (rc != NBT_OK) return rc;
+  if (!host || n != kP.total) return NBT_EINVAL;
+  NBT_CUDA_TRY(cudaMemcpy(net->params, host, (size_t)n * 4, cudaMemcpyHostToDevice));
+  NBT_CUDA_TRY(cudaMemset(net->adam_m, 0, (size_t)n * 4));
+  NBT_CUDA_TRY(cudaMemset(net->adam_v, 0, (size_t)n * 4));
+  net->step = 0;
+  rc = sync_weights(net, nullptr);
+  if (rc != NBT_OK) return rc;
+  NBT_CUDA_TRY(cudaDeviceSynchronize());
+  return NBT_OK;
+}
+
+int nbt_surrogate_get_params(nbt_surrogate net, float *host, int64_t n) {
+  int rc = check_net(net);
+  if (rc != NBT_OK) return rc;
+  if (!host || n != kP.total) return NBT_EINVAL;
+  NBT_CUDA_TRY(cudaDeviceSynchronize());
+  NBT_CUDA_TRY(cudaMemcpy(host, net->params, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  return NBT_OK;
+}
+
+int nbt_surrogate_crops(nbt_map map, const nbt_pose *poses, int64_t n, const nbt_camera *cam,
+                        const nbt_ig_params *params, void *crops, void *feats, void *stream) {
+  int rc = check_map(map);
+  if (rc != NBT_OK) return rc;
+  if (n < 0 || !cam || !params) return NBT_EINVAL;
+  if (n == 0) return NBT_OK;
+  if (!poses || !crops || !feats || ((uintptr_t)crops & 15u)) return NBT_EINVAL;
+  if (!(cam->fov_h > 0.0f && cam->fov_h < 3.14159f) || !(cam->fov_v > 0.0f && cam->fov_v < 3.14159f) ||
+      !(cam->max_range > 0.0f))
+    return NBT_EINVAL;
+  CropConst cc;
+  const double dh = (double)cam->max_range * tan((double)cam->fov_h * 0.5);
+  const double dv = (double)cam->max_range * tan((double)cam->fov_v * 0.5);
+  cc.x0 = (float)(-dh + dh / kCrop);
+  cc.xs = (float)(2.0 * dh / kCrop);
+  cc.y0 = (float)(-dv + dv / kCrop);
+  cc.ys = (float)(2.0 * dv / kCrop);
+  cc.zc = cam->max_range;
+  cc.inv_s = (float)(1.0 / (double)map->desc.voxel_size);
+  cc.ox = map->desc.origin[0];
+  cc.oy = map->desc.origin[1];
+  cc.oz = map->desc.origin[2];
+  cc.ext_x = (float)map->desc.nx * map->desc.voxel_size;  // one FP32 product (host, no contraction)
+  cc.ext_y = (float)map->desc.ny * map->desc.voxel_size;
+  cc.ext_z = (float)map->desc.nz * map->desc.voxel_size;
+  cc.occ_thr = params->occ_threshold;
+  cc.free_thr = params->free_threshold;
+  DevMap m;
+  m.payload = map->d_payload;  // raw states / probabilities (not derived gains)
+  m.tab = map->d_tab;
+  m.nx = map->desc.nx;
+  m.ny = map->desc.ny;
+  m.nz = map->desc.nz;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = grid_1d(n * kCrop * kCrop * kCrop);
+  switch (map->desc.encoding) {
+    case NBT_F32_PROB:
+      crop_kernel<PAYLOAD_GAIN_F32><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (bf16 *)crops, (bf16 *)feats);
+      break;
+    case NBT_U2_STATE:
+      crop_kernel<PAYLOAD_U2><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (bf16 *)crops, (bf16 *)feats);
+      break;
+    default:
+      crop_kernel<PAYLOAD_U8><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (bf16 *)crops, (bf16 *)feats);
+      break;
+  }
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+int nbt_surrogate_forward(nbt_surrogate net, const void *crops, const void *feats, int64_t n, float *pred,
+                          void *stream) {
+  int rc = check_net(net);
+  if (rc != NBT_OK) return rc;
+  if (n < 0) return NBT_EINVAL;
+  if (n == 0) return NBT_OK;
+  if (!crops || !feats || !pred || ((uintptr_t)crops & 15u)) return NBT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t per = (int64_t)kCrop * kCrop * kCrop * kC0;
+  for (int64_t b0 = 0; b0 < n; b0 += net->max_batch) {
+    const int nb = (int)std::min<int64_t>(net->max_batch, n - b0);
+    rc = forward_batch(net, (const bf16 *)crops + b0 * per, (const bf16 *)feats + b0 * kFeat, nb, pred + b0, s);
+    if (rc != NBT_OK) return rc;
+  }
+  return NBT_OK;
+}
+
+int nbt_surrogate_backward(nbt_surrogate net, const void *crops, const void *feats, const float *targets, int32_t n,
+                           float *grads_out, float *loss_out, void *stream) {
+  int rc = check_net(net);
+  if (rc != NBT_OK) return rc;
+  if (n < 1 || n > net->max_batch || n > 1024 || !crops || !feats || !targets) return NBT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = backward_batch(net, (const bf16 *)crops, (const bf16 *)feats, targets, n, s);
+  if (rc != NBT_OK) return rc;
+  if (grads_out) NBT_CUDA_TRY(cudaMemcpyAsync(grads_out, net->grads, kP.total * 4, cudaMemcpyDeviceToDevice, s));
+  if (loss_out) NBT_CUDA_TRY(cudaMemcpyAsync(loss_out, net->loss, 4, cudaMemcpyDeviceToDevice, s));
+  return NBT_OK;
+}
+
+int nbt_surrogate_train_step(nbt_surrogate net, const void *crops, const void *feats, const float *targets, int32_t n,
+                             float lr, float *loss_out, void *stream) {
+  int rc = nbt_surrogate_backward(net, crops, feats, targets, n, nullptr, loss_out, stream);
+  if (rc != NBT_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  net->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = (float)(1.0 - pow(0.9, (double)net->step)), c2 = (float)(1.0 - pow(0.999, (double)net->step));
+  adam_kernel<<<grid_1d(kP.total), 256, 0, s>>>(net->params, net->grads, net->adam_m, net->adam_v, kP.total, lr, b1,
+                                                b2, 1e-8f, c1, c2);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return sync_weights(net, s);
 }
 
 }  // extern "C"

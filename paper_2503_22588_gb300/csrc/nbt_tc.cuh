@@ -2,8 +2,8 @@
 //
 // C[M, N] = A[M, K] * B[N, K]^T with BF16 operands and FP32 accumulation in
 // tensor memory (TMEM), written directly in PTX for sm_103a:
-//   - a CTA of 128 threads owns one 128-row tile of C and all of its
-//     BN <= 256 columns (one TMEM accumulator of BN FP32 columns);
+//   - a CTA of 128 threads owns one 128-row x BN-column tile of C (BN <=
+//     256, one TMEM accumulator of BN FP32 columns) and one split of K;
 //   - K advances in stages of 64: all threads gather the A and B stage
 //     (through loader functors: a plain matrix, or an implicit-GEMM view of
 //     a convolution) into shared memory in the canonical no-swizzle K-major
@@ -145,19 +145,36 @@ __device__ __forceinline__ uint32_t stage_off(int r, int kc, int rows) {
 __host__ __device__ constexpr size_t stage_bytes(int bn) { return (size_t)(kBM + bn) * kBK * 2; }
 __host__ __device__ constexpr size_t gemm_smem_bytes(int bn) { return 2 * stage_bytes(bn) + 1024; }
 
-// The GEMM kernel.  LoadA / LoadB: `uint4 chunk(int row, int kchunk) const`
-// returns 8 BF16 (row `row` of the operand, K elements 8*kchunk .. +7; zero
-// outside).  Epi: `void row(int m, int n0, const float v[16]) const` for
-// each row m < M of the tile and column block n0 (16 columns).
+// Default stage fill from a chunk loader: 16-byte chunk (row, kchunk) of
+// the operand -> its place in the stage.  Threads take consecutive rows of
+// one chunk column, so a warp's 512-byte store is bank-conflict free.
+template <int ROWS, class L>
+__device__ __forceinline__ void fill_chunks(const L &l, uint8_t *stage, int row0, int kc0, int tid) {
+  for (int c = tid; c < ROWS * 8; c += kThreads) {
+    const int r = c % ROWS, kc = c / ROWS;
+    *(uint4 *)(stage + stage_off(r, kc, ROWS)) = l.chunk(row0 + r, kc0 + kc);
+  }
+}
+
+// The GEMM kernel.  Grid: x over 128-row tiles of M, y over BN-column tiles
+// of N, z over splits of K (kt_split stages of 64 each).
+// LoadA / LoadB: `template <int ROWS> void fill(uint8_t *stage, int row0,
+// int kc0, int tid) const` writes rows row0 .. row0+ROWS-1, K chunks
+// kc0 .. kc0+7 (8 BF16 each, zero outside the operand) into the stage
+// (fill_chunks does it from a `uint4 chunk(int row, int kchunk)`).
+// Epi: `void row(int m, int n, const float v[16], int z) const` receives
+// columns n .. n+15 of row m < M (columns past the real N are the loader's
+// zeros' products; the epilogue skips them).
 template <int BN, class LoadA, class LoadB, class Epi>
-__global__ void __launch_bounds__(kThreads) gemm_kernel(LoadA la, LoadB lb, Epi epi, int M, int K, int *err) {
+__global__ void __launch_bounds__(kThreads) gemm_kernel(LoadA la, LoadB lb, Epi epi, int M, int K, int kt_split,
+                                                        int *err) {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int m0 = blockIdx.x * kBM;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN, z = blockIdx.z;
   constexpr uint32_t NCOLS = (uint32_t)tmem_cols(BN);
   if (warp == 0) tmem_alloc(&tmem_base, NCOLS);
   if (tid == 0) {
@@ -170,25 +187,21 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(LoadA la, LoadB lb, Epi 
   fence_after_sync();
   const uint32_t tmem = tmem_base;
   constexpr uint32_t idesc = idesc_bf16(kBM, BN);
-  const int kt_n = (K + kBK - 1) / kBK;
+  const int kt_all = (K + kBK - 1) / kBK;
+  const int kt_begin = z * kt_split;
+  const int kt_end = min(kt_all, kt_begin + kt_split);
   bool ok = true;
   int issued = 0;
-  for (int kt = 0; kt < kt_n; ++kt) {
-    const int s = kt & 1;
-    if (kt >= 2) ok = mbar_wait(&mbar[s], (uint32_t)((kt - 2) >> 1) & 1u);
+  for (int kt = kt_begin; kt < kt_end; ++kt) {
+    const int it = kt - kt_begin, s = it & 1;
+    if (it >= 2) ok = mbar_wait(&mbar[s], (uint32_t)((it - 2) >> 1) & 1u);
     ok = __syncthreads_and(ok) != 0;
     if (!ok) break;
     uint8_t *sa = smem + s * stage_bytes(BN);
     uint8_t *sb = sa + kBM * kBK * 2;
     const int kc0 = kt * (kBK / 8);
-    for (int c = tid; c < kBM * 8; c += kThreads) {
-      const int r = c & (kBM - 1), kc = c >> 7;
-      *(uint4 *)(sa + stage_off(r, kc, kBM)) = la.chunk(m0 + r, kc0 + kc);
-    }
-    for (int c = tid; c < BN * 8; c += kThreads) {
-      const int r = c % BN, kc = c / BN;
-      *(uint4 *)(sb + stage_off(r, kc, BN)) = lb.chunk(r, kc0 + kc);
-    }
+    la.template fill<kBM>(sa, m0, kc0, tid);
+    lb.template fill<BN>(sb, n0, kc0, tid);
     fence_smem_async();
     __syncthreads();
     if (tid == 0) {
@@ -198,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(LoadA la, LoadB lb, Epi 
       for (int kk = 0; kk < 4; ++kk) {
         const uint64_t ad = sdesc(a0 + kk * (kBM * 32), 128, 256);
         const uint64_t bd = sdesc(b0 + kk * (BN * 32), 128, 256);
-        mma_bf16(tmem, ad, bd, idesc, (kt | kk) != 0 ? 1u : 0u);
+        mma_bf16(tmem, ad, bd, idesc, (it | kk) != 0 ? 1u : 0u);
       }
       mma_commit(&mbar[s]);
     }
@@ -213,10 +226,15 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(LoadA la, LoadB lb, Epi 
   if (ok) {
     const int row = m0 + warp * 32 + (tid & 31);
 #pragma unroll 1
-    for (int n0 = 0; n0 < BN; n0 += 16) {
+    for (int nn = 0; nn < BN; nn += 16) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0, v);
-      if (row < M) epi.row(row, n0, v);
+      if (issued > 0) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)nn, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.0f;  // empty K split: contributes zeros
+      }
+      if (row < M) epi.row(row, n0 + nn, v, z);
     }
   } else {
     if (tid == 0) atomicExch(err, 1);

@@ -1,0 +1,150 @@
+"""The learned surrogate's CUDA kernels against the FP64 oracle (GPU required).
+
+Crops: byte-exact.  Forward: relative 2e-2 against the oracle evaluated with
+the same BF16 rounding of weights and activations (the only remaining
+differences are FP32-vs-FP64 accumulation and the BF16 roundings that flips
+in it cause).  Gradients: relative L2 error per tensor <= 5e-2 (the GPU also
+rounds the backward intermediates to BF16).  Adam: the update the oracle
+computes from the GPU's gradients, to FP32 precision.
+"""
+
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2503_22588_gb300 as nbt
+from oracle import surrogate as S
+from paper_2503_22588_gb300 import _lib
+from paper_2503_22588_gb300 import surrogate as gs
+from workload import configs, poses, scenes
+
+pytestmark = pytest.mark.gpu
+
+BF16_WEIGHTS = ("w0", "w1", "w2", "w3", "f1")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    nbt.build()
+
+
+def no_device_timeout():
+    f = C.c_int32()
+    assert _lib.lib().nbt_tc_error(C.byref(f)) == 0
+    return f.value == 0
+
+
+def as_used_by_gpu(p):
+    """The parameters as the GPU uses them: BF16 weights, FP32 biases and f2."""
+    q = {k: np.asarray(v, np.float64) for k, v in p.items()}
+    for k in BF16_WEIGHTS:
+        q[k] = S._bf16(p[k])
+    return q
+
+
+def small_scene(enc, seed=0, n=48):
+    grid = scenes.boxes_spheres(n, 30, seed, size_range=(2.0, 10.0), half_unknown=True)
+    if enc == "f32":
+        occ = grid == 2
+        unk = grid == 0
+        grid = scenes.probabilities_from_masks(occ, unk, seed)
+    poi = np.full(3, n * 0.005)
+    p = poses.shell_views(poi, 8, 0.1, 0.3, seed)
+    return grid, p
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("enc", ["u8", "u2", "f32"])
+def test_crops_bitexact(enc):
+    grid, p = small_scene(enc, seed=3)
+    cam = nbt.camera(64, 48, math.radians(60), math.radians(45), 0.5)
+    prm = nbt.ig_params("count" if enc != "f32" else "entropy")
+    m = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01, (0.0, 0.0, 0.0), enc)
+    cr, ft = gs.crops(m, torch.from_numpy(p).cuda(), cam, prm)
+    cr = cr.float().cpu().numpy()
+    ft = ft.float().cpu().numpy()
+    cc = S.crop_consts(math.radians(60), math.radians(45), 0.5)
+    for v in range(3):
+        oc, of = S.frustum_crop(grid, 0.01, (0, 0, 0), p[v], cc)
+        assert np.array_equal(cr[v].astype(np.uint8), oc), v
+        assert np.array_equal(ft[v], S._bf16(of).astype(np.float32)), v
+        assert oc[..., 0].any() and oc[..., 1].any()
+
+
+def _batch(n_views=6, seed=2):
+    grid, p = small_scene("u8", seed=seed)
+    cam = nbt.camera(64, 48, math.radians(60), math.radians(45), 0.5)
+    m = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01)
+    pz = torch.from_numpy(np.concatenate([p, p])[:n_views]).cuda()
+    return gs.crops(m, pz, cam, nbt.ig_params("count"))
+
+
+def test_forward_matches_oracle():
+    cr, ft = _batch(6)
+    params = S.init_params(1)
+    params["b0"] += 0.05
+    params["g1"] += 0.02
+    net = gs.Surrogate(max_batch=4, params=params)   # 6 samples: two passes
+    pred = net.forward(cr, ft).cpu().numpy().astype(np.float64)
+    y, _ = S.forward(as_used_by_gpu(params), cr.float().cpu().numpy(), ft.float().cpu().numpy(), bf16_activations=True)
+    assert no_device_timeout()
+    assert np.allclose(pred, y, rtol=2e-2, atol=2e-2 * np.abs(y).max()), (pred, y)
+    net.close()
+
+
+def test_backward_matches_oracle_gradients():
+    cr, ft = _batch(8, seed=5)
+    params = S.init_params(4)
+    params["g1"] += 0.05
+    net = gs.Surrogate(max_batch=8, params=params)
+    t = torch.linspace(0.0, 1.0, 8, device="cuda")
+    loss, grads = net.backward(cr, ft, t)
+    torch.cuda.synchronize()
+    assert no_device_timeout()
+    g = gs.unpack(grads.cpu().numpy())
+    oloss, og = S.loss_and_grads(as_used_by_gpu(params), cr.float().cpu().numpy(), ft.float().cpu().numpy(),
+                                 t.cpu().numpy(), bf16_activations=True)
+    assert abs(loss.item() - oloss) <= 2e-2 * abs(oloss)
+    for k in og:
+        err = rel_l2(g[k], og[k])
+        assert err <= 5e-2, (k, err)
+    net.close()
+
+
+def test_adam_step_matches_oracle_update():
+    cr, ft = _batch(8, seed=6)
+    params = S.init_params(7)
+    net = gs.Surrogate(max_batch=8, params=params)
+    t = torch.rand(8, device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    _, grads = net.backward(cr, ft, t)
+    g = gs.unpack(grads.cpu().numpy())
+    net.train_step(cr, ft, t, lr=1e-3)
+    got = net.get_params()
+    zeros = {k: np.zeros_like(v, np.float64) for k, v in params.items()}
+    want, _, _ = S.adam(params, g, zeros, zeros, 1, lr=1e-3)
+    for k in params:
+        assert np.allclose(got[k], want[k], rtol=1e-5, atol=1e-7), k
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    cr, ft = _batch(32, seed=8)
+    net = gs.Surrogate(max_batch=32, params=S.init_params(9))
+    t = torch.rand(32, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    first = net.backward(cr, ft, t)[0].item()
+    for _ in range(60):
+        net.train_step(cr, ft, t, lr=1e-3)
+    last = net.backward(cr, ft, t)[0].item()
+    assert no_device_timeout()
+    assert last < 0.5 * first, (first, last)
+    net.close()
