@@ -277,8 +277,8 @@ int nbt_tc_error(int32_t *flag);
  * zero outside the map) of the voxel holding it, BF16 NDHWC [n][32][32][32]
  * [8] -- and 8 BF16 pose features ((position - origin) / map extent, the
  * quaternion, 1).  Output: the predicted mean ray IG (the training target
- * the caller chooses, e.g. g_P / 100).  Network: 3^3 convolutions 8->16
- * (stride 1), 16->32, 32->64, 64->64 (stride 2), ReLU; 4096 + 8 -> 128
+ * the caller chooses, e.g. g_P / 100).  Network: 3^3 convolutions 8->16,
+ * 16->32, 32->64 (stride 2) and 64->64 (stride 1), ReLU; 4096 + 8 -> 128
  * (ReLU) -> 1; BF16 weights and activations, FP32 accumulation on tcgen05
  * tensor cores, FP32 master weights, MSE loss, Adam. */
 typedef struct nbt_surrogate_s *nbt_surrogate;
@@ -318,6 +318,20 @@ int nbt_surrogate_backward(nbt_surrogate net, const void *crops, const void *fea
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on one batch. */
 int nbt_surrogate_train_step(nbt_surrogate net, const void *crops, const void *feats, const float *targets, int32_t n,
                              float lr, float *loss_out, void *stream);
+
+/* Surrogate-pruned planning helpers.  Candidates come in segments of seg
+ * perspectives (e.g. the views around one PoI); n % seg == 0.
+ * nbt_segment_topk: for each segment, the global indices of its keep
+ * highest scores (descending; ties to the lower index; NaN last), device
+ * int32[n / seg][keep]; with poses / poses_out (both or neither) also the
+ * kept poses, device nbt_pose[n / seg][keep].  seg <= 8192.
+ * nbt_segment_argmax: for each segment the largest value and the index
+ * that holds it (idx[position] if idx is given, else the position; ties
+ * to the lowest index), device int32 / float[n / seg] (best_val nullable). */
+int nbt_segment_topk(const float *scores, int64_t n, int32_t seg, int32_t keep, int32_t *idx_out, const nbt_pose *poses,
+                     nbt_pose *poses_out, void *stream);
+int nbt_segment_argmax(const float *values, const int32_t *idx, int64_t n, int32_t seg, int32_t *best_idx,
+                       float *best_val, void *stream);
 
 /* Size of the fixed device scratch array behind nbt_views_ig_noalloc. */
 #define NBT_NOALLOC_SCRATCH_BYTES (4 << 20)

@@ -15,7 +15,7 @@ the CUDA surrogate computes, so the GPU kernels can be checked:
   The sample arithmetic is FP32 in one fixed order (numpy rounds every
   float32 operation separately), as on the GPU, so crops are byte-exact.
 * ``forward`` / ``backward``: four 3x3x3 convolutions (padding 1; strides
-  1, 2, 2, 2; ReLU), flatten, concatenation with 8 pose features, a hidden
+  2, 2, 2, 1; ReLU), flatten, concatenation with 8 pose features, a hidden
   layer of 128 ReLU units and one linear output; loss = mean squared error.
   Tensors are NDHWC; a convolution weight is [C_out, 27 * C_in] with the
   tap index (dz * 3 + dy) * 3 + dx and the input channel fastest.
@@ -30,7 +30,7 @@ import numpy as np
 
 CROP = 32
 C0 = 8
-LAYERS = ((8, 16, 1), (16, 32, 2), (32, 64, 2), (64, 64, 2))   # (C_in, C_out, stride)
+LAYERS = ((8, 16, 2), (16, 32, 2), (32, 64, 2), (64, 64, 1))   # (C_in, C_out, stride)
 FEATS = 8
 HIDDEN = 128
 

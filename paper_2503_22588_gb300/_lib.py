@@ -70,6 +70,8 @@ SIGNATURES = {
     "nbt_tc_gemm": (C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp]),
     "nbt_tc_error": (C.c_int, [P(C.c_int32)]),
     "nbt_surrogate_param_count": (C.c_int, [P(C.c_int64)]),
+    "nbt_segment_topk": (C.c_int, [_vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "nbt_segment_argmax": (C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp]),
     "nbt_surrogate_create": (C.c_int, [_i32, P(_vp)]),
     "nbt_surrogate_destroy": (C.c_int, [_vp]),
     "nbt_surrogate_set_params": (C.c_int, [_vp, _vp, _i64]),

@@ -8,7 +8,7 @@
 // Network (all layers on the tcgen05 GEMM of nbt_tc.cuh, BF16 operands and
 // activations, FP32 accumulation and FP32 master weights):
 //   crop 32^3 x 8 (one-hot unknown / free / occupied in channels 0..2)
-//   conv 3^3 8->16 s1, conv 16->32 s2, conv 32->64 s2, conv 64->64 s2 (ReLU)
+//   conv 3^3 8->16 s2, conv 16->32 s2, conv 32->64 s2, conv 64->64 s1 (ReLU)
 //   flatten 4^3 x 64 = 4096 | 8 pose features -> fc 4104->128 (ReLU) -> fc 128->1
 // Convolutions are implicit GEMMs: a loader gathers the im2col tile of the
 // stage straight from the NDHWC activations into shared memory (nothing is
@@ -41,7 +41,7 @@ constexpr int kLayers = 4;
 struct LayerDims {
   int cin, cout, stride, din, dout;
 };
-constexpr LayerDims kL[kLayers] = {{8, 16, 1, 32, 32}, {16, 32, 2, 32, 16}, {32, 64, 2, 16, 8}, {64, 64, 2, 8, 4}};
+constexpr LayerDims kL[kLayers] = {{8, 16, 2, 32, 16}, {16, 32, 2, 16, 8}, {32, 64, 2, 8, 4}, {64, 64, 1, 4, 4}};
 // (the device-side weight copy kernel repeats these channel counts as literals)
 constexpr int kSplitBytes = 64 << 20;  // weight-gradient split-K partials
 
@@ -506,6 +506,85 @@ __global__ void sync_weights_kernel(const float *__restrict__ p, bf16 *__restric
   }
 }
 
+// Per-segment top-k (one CTA per segment of seg <= 8192 scores): bitonic
+// sort in shared memory, descending score, ties to the lower index (so the
+// order is deterministic); writes the kept global indices and, if asked,
+// the kept poses.
+__global__ void segment_topk_kernel(const float *__restrict__ scores, int seg, int keep, int pow2,
+                                    int32_t *__restrict__ idx_out, const float *__restrict__ poses,
+                                    float *__restrict__ poses_out) {
+  extern __shared__ uint8_t sm[];
+  float *key = (float *)sm;
+  int32_t *id = (int32_t *)(key + pow2);
+  const int64_t base = (int64_t)blockIdx.x * seg;
+  for (int i = threadIdx.x; i < pow2; i += blockDim.x) {
+    const float v = i < seg ? scores[base + i] : -INFINITY;
+    key[i] = v != v ? -INFINITY : v;  // NaN scores rank last
+    id[i] = i;
+  }
+  __syncthreads();
+  for (int k = 2; k <= pow2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < pow2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          // "before(a, b)": a ranks ahead of b
+          const bool ab = key[i] > key[l] || (key[i] == key[l] && id[i] < id[l]);
+          const bool desc = (i & k) == 0;
+          if (desc ? !ab : ab) {
+            const float tk = key[i];
+            key[i] = key[l];
+            key[l] = tk;
+            const int32_t ti = id[i];
+            id[i] = id[l];
+            id[l] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = threadIdx.x; r < keep; r += blockDim.x) {
+    const int64_t g = base + id[r];
+    idx_out[(int64_t)blockIdx.x * keep + r] = (int32_t)g;
+    if (poses && poses_out)
+      for (int q = 0; q < 7; ++q) poses_out[((int64_t)blockIdx.x * keep + r) * 7 + q] = poses[g * 7 + q];
+  }
+}
+
+// Per-segment argmax (one warp per segment): the largest value, ties to the
+// lowest original index (idx maps position -> original index, or identity).
+__global__ void segment_argmax_kernel(const float *__restrict__ vals, const int32_t *__restrict__ idx, int64_t n_seg,
+                                      int seg, int32_t *__restrict__ best_idx, float *__restrict__ best_val) {
+  const int64_t sgi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (sgi >= n_seg) return;
+  float bv = -INFINITY;
+  int32_t bi = INT32_MAX;
+  for (int i = lane; i < seg; i += 32) {
+    const int64_t p = sgi * seg + i;
+    const float v = vals[p];
+    const int32_t o = idx ? idx[p] : (int32_t)p;
+    if (v > bv || (v == bv && o < bi)) {
+      bv = v;
+      bi = o;
+    }
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, bv, s);
+    const int32_t oi = __shfl_xor_sync(0xffffffffu, bi, s);
+    if (ov > bv || (ov == bv && oi < bi)) {
+      bv = ov;
+      bi = oi;
+    }
+  }
+  if (lane == 0) {
+    best_idx[sgi] = bi;
+    if (best_val) best_val[sgi] = bv;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -897,6 +976,36 @@ int nbt_surrogate_train_step(nbt_surrogate net, const void *crops, const void *f
                                                 b2, 1e-8f, c1, c2);
   NBT_CUDA_TRY(cudaGetLastError());
   return sync_weights(net, s);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int nbt_segment_topk(const float *scores, int64_t n, int32_t seg, int32_t keep, int32_t *idx_out, const nbt_pose *poses,
+                     nbt_pose *poses_out, void *stream) {
+  if (!scores || !idx_out || seg < 1 || seg > 8192 || keep < 1 || keep > seg || n < 0 || n % seg) return NBT_EINVAL;
+  if ((poses == nullptr) != (poses_out == nullptr)) return NBT_EINVAL;
+  if (n == 0) return NBT_OK;
+  int pow2 = 1;
+  while (pow2 < seg) pow2 <<= 1;
+  const size_t smem = (size_t)pow2 * 8;
+  NBT_CUDA_TRY(cudaFuncSetAttribute(segment_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  segment_topk_kernel<<<(unsigned)(n / seg), 512, smem, (cudaStream_t)stream>>>(
+      scores, seg, keep, pow2, idx_out, (const float *)poses, (float *)poses_out);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+int nbt_segment_argmax(const float *values, const int32_t *idx, int64_t n, int32_t seg, int32_t *best_idx,
+                       float *best_val, void *stream) {
+  if (!values || !best_idx || seg < 1 || n < 0 || n % seg) return NBT_EINVAL;
+  if (n == 0) return NBT_OK;
+  const int64_t n_seg = n / seg;
+  segment_argmax_kernel<<<(unsigned)((n_seg * 32 + 255) / 256), 256, 0, (cudaStream_t)stream>>>(values, idx, n_seg, seg,
+                                                                                              best_idx, best_val);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
 }
 
 }  // extern "C"

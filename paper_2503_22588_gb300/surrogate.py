@@ -16,7 +16,7 @@ import torch
 from ._lib import check, lib
 from .api import Camera, IgParams, Map, _dev, _stream
 
-LAYERS = ((8, 16, 1), (16, 32, 2), (32, 64, 2), (64, 64, 2))
+LAYERS = ((8, 16, 2), (16, 32, 2), (32, 64, 2), (64, 64, 1))
 CROP, C0, FEATS, HIDDEN, FC_IN = 32, 8, 8, 128, 4104
 SHAPES = ([item for i, (ci, co, _) in enumerate(LAYERS) for item in ((f"w{i}", (co, 27 * ci)), (f"b{i}", (co,)))]
           + [("f1", (HIDDEN, FC_IN)), ("g1", (HIDDEN,)), ("f2", (HIDDEN,)), ("g2", (1,))])

@@ -148,3 +148,40 @@ def test_training_reduces_the_loss():
     assert no_device_timeout()
     assert last < 0.5 * first, (first, last)
     net.close()
+
+
+def test_segment_topk_and_argmax_match_numpy():
+    from paper_2503_22588_gb300 import planning as P
+    g = torch.Generator(device="cuda").manual_seed(3)
+    for seg, keep in ((4096, 205), (100, 7), (33, 33), (1, 1)):
+        n = seg * 5
+        scores = torch.rand(n, device="cuda", generator=g)
+        if seg > 5:
+            scores[3] = scores[5]  # a tie inside the first segment
+        pz = torch.rand((n, 7), device="cuda", generator=g)
+        idx, kept = P.segment_topk(scores, seg, keep, pz)
+        s = scores.cpu().numpy().reshape(-1, seg)
+        for k in range(5):
+            order = sorted(range(seg), key=lambda i: (-s[k, i], i))[:keep]
+            assert list(idx[k].cpu().numpy() - k * seg) == order, (seg, k)
+        assert torch.equal(kept, pz[idx.reshape(-1).long()])
+        best, val = P.segment_argmax(scores, seg)
+        assert np.array_equal(best.cpu().numpy(), s.argmax(1) + np.arange(5) * seg)
+        assert np.array_equal(val.cpu().numpy(), s.max(1))
+
+
+def test_pruned_selection_keeps_the_exact_best_when_everything_is_kept():
+    """keep = seg: pruning changes nothing, so the pruned choice equals the exact one."""
+    from paper_2503_22588_gb300 import planning as P
+    w = configs.exact64(seed=4, n_views=64)
+    cam = nbt.camera(32, 24, w.camera.fov_h, w.camera.fov_v, 1.0)
+    prm = nbt.ig_params("count")
+    m = nbt.Map.from_grid(torch.from_numpy(w.grid).cuda(), 0.01)
+    pz = torch.from_numpy(w.poses).cuda()
+    net = gs.Surrogate(max_batch=32, params=S.init_params(2))
+    bx, vx, _ = P.exact_best(m, pz, 16, cam, prm)
+    bp, vp, kept = P.pruned_best(net, m, pz, 16, 16, cam, prm)
+    assert torch.equal(bx, bp) and torch.equal(vx, vp)
+    bp2, vp2, kept2 = P.pruned_best(net, m, pz, 16, 3, cam, prm)
+    assert kept2.shape == (4, 3) and torch.all(vp2 <= vx)
+    net.close()
