@@ -45,6 +45,8 @@ def describe(w) -> str:
                    "320x240 rays, unknown-voxel count",
         "traj256": "traj256: 256^3 uint8 tabletop, 512 trajectories of 5-40 poses around 4 PoIs, 128x96 rays, "
                    "trajectory IG = sum of per-pose unknown counts, one CUDA-graph replay per step",
+        "idw_cost": "idw_cost: c_I of 16384 candidate trajectories x 31 states (3 s horizon, 0.1 s steps) against "
+                    "N_B=10 buffered IDs of N_P=500 perspectives (Eq. 3, p=2, orientation factor, eps=1e-7)",
     }.get(w.name, w.name)
 
 
@@ -125,6 +127,8 @@ class ClockSampler:
 
 def build_workload(name: str, rank: int):
     from workload import configs
+    if name == "idw_cost":
+        return configs.idw_cost(seed=rank)
     return configs.WORKLOADS[name](seed=rank)
 
 
@@ -171,9 +175,59 @@ def traj_cpu_baseline(w, budget_s: float = 12.0) -> dict:
                       f"voxel steps)", "voxel_steps_per_s": float(st.sum()) / dt}
 
 
+COST_METRIC = "IG cost states/s (Eq. 3 interpolation + orientation factor + c_I per candidate trajectory)"
+MUFU_PER_CLK_PER_SM = 16     # reciprocal / log2 / exp2 results per SM per clock
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def cost_cpu_sample(w, n_traj: int):
+    """Run the oracle's c_I on the first n_traj trajectories; returns (seconds, states)."""
+    from oracle import idw as I
+    ids = [(pz[:, :3].astype(np.float64), g.astype(np.float64)) for pz, g in w.ids]
+    n = int(w.offsets[n_traj])
+    t0 = time.perf_counter()
+    I.ig_cost(w.poses[:n], w.offsets[:n_traj + 1], w.poi.astype(np.float64), w.fov_h, w.fov_v, ids, w.n_b, w.power,
+              w.w_info, w.eps)
+    return time.perf_counter() - t0, n
+
+
+def cost_cpu_baseline(w, budget_s: float = 12.0) -> dict:
+    """The oracle as it stands (FP64 numpy, one host thread) on a bounded sample of trajectories."""
+    dt1, _ = cost_cpu_sample(w, 1)
+    n_traj = int(max(1, min(len(w.offsets) - 1, budget_s / max(dt1, 1e-4))))
+    dt, n = cost_cpu_sample(w, n_traj)
+    return {"value": n / dt, "unit": "states/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n_traj} of {len(w.offsets) - 1} trajectories ({n} states)"}
+
+
+def run_reference_cost(args) -> None:
+    w = build_workload("idw_cost", 0)
+    dt1, _ = cost_cpu_sample(w, 1)
+    per_step_s = min(8.0, 120.0 / max(1, args.steps + args.warmup))
+    n_traj = int(max(1, min(len(w.offsets) - 1, per_step_s / max(dt1, 1e-4))))
+    for _ in range(args.warmup):
+        cost_cpu_sample(w, n_traj)
+    times = [cost_cpu_sample(w, n_traj) for _ in range(args.steps)]
+    total = sum(t for t, _ in times)
+    n = times[0][1]
+    value = n * args.steps / total
+    line = {"impl": "reference", "metric": COST_METRIC, "value": value, "unit": "states/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(w), "states_per_step": n, "parallelism": "one host thread"},
+            "cpu_baseline": {"value": value, "unit": "states/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n_traj} trajectories ({n} states) per step"},
+            "e2e": {"value": value, "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "idw_cost":
+        run_reference_cost(args)
         return
     import oracle
     w = build_workload(args.workload, 0)
@@ -214,7 +268,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="prob256",
-                    choices=["prob256", "exact64", "room512", "traj256", "room512-pruned"])
+                    choices=["prob256", "exact64", "room512", "traj256", "room512-pruned", "idw_cost"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -239,6 +293,9 @@ def main() -> None:
 
     if args.workload == "room512-pruned":
         run_pruned(args, nbt, torch, dev, world, rank, local, dist)
+        return
+    if args.workload == "idw_cost":
+        run_cost(args, nbt, torch, dev, stream, world, rank, local, dist)
         return
     w = build_workload(args.workload, rank)
     if w.offsets is not None:
@@ -463,6 +520,96 @@ def run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist) -> None
         print(json.dumps(line), flush=True)
     plan.close()
     m.close()
+
+
+def run_cost(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
+    """IG cost of candidate trajectories: per step, push the newest ID, then nbt_ig_cost over all candidates."""
+    w = build_workload("idw_cost", rank)
+    buf = nbt.IdBuffer(w.n_b, max(len(g) for _, g in w.ids))
+    id_dev = [(torch.from_numpy(pz).to(dev), torch.from_numpy(g).to(dev)) for pz, g in w.ids]
+    for pz, g in id_dev:
+        buf.push(pz, g, stream)
+    poses_dev = torch.from_numpy(w.poses).to(dev)
+    off_dev = torch.from_numpy(w.offsets).to(dev)
+    n_states, n_traj = w.poses.shape[0], len(w.offsets) - 1
+    pairs = n_states * sum(len(g) for _, g in w.ids)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(k, poses, off):
+        pz, g = id_dev[k % len(id_dev)]
+        buf.push(pz, g, stream)
+        return nbt.ig_cost(buf, poses, off, w.poi, w.fov_h, w.fov_v, w.w_info, w.power, w.eps, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for k in range(max(args.warmup, 3)):
+        step(k, poses_dev, off_dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, c = ev[k]
+        a.record(stream)
+        step(k, poses_dev, off_dev)
+        c.record(stream)
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # end to end: pinned host poses and offsets in, per-trajectory cost out
+    poses_host = torch.from_numpy(w.poses).pin_memory()
+    off_host = torch.from_numpy(w.offsets).pin_memory()
+    cost_host = torch.empty(n_traj, dtype=torch.float32).pin_memory()
+    e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, c = ev[k]
+        a.record(stream)
+        poses_dev.copy_(poses_host, non_blocking=True)
+        off_dev.copy_(off_host, non_blocking=True)
+        cost_host.copy_(step(k, poses_dev, off_dev), non_blocking=True)
+        c.record(stream)
+        c.synchronize()
+        e_ms.append(a.elapsed_time(c))
+    e2e_total = float(sum(e_ms))
+    mean_s = total_ms * 1e-3 / args.steps
+    peak = MUFU_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9   # Gpair/s at one MUFU op per pair
+    achieved = pairs / mean_s / 1e9
+    states_total = world * n_states * args.steps
+    line = {
+        "metric": COST_METRIC, "value": states_total / (total_ms * 1e-3), "unit": "states/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": describe(w), "states_per_gpu": n_states, "trajectories": n_traj,
+                   "ids": len(w.ids), "perspectives_per_id": len(w.ids[0][1]), "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "step": "nbt_id_buffer_push (newest ID) + nbt_ig_cost (IDW/orientation/term kernel + reduce)"},
+        "pairs_per_step": pairs,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "idw_kernel (+cost_reduce, id_push)",
+                     "algorithmic": f"1 MUFU reciprocal per (state, perspective) pair x {pairs} pairs",
+                     "peak_kind": f"derived: {MUFU_PER_CLK_PER_SM} MUFU/clk/SM x {SM_COUNT} SMs x {SM_MAX_MHZ} MHz"},
+        "e2e": {"value": states_total / (e2e_total * 1e-3), "unit": "states/s",
+                "h2d_bytes_per_step": int(poses_host.numel() * 4 + off_host.numel() * 4),
+                "d2h_bytes_per_step": int(cost_host.numel() * 4)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cost_cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    buf.close()
 
 
 def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:

@@ -333,6 +333,79 @@ int nbt_segment_topk(const float *scores, int64_t n, int32_t seg, int32_t keep, 
 int nbt_segment_argmax(const float *values, const int32_t *idx, int64_t n, int32_t seg, int32_t *best_idx,
                        float *best_val, void *stream);
 
+/* IG between perspectives (Section III "Orientation Factor and IG", Eq. 3,
+ * and "Cost Function Extension").  An information distribution (ID) is one
+ * set of N_P perspectives: start points p_P,j (metres, world frame) and
+ * IGs g_P,j (e.g. the mean ray IG nbt_views_ig returns).  The buffer keeps
+ * the N_B most recent IDs; a camera position x between perspectives gets
+ *   G(x) = sum_{u=0}^{N_B-1} 1 / (N_B - u) * IDW_u(x),
+ *   IDW_u(x) = sum_j g_P,j d_j^-p / sum_j d_j^-p,  d_j = |x - p_P,j|,
+ * for the IDs u of the buffer, u = 0 the oldest.  With n < N_B IDs stored
+ * the n IDs take u = N_B - n .. N_B - 1 (the newest always weighs 1).  A
+ * position that coincides with start points (FP32 d_j^2 == 0) takes, for
+ * that ID, the mean gain of those points; an empty ID adds nothing.
+ * Arithmetic: FP32 per pair (rcp.approx for p = 2, else exp2f / log2f),
+ * sums of 32 terms per lane folded into compensated FP32 totals, one IEEE
+ * division per ID; an ID whose FP32 sums overflow (points very close to
+ * the query, large p) is recomputed with FP64 weights and sums.  Positions
+ * must be finite; distinct positions closer than about 1e-19 m (FP32 d^2
+ * below the smallest normal float) read as coincident. */
+typedef struct nbt_id_buffer_s *nbt_id_buffer;
+
+/* Create an empty buffer of n_b (1 .. 32) IDs of up to max_views
+ * (1 .. 1 << 20) perspectives each on the current device.
+ * Errors: NBT_EINVAL, NBT_ENOMEM, NBT_ECUDA. */
+int nbt_id_buffer_create(int32_t n_b, int32_t max_views, nbt_id_buffer *out);
+int nbt_id_buffer_destroy(nbt_id_buffer buf);
+
+/* Append one ID: n_views (0 .. max_views) perspectives, poses as device
+ * nbt_pose[n_views] (the start point is the position; the rotation is not
+ * used) and ig as device float[n_views].  When the buffer already holds n_b
+ * IDs the oldest is dropped.  Asynchronous on stream: a query enqueued
+ * later on the same stream sees the new ID; the bookkeeping (which slot is
+ * oldest, how many perspectives each holds) is host-side and updated at
+ * once.  Errors: NBT_EINVAL, NBT_ECUDA. */
+int nbt_id_buffer_push(nbt_id_buffer buf, const nbt_pose *poses, const float *ig, int32_t n_views, void *stream);
+
+/* Forget every ID (host-side; nothing is enqueued). */
+int nbt_id_buffer_clear(nbt_id_buffer buf);
+
+/* Number of IDs held (0 .. n_b). */
+int nbt_id_buffer_count(nbt_id_buffer buf, int32_t *n_ids);
+
+/* G(x) for n query poses (device nbt_pose[n]; positions used) with
+ * distance power p = power (0 < power <= 8), written to device
+ * float[n].  n == 0 enqueues nothing.  Errors: NBT_EINVAL, NBT_ECUDA. */
+int nbt_idw_gain(nbt_id_buffer buf, const nbt_pose *poses, int64_t n, float power, float *gain_out, void *stream);
+
+/* Parameters of the IG cost: distance power p, weight w_I >= 0 and the
+ * epsilon of c_I (the paper uses 1e-7). */
+typedef struct {
+  float power;
+  float w_info;
+  float eps;
+} nbt_cost_params;
+
+/* IG cost of n_traj candidate trajectories (the states x_0 .. x_K of
+ * trajectory t are the camera poses offsets[t] .. offsets[t+1]-1 of poses,
+ * device int32 CSR offsets, n_traj + 1 entries, clamped to [0, n_poses]):
+ *   O(x) = cos of the angle between the optical axis (camera +z) and the
+ *          direction to poi, 0 when the PoI lies outside the field of view
+ *          (camera-frame direction c: inside iff c_z > 0,
+ *          |c_x| <= c_z tan(fov_h / 2), |c_y| <= c_z tan(fov_v / 2); the
+ *          decision in FP32: c_k = (R_0k v_0 + R_1k v_1) + R_2k v_2, v =
+ *          poi - position, R from the quaternion, each operation rounded,
+ *          the tangents evaluated in FP64 on the host and rounded once);
+ *   G(x) as nbt_idw_gain;
+ *   term(x) = w_I / (O(x) G(x) + eps);  cost_out[t] = sum_k term(x_k)
+ *   (per-trajectory sums in FP64, fixed order).
+ * poi: host float[3].  gain_out, orient_out: device float[n_poses] or NULL;
+ * term_out: device float[n_poses] (required); cost_out: device
+ * float[n_traj].  Errors: NBT_EINVAL, NBT_ECUDA. */
+int nbt_ig_cost(nbt_id_buffer buf, const nbt_pose *poses, int64_t n_poses, const int32_t *offsets, int32_t n_traj,
+                const float *poi, float fov_h, float fov_v, const nbt_cost_params *params, float *gain_out,
+                float *orient_out, float *term_out, float *cost_out, void *stream);
+
 /* Size of the fixed device scratch array behind nbt_views_ig_noalloc. */
 #define NBT_NOALLOC_SCRATCH_BYTES (4 << 20)
 

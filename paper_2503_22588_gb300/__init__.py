@@ -10,4 +10,5 @@ from .api import (Map, TrajPlan, camera, ig_params, trace_segments, traj_ig, vie
                   views_ig, views_ig_noalloc, workspace, workspace_size)
 from .autotune import autotune  # noqa: F401
 from . import surrogate  # noqa: F401
+from .idw import IdBuffer, idw_gain, ig_cost  # noqa: F401
 from .build import LIB_PATH, build  # noqa: F401

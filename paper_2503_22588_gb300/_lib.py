@@ -46,6 +46,10 @@ class IgParams(C.Structure):
                 ("include_hit", C.c_int32), ("reduce", C.c_int32)]
 
 
+class CostParams(C.Structure):
+    _fields_ = [("power", C.c_float), ("w_info", C.c_float), ("eps", C.c_float)]
+
+
 # Every symbol include/nbt.h declares, with (restype, argtypes).
 _vp, _i32, _i64, _f = C.c_void_p, C.c_int32, C.c_int64, C.c_float
 P = C.POINTER
@@ -81,6 +85,13 @@ SIGNATURES = {
     "nbt_surrogate_backward": (C.c_int, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "nbt_surrogate_train_step": (C.c_int, [_vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp]),
     "nbt_map_get_tuning": (C.c_int, [_vp, P(Tuning)]),
+    "nbt_id_buffer_create": (C.c_int, [_i32, _i32, P(_vp)]),
+    "nbt_id_buffer_destroy": (C.c_int, [_vp]),
+    "nbt_id_buffer_push": (C.c_int, [_vp, _vp, _vp, _i32, _vp]),
+    "nbt_id_buffer_clear": (C.c_int, [_vp]),
+    "nbt_id_buffer_count": (C.c_int, [_vp, P(C.c_int32)]),
+    "nbt_idw_gain": (C.c_int, [_vp, _vp, _i64, _f, _vp, _vp]),
+    "nbt_ig_cost": (C.c_int, [_vp, _vp, _i64, _vp, _i32, P(_f), _f, _f, P(CostParams), _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None

@@ -95,14 +95,13 @@ __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
 
-// Segment (voxel units) of ray (i, j) for a pose: Section III endpoint grid.
-__device__ __forceinline__ void ray_segment(const CamConst &cc, const float *pose, int i, int j, float o[3],
-                                            float d[3]) {
-  const float qw = pose[3], qx = pose[4], qy = pose[5], qz = pose[6];
+// Camera-to-world rotation (row-major) of the unit quaternion q = (w, x, y, z),
+// every operation rounded to FP32 in this fixed order.
+__device__ __forceinline__ void quat_rot_f32(const float *q, float r[9]) {
+  const float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
   const float xx = fmul(qx, qx), yy = fmul(qy, qy), zz = fmul(qz, qz);
   const float xy = fmul(qx, qy), xz = fmul(qx, qz), yz = fmul(qy, qz);
   const float wx = fmul(qw, qx), wy = fmul(qw, qy), wz = fmul(qw, qz);
-  float r[9];
   r[0] = fsub(1.0f, fmul(2.0f, fadd(yy, zz)));
   r[1] = fmul(2.0f, fsub(xy, wz));
   r[2] = fmul(2.0f, fadd(xz, wy));
@@ -112,6 +111,13 @@ __device__ __forceinline__ void ray_segment(const CamConst &cc, const float *pos
   r[6] = fmul(2.0f, fsub(xz, wy));
   r[7] = fmul(2.0f, fadd(yz, wx));
   r[8] = fsub(1.0f, fmul(2.0f, fadd(xx, yy)));
+}
+
+// Segment (voxel units) of ray (i, j) for a pose: Section III endpoint grid.
+__device__ __forceinline__ void ray_segment(const CamConst &cc, const float *pose, int i, int j, float o[3],
+                                            float d[3]) {
+  float r[9];
+  quat_rot_f32(pose + 3, r);
   float cx = fadd(cc.x0, fmul((float)i, cc.xstep));
   float cy = fadd(cc.y0, fmul((float)j, cc.ystep));
   float cz = cc.zc;

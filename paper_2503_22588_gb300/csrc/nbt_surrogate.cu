@@ -286,20 +286,8 @@ __global__ void crop_kernel(DevMap m, CropConst cc, const float *__restrict__ po
     float pz[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) pz[q] = __ldg(poses + v * 7 + q);
-    const float qw = pz[3], qx = pz[4], qy = pz[5], qz = pz[6];
-    const float xx = fmul(qx, qx), yy = fmul(qy, qy), zz = fmul(qz, qz);
-    const float xy = fmul(qx, qy), xz = fmul(qx, qz), yz = fmul(qy, qz);
-    const float wx = fmul(qw, qx), wy = fmul(qw, qy), wz = fmul(qw, qz);
     float r[9];
-    r[0] = fsub(1.0f, fmul(2.0f, fadd(yy, zz)));
-    r[1] = fmul(2.0f, fsub(xy, wz));
-    r[2] = fmul(2.0f, fadd(xz, wy));
-    r[3] = fmul(2.0f, fadd(xy, wz));
-    r[4] = fsub(1.0f, fmul(2.0f, fadd(xx, zz)));
-    r[5] = fmul(2.0f, fsub(yz, wx));
-    r[6] = fmul(2.0f, fsub(xz, wy));
-    r[7] = fmul(2.0f, fadd(yz, wx));
-    r[8] = fsub(1.0f, fmul(2.0f, fadd(xx, yy)));
+    quat_rot_f32(pz + 3, r);
     const float fr = __fdiv_rn((float)k + 0.5f, 32.0f);
     const float cx = fadd(cc.x0, fmul((float)i, cc.xs));
     const float cy = fadd(cc.y0, fmul((float)j, cc.ys));

@@ -52,6 +52,18 @@ def test_host_only_entry_points(libnbt):
     assert L.nbt_workspace_size(-1, C.byref(cam), C.byref(b)) == -1
     bad = libnbt.camera(0, 120, 1.0, 0.8, 1.0)
     assert L.nbt_workspace_size(4, C.byref(bad), C.byref(b)) == -1
+    h = C.c_void_p()
+    assert L.nbt_id_buffer_create(0, 10, C.byref(h)) == -1        # N_B out of range
+    assert L.nbt_id_buffer_create(33, 10, C.byref(h)) == -1
+    assert L.nbt_id_buffer_create(10, 0, C.byref(h)) == -1        # no perspectives
+    assert L.nbt_id_buffer_create(10, 10, None) == -1
+    assert L.nbt_id_buffer_destroy(None) == 0
+    assert L.nbt_id_buffer_clear(None) == -1
+    assert L.nbt_id_buffer_count(None, None) == -1
+    assert L.nbt_idw_gain(None, None, 0, 2.0, None, None) == -1
+    prm = _lib.CostParams(2.0, 1.0, 1e-7)
+    poi = (C.c_float * 3)(0.0, 0.0, 0.0)
+    assert L.nbt_ig_cost(None, None, 0, None, 0, poi, 1.0, 1.0, C.byref(prm), None, None, None, None, None) == -1
 
 
 def test_structs_match_header_sizes():
@@ -60,6 +72,7 @@ def test_structs_match_header_sizes():
     assert C.sizeof(_lib.Camera) == 28
     assert C.sizeof(_lib.IgParams) == 20
     assert C.sizeof(_lib.Tuning) == 8
+    assert C.sizeof(_lib.CostParams) == 12
 
 
 def test_product_package_does_not_touch_the_oracle():

@@ -18,6 +18,11 @@ Names (sizes in the name, as the workloads are referred to everywhere):
   128 x 96 rays; per-trajectory IG = sum of per-pose IG.
 * ``room512``  : 512^3 2-bit states, room of 2000 primitives, 40 % unknown;
   8 PoIs x 4096 views; 320 x 240 rays.
+* ``idw_cost`` : IG cost of candidate trajectories (no map): a buffer of
+  N_B = 10 IDs of N_P = 500 perspectives each (Eq. 1 in a ball of r_S = 1 m
+  around the PoI; the paper's Section IV settings), and 16,384 candidate
+  trajectories of 31 states (a 3 s horizon at 0.1 s steps), camera
+  orientation jittered up to 40 degrees off the PoI.
 """
 
 from __future__ import annotations
@@ -115,6 +120,52 @@ def room512(seed: int = 0, n_pois: int = 8, views_per_poi: int = 4096, n: int = 
     poses = np.concatenate([_poses.shell_views(p, views_per_poi, 0.3, 0.8, seed + 1 + k)
                             for k, p in enumerate(pois)])
     return Workload("room512", n, "u2", "count", Camera(320, 240), grid, poses, pois)
+
+
+@dataclass
+class CostWorkload:
+    name: str
+    ids: list                          # [(poses (N_P, 7) float32, g (N_P,) float32)], oldest first
+    n_b: int
+    poses: np.ndarray                  # (n_traj * horizon, 7) float32 candidate states
+    offsets: np.ndarray                # (n_traj + 1,) int32
+    poi: np.ndarray                    # (3,) float32
+    fov_h_deg: float = 60.0
+    fov_v_deg: float = 45.0
+    power: float = 2.0
+    w_info: float = 1.0
+    eps: float = 1e-7
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def fov_h(self) -> float:
+        return float(np.float32(math.radians(self.fov_h_deg)))
+
+    @property
+    def fov_v(self) -> float:
+        return float(np.float32(math.radians(self.fov_v_deg)))
+
+
+def id_gains(pos: np.ndarray, poi, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Synthetic mean ray IGs of perspectives at ``pos``: highest on a shell
+    around the PoI, varying with azimuth, plus uniform noise (all >= 0)."""
+    rng = np.random.default_rng(seed)
+    v = pos - np.asarray(poi, np.float64)[None, :]
+    r = np.linalg.norm(v, axis=1)
+    phi = np.arctan2(v[:, 1], v[:, 0])
+    g = 30.0 * np.exp(-((r - 0.6) / 0.3) ** 2) * (0.75 + 0.25 * np.cos(2.0 * phi)) + rng.uniform(0.0, 2.0, len(r))
+    return (scale * g).astype(np.float32)
+
+
+def idw_cost(seed: int = 0, n_traj: int = 16384, horizon: int = 31, n_ids: int = 10, n_p: int = 500,
+             n_b: int = 10, jitter_deg: float = 40.0) -> CostWorkload:
+    poi = np.array([0.8, 0.7, 0.5], np.float32)
+    ids = []
+    for m in range(n_ids):
+        pz = _poses.ball_views(poi.astype(np.float64), n_p, 1.0, seed * 1000 + m)
+        ids.append((pz, id_gains(pz[:, :3].astype(np.float64), poi, seed * 1000 + 500 + m, 0.7 + 0.03 * m)))
+    poses, offsets = _traj.horizon_trajectories(poi, n_traj, horizon, seed, jitter_deg=jitter_deg)
+    return CostWorkload("idw_cost", ids, n_b, poses, offsets, poi, meta={"horizon": horizon, "n_p": n_p})
 
 
 WORKLOADS = {"exact64": exact64, "prob256": prob256, "traj256": traj256, "room512": room512}

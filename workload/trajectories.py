@@ -64,3 +64,48 @@ def random_trajectories(pois, n_traj: int, seed: int, len_range=(5, 40), r_min: 
     rot = np.concatenate(all_rot)
     poses = make_poses(pos, rotation_to_quaternion(rot))
     return poses, offsets.astype(np.int32)
+
+
+def horizon_trajectories(poi, n_traj: int, horizon: int, seed: int, r_min: float = 0.3, r_max: float = 0.8,
+                         jitter_deg: float = 40.0):
+    """``n_traj`` candidate trajectories of exactly ``horizon`` states around one PoI.
+
+    The same construction as ``random_trajectories`` (spline of the
+    direction and of the radius through four control points; look-at
+    orientation tilted by up to ``jitter_deg`` about a random axis), drawn in
+    whole arrays so that tens of thousands of candidates take well under a
+    second.
+    """
+    rng = np.random.default_rng(seed)
+    poi = np.asarray(poi, dtype=np.float64).reshape(3)
+    d = rng.standard_normal((n_traj, 4, 3))
+    d /= np.linalg.norm(d, axis=2, keepdims=True)
+    for k in range(1, 4):
+        flip = np.sum(d[:, k] * d[:, k - 1], axis=1) < 0.0
+        d[flip, k] = -d[flip, k]
+        d[:, k] = d[:, k - 1] + 0.6 * d[:, k]
+        d[:, k] /= np.linalg.norm(d[:, k], axis=1, keepdims=True)
+    radii = rng.uniform(r_min, r_max, size=(n_traj, 4))
+    t = np.linspace(0.0, 1.0, horizon)[None, :, None]
+    u = _catmull_rom_batch(d[:, 0, None], d[:, 1, None], d[:, 2, None], d[:, 3, None], t)
+    u /= np.linalg.norm(u, axis=2, keepdims=True)
+    rr = radii[:, :, None, None]
+    r = np.clip(_catmull_rom_batch(rr[:, 0], rr[:, 1], rr[:, 2], rr[:, 3], t)[..., 0], r_min, r_max)
+    pos = (poi[None, None, :] + r[..., None] * u).reshape(-1, 3)
+    rot = look_at_rotation(pos, poi)
+    axis = rng.standard_normal((len(pos), 3))
+    axis /= np.linalg.norm(axis, axis=1, keepdims=True)
+    ang = math.radians(jitter_deg) * rng.random(len(pos))
+    K = np.zeros((len(pos), 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -axis[:, 2], axis[:, 1], -axis[:, 0]
+    K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = axis[:, 2], -axis[:, 1], axis[:, 0]
+    tilt = np.eye(3)[None] + np.sin(ang)[:, None, None] * K + (1.0 - np.cos(ang))[:, None, None] * (K @ K)
+    rot = rot @ tilt
+    poses = make_poses(pos, rotation_to_quaternion(rot))
+    offsets = (np.arange(n_traj + 1) * horizon).astype(np.int32)
+    return poses, offsets
+
+
+def _catmull_rom_batch(p0, p1, p2, p3, t):
+    return 0.5 * ((2.0 * p1) + (-p0 + p2) * t + (2.0 * p0 - 5.0 * p1 + 4.0 * p2 - p3) * t * t
+                  + (-p0 + 3.0 * p1 - 3.0 * p2 + p3) * t * t * t)
