@@ -50,9 +50,9 @@ def describe(w) -> str:
     }.get(w.name, w.name)
 
 
-def kernel_hash() -> str:
+def kernel_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -69,7 +69,7 @@ def ncu_traffic(workload: str):
     if not os.path.exists(TRAFFIC_FILE):
         return None
     t = json.load(open(TRAFFIC_FILE)).get(workload)
-    if not t or t.get("kernel_hash") != kernel_hash():
+    if not t or t.get("kernel_hash") != kernel_hash(t.get("sources", KERNEL_SOURCES)):
         return None
     return t.get("bytes_per_launch")
 
@@ -535,9 +535,11 @@ def run_cost(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
     pairs = n_states * sum(len(g) for _, g in w.ids)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def step(k, poses, off):
+    def step(k, poses, off, mid=None):
         pz, g = id_dev[k % len(id_dev)]
         buf.push(pz, g, stream)
+        if mid is not None:
+            mid.record(stream)
         return nbt.ig_cost(buf, poses, off, w.poi, w.fov_h, w.fov_v, w.w_info, w.power, w.eps, stream=stream)
 
     def barrier():
@@ -548,19 +550,21 @@ def run_cost(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
 
     for k in range(max(args.warmup, 3)):
         step(k, poses_dev, off_dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
     for k in range(args.steps):
         flush.fill_(k & 0xFF)
-        a, c = ev[k]
+        a, b, c = ev[k]
         a.record(stream)
-        step(k, poses_dev, off_dev)
+        step(k, poses_dev, off_dev, b)
         c.record(stream)
     barrier()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(c) for a, c in ev]
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    cost_ms = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
     total_ms = float(sum(step_ms))
     if dist is not None:
         t = torch.tensor([total_ms], device=dev)
@@ -573,7 +577,7 @@ def run_cost(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
     e_ms = []
     for k in range(args.steps):
         flush.fill_(k & 0xFF)
-        a, c = ev[k]
+        a, _, c = ev[k]
         a.record(stream)
         poses_dev.copy_(poses_host, non_blocking=True)
         off_dev.copy_(off_host, non_blocking=True)
@@ -582,9 +586,8 @@ def run_cost(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
         c.synchronize()
         e_ms.append(a.elapsed_time(c))
     e2e_total = float(sum(e_ms))
-    mean_s = total_ms * 1e-3 / args.steps
     peak = MUFU_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9   # Gpair/s at one MUFU op per pair
-    achieved = pairs / mean_s / 1e9
+    achieved = pairs / (cost_ms * 1e-3) / 1e9
     states_total = world * n_states * args.steps
     line = {
         "metric": COST_METRIC, "value": states_total / (total_ms * 1e-3), "unit": "states/s", "n_gpus": world,
@@ -594,11 +597,13 @@ def run_cost(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
                    "ids": len(w.ids), "perspectives_per_id": len(w.ids[0][1]), "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "step": "nbt_id_buffer_push (newest ID) + nbt_ig_cost (IDW/orientation/term kernel + reduce)"},
-        "pairs_per_step": pairs,
+        "pairs_per_step": pairs, "ig_cost_ms": cost_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "idw_kernel (+cost_reduce, id_push)",
-                     "algorithmic": f"1 MUFU reciprocal per (state, perspective) pair x {pairs} pairs",
-                     "peak_kind": f"derived: {MUFU_PER_CLK_PER_SM} MUFU/clk/SM x {SM_COUNT} SMs x {SM_MAX_MHZ} MHz"},
+                     "traffic": ncu_traffic("idw_cost"), "kernel": "idw_kernel (+cost_reduce)",
+                     "algorithmic": f"1 MUFU reciprocal and 8 FP32 lane ops per (state, perspective) pair x {pairs} "
+                                    "pairs",
+                     "peak_kind": f"derived: {MUFU_PER_CLK_PER_SM} MUFU/clk/SM (= 128 FP32 lanes / 8) x {SM_COUNT} "
+                                  f"SMs x {SM_MAX_MHZ} MHz"},
         "e2e": {"value": states_total / (e2e_total * 1e-3), "unit": "states/s",
                 "h2d_bytes_per_step": int(poses_host.numel() * 4 + off_host.numel() * 4),
                 "d2h_bytes_per_step": int(cost_host.numel() * 4)},

@@ -12,8 +12,10 @@
 // pad adds nothing to either sum.
 //
 // The query kernel is arithmetic-bound: per (query, perspective) pair it
-// issues about five instructions and one MUFU reciprocal (p = 2), with the
-// perspectives staged through shared memory and broadcast to the warp.
+// needs eight FP32 lane operations (four packed f32x2 instructions per two
+// pairs) and one MUFU reciprocal (p = 2); both give the same ceiling of
+// 16 pairs per clock per SM.  The perspectives are staged through shared
+// memory and broadcast to the warp.
 
 #include <cuda_runtime.h>
 
@@ -33,7 +35,7 @@ constexpr int kMaxIds = 32;
 constexpr int kBlock = 64;         // perspectives per FP32 lane-sum block (32 per f32x2 lane)
 constexpr int kTile = 512;         // perspectives staged in shared memory per pass
 constexpr int kIdwThreads = 128;
-constexpr int kQ = 2;              // queries per thread
+constexpr int kQ = 1;              // queries per thread
 
 struct IdSet {
   const float4 *slots;
