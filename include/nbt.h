@@ -153,6 +153,19 @@ int nbt_map_upload(nbt_map map, const void *src, int64_t bytes, int32_t src_on_d
 /* Description and device bytes held by the map (either output may be NULL). */
 int nbt_map_info(nbt_map map, nbt_map_desc *desc, int64_t *device_bytes);
 
+/* The paper's endpoint grid for grid factor s_G (Section III "Endpoint
+ * Calculation": corner rays on the far plane at d_Cam, grid spacing
+ * s_G * s_Vox): fills *cam with fov_h, fov_v, max_range, corner grid mode,
+ * planar range and
+ *   width  = max(2, floor((2 d_h) / (s_G s_Vox)) + 1),  d_h = d_Cam tan(fov_h / 2),
+ *   height = max(2, floor((2 d_v) / (s_G s_Vox)) + 1),  d_v = d_Cam tan(fov_v / 2),
+ * evaluated in FP64 from the float arguments: the densest grid whose
+ * spacing is not finer than s_G s_Vox.  Host only.  Errors: NBT_EINVAL
+ * (an argument not finite and positive, a FoV not below pi, a side above
+ * 65535). */
+int nbt_camera_from_grid_scale(float fov_h, float fov_v, float max_range, float voxel_size, float grid_scale,
+                               nbt_camera *cam);
+
 /* Device workspace, in bytes, that nbt_views_ig / nbt_traj_ig need for
  * n_poses perspectives of camera `cam` (per-tile partial sums).  The caller
  * allocates it (any device allocator) and passes it to those calls; it may

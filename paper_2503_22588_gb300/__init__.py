@@ -6,7 +6,7 @@ Distribution) as hand-written sm_103a CUDA kernels behind a C ABI
 """
 
 from ._lib import LibraryMissing, NbtError, lib  # noqa: F401
-from .api import (Map, TrajPlan, camera, ig_params, trace_segments, traj_ig, view_segments,  # noqa: F401
+from .api import (Map, TrajPlan, camera, camera_from_grid_scale, ig_params, trace_segments, traj_ig, view_segments,  # noqa: F401
                   views_ig, views_ig_noalloc, workspace, workspace_size)
 from .autotune import autotune  # noqa: F401
 from . import surrogate  # noqa: F401

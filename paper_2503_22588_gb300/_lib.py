@@ -61,6 +61,7 @@ SIGNATURES = {
     "nbt_map_upload": (C.c_int, [_vp, _vp, _i64, _i32, _vp]),
     "nbt_map_info": (C.c_int, [_vp, P(MapDesc), P(C.c_int64)]),
     "nbt_workspace_size": (C.c_int, [_i64, P(Camera), P(C.c_int64)]),
+    "nbt_camera_from_grid_scale": (C.c_int, [_f, _f, _f, _f, _f, P(Camera)]),
     "nbt_views_ig": (C.c_int, [_vp, _vp, _i64, P(Camera), P(IgParams), _vp, _vp, _vp, _i64, _vp]),
     "nbt_traj_ig": (C.c_int, [_vp, _vp, _i64, _vp, _i32, P(Camera), P(IgParams), _vp, _vp, _vp, _i64, _vp]),
     "nbt_trace_segments": (C.c_int, [_vp, _vp, _vp, _i32, P(IgParams), _vp, _i32, _vp, _vp]),

@@ -40,6 +40,15 @@ def camera(width: int, height: int, fov_h: float, fov_v: float, max_range: float
                   RANGE[range_mode])
 
 
+def camera_from_grid_scale(fov_h: float, fov_v: float, max_range: float, voxel_size: float,
+                           grid_scale: float) -> Camera:
+    """nbt_camera_from_grid_scale: the paper's corner-to-corner endpoint grid with spacing s_G * s_Vox."""
+    cam = Camera()
+    check(lib().nbt_camera_from_grid_scale(float(fov_h), float(fov_v), float(max_range), float(voxel_size),
+                                           float(grid_scale), C.byref(cam)), "nbt_camera_from_grid_scale")
+    return cam
+
+
 def ig_params(metric: str = "count", occ_threshold: float = 0.7, free_threshold: float = 0.3,
               include_hit: bool = True, reduce: str = "sum") -> IgParams:
     """nbt_ig_params: metric 'count' | 'eq2' | 'entropy', reduce 'sum' | 'mean'."""

@@ -20,6 +20,8 @@
 
 #include <math.h>
 
+#include <cmath>
+
 #include <algorithm>
 
 #include "nbt_internal.cuh"
@@ -376,10 +378,20 @@ template <int KIND, bool HIT, bool LINEAR>
 int launch_tiles_t(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
                    void *workspace, cudaStream_t stream) {
   const size_t smem = LINEAR ? 0 : tile_smem(map);
+  // Resident CTAs per SM: fixed per device for the linear layout (no dynamic
+  // shared memory), so it is queried once per device; bricked layouts query
+  // it for their table size.
+  static int linear_per_sm[64] = {0};
   int per_sm = 0;
-  NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ig_tiles_kernel<KIND, HIT, LINEAR>, kThreads,
-                                                             smem));
-  per_sm = std::max(per_sm, 1);
+  const int dev = map->device;
+  if (LINEAR && dev >= 0 && dev < 64 && linear_per_sm[dev] > 0) {
+    per_sm = linear_per_sm[dev];
+  } else {
+    NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ig_tiles_kernel<KIND, HIT, LINEAR>,
+                                                               kThreads, smem));
+    per_sm = std::max(per_sm, 1);
+    if (LINEAR && dev >= 0 && dev < 64) linear_per_sm[dev] = per_sm;
+  }
   const int64_t grid = std::min<int64_t>(n_items, (int64_t)sm_count() * per_sm);
   unsigned long long *queue = (unsigned long long *)workspace;
   Partial *partials = (Partial *)((char *)workspace + 256);
@@ -445,6 +457,32 @@ int run_tiles(nbt_map map, const nbt_pose *poses, int64_t n_poses, const nbt_cam
 using namespace nbt;
 
 extern "C" {
+
+int nbt_camera_from_grid_scale(float fov_h, float fov_v, float max_range, float voxel_size, float grid_scale,
+                               nbt_camera *cam) {
+  if (!cam) return NBT_EINVAL;
+  const float args[5] = {fov_h, fov_v, max_range, voxel_size, grid_scale};
+  for (float a : args)
+    if (!std::isfinite(a) || !(a > 0.0f)) return NBT_EINVAL;
+  if (!(fov_h < 3.14159265f) || !(fov_v < 3.14159265f)) return NBT_EINVAL;
+  const double step = (double)grid_scale * (double)voxel_size;
+  int32_t side[2];
+  const float fovs[2] = {fov_h, fov_v};
+  for (int a = 0; a < 2; ++a) {
+    const double half = (double)max_range * std::tan((double)fovs[a] * 0.5);
+    const double n = std::floor((2.0 * half) / step) + 1.0;
+    if (!(n <= 65535.0)) return NBT_EINVAL;
+    side[a] = std::max(2, (int32_t)n);
+  }
+  cam->width = side[0];
+  cam->height = side[1];
+  cam->fov_h = fov_h;
+  cam->fov_v = fov_v;
+  cam->max_range = max_range;
+  cam->grid_mode = NBT_GRID_CORNERS;
+  cam->range_mode = NBT_RANGE_PLANAR;
+  return NBT_OK;
+}
 
 int nbt_workspace_size(int64_t n_poses, const nbt_camera *cam, int64_t *bytes) {
   if (!bytes || n_poses < 0 || !valid_camera(cam)) return NBT_EINVAL;

@@ -83,3 +83,25 @@ def test_product_package_does_not_touch_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 for bad in ("import oracle", "from oracle", "liborc", "nbt_oracle"):
                     assert bad not in text, (f, bad)
+
+
+def test_grid_scale_camera_matches_the_oracle(libnbt):
+    """Host-only entry point: the paper's s_G endpoint grid, against oracle/endpoints.py."""
+    import math
+    import numpy as np
+    from oracle import endpoints as E
+    rng = np.random.default_rng(1)
+    cases = [(math.radians(60), math.radians(45), 1.0, 0.01, g) for g in (1, 5, 10, 20, 50, 100, 200)]
+    cases += [tuple(rng.uniform(0.2, 2.5, 2)) + (rng.uniform(0.2, 5.0), 0.01, rng.uniform(1.0, 300.0))
+              for _ in range(200)]
+    for fh, fv, d, sv, sg in cases:
+        cam = libnbt.camera_from_grid_scale(fh, fv, d, sv, sg)
+        assert (cam.width, cam.height) == E.grid_size(fh, fv, d, sv, sg), (fh, fv, d, sv, sg)
+        assert cam.grid_mode == 0 and cam.range_mode == 0
+        assert abs(cam.fov_h - fh) <= 1e-6 * fh and cam.max_range == np.float32(d)
+    from paper_2503_22588_gb300 import NbtError
+    import pytest as _pt
+    for bad in ((0.0, 1.0, 1.0, 0.01, 5.0), (1.0, 3.2, 1.0, 0.01, 5.0), (1.0, 1.0, 1.0, 0.01, -1.0),
+                (1.0, 1.0, float("nan"), 0.01, 5.0), (3.0, 1.0, 100.0, 0.0001, 0.01)):
+        with _pt.raises(NbtError):
+            libnbt.camera_from_grid_scale(*bad)

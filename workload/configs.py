@@ -18,6 +18,10 @@ Names (sizes in the name, as the workloads are referred to everywhere):
   128 x 96 rays; per-trajectory IG = sum of per-pose IG.
 * ``room512``  : 512^3 2-bit states, room of 2000 primitives, 40 % unknown;
   8 PoIs x 4096 views; 320 x 240 rays.
+* ``fig3`` (``fig3_scene``): the paper-exact ID on the prob256 tabletop --
+  N_P perspectives from Eq. 1 in a ball of r_S = 1 m around the PoI, the
+  endpoint grid of grid factor s_G (Section III), Eq. 2, mean per
+  perspective -- swept over s_G x N_P like the paper's Fig. 3.
 * ``idw_cost`` : IG cost of candidate trajectories (no map): a buffer of
   N_B = 10 IDs of N_P = 500 perspectives each (Eq. 1 in a ball of r_S = 1 m
   around the PoI; the paper's Section IV settings), and 16,384 candidate
@@ -120,6 +124,23 @@ def room512(seed: int = 0, n_pois: int = 8, views_per_poi: int = 4096, n: int = 
     poses = np.concatenate([_poses.shell_views(p, views_per_poi, 0.3, 0.8, seed + 1 + k)
                             for k, p in enumerate(pois)])
     return Workload("room512", n, "u2", "count", Camera(320, 240), grid, poses, pois)
+
+
+FIG3_GRID_SCALES = (1, 5, 10, 20, 50, 100, 200)
+FIG3_VIEW_COUNTS = (100, 250, 500, 1000)
+
+
+def fig3_scene(seed: int = 0, n: int = 256, n_prims: int = 200):
+    """The paper-exact ID setting on the tabletop: (grid, PoI, perspectives for N_P = 1000).
+
+    FP32 probability tabletop (the ``prob256`` scene), PoI at the map centre,
+    perspectives drawn with Eq. 1 in the ball of r_S = 1 m around it and
+    looking at it (the first N_P rows are the N_P-perspective ID).
+    """
+    grid = _scenes.tabletop_probabilities(n, n_prims, seed)
+    poi = np.full(3, n * VOXEL / 2)
+    poses = _poses.ball_views(poi, max(FIG3_VIEW_COUNTS), 1.0, seed)
+    return grid, poi, poses
 
 
 @dataclass
