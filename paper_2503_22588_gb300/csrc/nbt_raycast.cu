@@ -175,11 +175,63 @@ __device__ __forceinline__ void ray_ig(const void *payload, const int32_t *tab, 
   if (LINEAR) steps += (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
 }
 
+// Latency-bound variant of ray_ig (linear layout): the walk runs K voxels
+// ahead of the reads -- it records K addresses, issues the K loads back to
+// back, then consumes them in order -- so a ray waits for memory once per K
+// steps instead of once per step.  Same visit order and the same sums as
+// ray_ig; up to K - 1 voxels past the occluding one are walked and read but
+// not used.  Used when there are too few rays to hide the per-step latency.
+template <int KIND, bool HIT, int K>
+__device__ __forceinline__ void ray_ig_chunked(const void *payload, uint32_t addr_max, int nx, int ny, int nz,
+                                               const float o[3], const float d[3], float &facc, uint32_t &iacc,
+                                               uint32_t &steps) {
+  Walk w;
+  if (!walk_init(w, o, d, nx, ny, nz)) return;
+  walk_linear_steps(w, nx, ny);
+  int lin = walk_linear_index(w, nx, ny);
+  bool alive = true;  // the walk has a current voxel not yet recorded
+  for (;;) {
+    uint32_t a[K], r[K];
+    int n = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      a[k] = min((uint32_t)lin, addr_max);
+      if (alive) {
+        n = k + 1;
+        alive = walk_advance_lin(w, lin);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) r[k] = k < n ? raw_load<KIND>(payload, a[k]) : 0u;
+    bool stop = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (k < n && !stop) {
+        steps += 1u;
+        bool occ;
+        if (KIND == PAYLOAD_GAIN_F32) {
+          occ = (int32_t)r[k] < 0;
+          const float g = fabsf(__uint_as_float(r[k]));
+          if (HIT || !occ) facc += g;
+        } else {
+          uint32_t st = r[k];
+          if (KIND == PAYLOAD_U2) st = (st >> ((a[k] & 3u) << 1)) & 3u;
+          occ = st >= 2u;
+          iacc += st == 0u ? 1u : 0u;
+        }
+        stop = occ;
+      }
+    }
+    if (stop || !alive) break;
+  }
+}
+
 // Items = (pose, 32 x 8 ray tile).  A CTA takes one item at a time; warp w
 // casts packet w of the tile; the 8 packet sums are added in warp order
-// into partials[item].
-template <int KIND, bool HIT, bool LINEAR>
-__global__ void __launch_bounds__(kThreads, LINEAR ? 6 : 5)
+// into partials[item].  CHUNK > 0 (linear layout only) walks CHUNK voxels
+// ahead of the reads (ray_ig_chunked).
+template <int KIND, bool HIT, bool LINEAR, int CHUNK>
+__global__ void __launch_bounds__(kThreads, CHUNK ? 4 : (LINEAR ? 6 : 5))
     ig_tiles_kernel(DevMap m, CamConst cc, const float *__restrict__ poses, int64_t n_items, uint32_t addr_max,
                     unsigned long long *queue, Partial *partials) {
   extern __shared__ int32_t stab[];
@@ -217,7 +269,10 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 6 : 5)
     if (i < cc.W && j < cc.H) {
       float o[3], d[3];
       ray_segment(cc, s_pose, i, j, o, d);
-      ray_ig<KIND, HIT, LINEAR>(m.payload, stab, addr_max, m.nx, m.ny, m.nz, o, d, facc, iacc, steps);
+      if constexpr (CHUNK > 0)
+        ray_ig_chunked<KIND, HIT, CHUNK>(m.payload, addr_max, m.nx, m.ny, m.nz, o, d, facc, iacc, steps);
+      else
+        ray_ig<KIND, HIT, LINEAR>(m.payload, stab, addr_max, m.nx, m.ny, m.nz, o, d, facc, iacc, steps);
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
@@ -374,32 +429,59 @@ size_t tile_smem(nbt_map map) { return (size_t)(map->desc.nx + map->desc.ny + ma
 
 uint32_t addr_max_of(nbt_map map) { return (uint32_t)(map->elems - 1); }
 
-template <int KIND, bool HIT, bool LINEAR>
+// Resident CTAs per SM of one tile-kernel instantiation: queried once per
+// device for the linear layout (no dynamic shared memory), per call for
+// bricked layouts (their table size varies).
+template <int KIND, bool HIT, bool LINEAR, int CHUNK>
+int tiles_per_sm(nbt_map map, size_t smem, int *per_sm) {
+  static int cached[64] = {0};
+  const int dev = map->device;
+  if (LINEAR && dev >= 0 && dev < 64 && cached[dev] > 0) {
+    *per_sm = cached[dev];
+    return NBT_OK;
+  }
+  int n = 0;
+  NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ig_tiles_kernel<KIND, HIT, LINEAR, CHUNK>, kThreads,
+                                                             smem));
+  *per_sm = std::max(n, 1);
+  if (LINEAR && dev >= 0 && dev < 64) cached[dev] = *per_sm;
+  return NBT_OK;
+}
+
+template <int KIND, bool HIT, bool LINEAR, int CHUNK>
 int launch_tiles_t(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
                    void *workspace, cudaStream_t stream) {
   const size_t smem = LINEAR ? 0 : tile_smem(map);
-  // Resident CTAs per SM: fixed per device for the linear layout (no dynamic
-  // shared memory), so it is queried once per device; bricked layouts query
-  // it for their table size.
-  static int linear_per_sm[64] = {0};
-  int per_sm = 0;
-  const int dev = map->device;
-  if (LINEAR && dev >= 0 && dev < 64 && linear_per_sm[dev] > 0) {
-    per_sm = linear_per_sm[dev];
-  } else {
-    NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ig_tiles_kernel<KIND, HIT, LINEAR>,
-                                                               kThreads, smem));
-    per_sm = std::max(per_sm, 1);
-    if (LINEAR && dev >= 0 && dev < 64) linear_per_sm[dev] = per_sm;
-  }
+  int per_sm = 1;
+  int rc = tiles_per_sm<KIND, HIT, LINEAR, CHUNK>(map, smem, &per_sm);
+  if (rc != NBT_OK) return rc;
   const int64_t grid = std::min<int64_t>(n_items, (int64_t)sm_count() * per_sm);
   unsigned long long *queue = (unsigned long long *)workspace;
   Partial *partials = (Partial *)((char *)workspace + 256);
   NBT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream));
-  ig_tiles_kernel<KIND, HIT, LINEAR><<<(unsigned)grid, kThreads, smem, stream>>>(
+  ig_tiles_kernel<KIND, HIT, LINEAR, CHUNK><<<(unsigned)grid, kThreads, smem, stream>>>(
       dev_map(map, payload), cc, poses, n_items, addr_max_of(map), queue, partials);
   NBT_CUDA_TRY(cudaGetLastError());
   return NBT_OK;
+}
+
+// Voxels the latency-bound variant walks ahead of its reads.
+constexpr int kChunk = 8;
+
+// Linear layout: few rays (at most two per thread slot of the throughput
+// kernel's resident CTAs) cannot hide the per-step read latency, so they
+// take the walk-ahead kernel; more rays take the rolling one-voxel prefetch,
+// which issues fewer instructions per step.
+template <int KIND, bool HIT>
+int launch_tiles_linear(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
+                        void *workspace, cudaStream_t stream) {
+  int per_sm = 1;
+  int rc = tiles_per_sm<KIND, HIT, true, 0>(map, 0, &per_sm);
+  if (rc != NBT_OK) return rc;
+  const int64_t n_rays = n_items / cc.tiles_per_pose * cc.W * cc.H;
+  if (n_rays <= 2 * (int64_t)sm_count() * per_sm * kThreads)
+    return launch_tiles_t<KIND, HIT, true, kChunk>(map, payload, cc, poses, n_items, workspace, stream);
+  return launch_tiles_t<KIND, HIT, true, 0>(map, payload, cc, poses, n_items, workspace, stream);
 }
 
 template <int KIND>
@@ -407,10 +489,10 @@ int launch_tiles(nbt_map map, const void *payload, const CamConst &cc, const flo
                  int include_hit, void *workspace, cudaStream_t stream) {
   const bool lin = map->brick == 1;
   if (include_hit)
-    return lin ? launch_tiles_t<KIND, true, true>(map, payload, cc, poses, n_items, workspace, stream)
-               : launch_tiles_t<KIND, true, false>(map, payload, cc, poses, n_items, workspace, stream);
-  return lin ? launch_tiles_t<KIND, false, true>(map, payload, cc, poses, n_items, workspace, stream)
-             : launch_tiles_t<KIND, false, false>(map, payload, cc, poses, n_items, workspace, stream);
+    return lin ? launch_tiles_linear<KIND, true>(map, payload, cc, poses, n_items, workspace, stream)
+               : launch_tiles_t<KIND, true, false, 0>(map, payload, cc, poses, n_items, workspace, stream);
+  return lin ? launch_tiles_linear<KIND, false>(map, payload, cc, poses, n_items, workspace, stream)
+             : launch_tiles_t<KIND, false, false, 0>(map, payload, cc, poses, n_items, workspace, stream);
 }
 
 template <int KIND>

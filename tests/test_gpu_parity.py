@@ -190,6 +190,28 @@ def test_views_ig_degenerate_maps_and_poses():
     assert out.numel() == 0
 
 
+@pytest.mark.parametrize("encoding,metric", [("u8", "count"), ("u2", "count"), ("f32", "entropy"), ("f32", "eq2")])
+def test_latency_and_throughput_kernels_agree(encoding, metric):
+    """Few rays take the walk-ahead kernel, many the rolling-prefetch kernel: identical results."""
+    w = configs.exact64(seed=5, n_views=512)
+    grid = w.grid
+    if encoding == "f32":
+        grid = scenes.probabilities_from_masks(grid == 2, grid == 0, 5)
+    gm = nbt.Map.from_grid(torch.from_numpy(np.ascontiguousarray(grid)).cuda(), w.voxel_size, w.origin, encoding)
+    cam, prm = gpu_camera(w.camera), nbt.ig_params(metric)
+    p = torch.from_numpy(w.poses).cuda()
+    big_ig, big_st = nbt.views_ig(gm, p, cam, prm)                      # 1.57M rays: rolling prefetch
+    parts = [nbt.views_ig(gm, p[k:k + 32], cam, prm) for k in range(0, 512, 32)]   # 98k rays: walk-ahead
+    torch.cuda.synchronize()
+    assert torch.equal(big_ig, torch.cat([a for a, _ in parts]))
+    assert torch.equal(big_st, torch.cat([b for _, b in parts]))
+    rig, rst = oracle.views_ig(oracle.Map(grid, w.voxel_size, w.origin), w.poses[:64], oracle_camera(w.camera),
+                               oracle.params(metric), "f32", 8)
+    assert np.array_equal(big_st.cpu().numpy()[:64], rst)
+    assert rel_err(big_ig.cpu().numpy()[:64], rig).max() <= RTOL
+    gm.close()
+
+
 def test_closed_forms_on_gpu():
     """All-free map: IG 0; all-occupied: one step per ray that meets the map."""
     cam = configs.Camera(24, 18)
