@@ -1,0 +1,99 @@
+"""CPU oracle of the voxel-map update from a depth point cloud -- TEST INFRASTRUCTURE, NOT PRODUCT CODE.
+
+Section III: every captured point cloud is thinned by a voxel filter and
+inserted into the probabilistic voxel map whose states and occupancy
+probabilities P(v) the IG is computed from.  The paper names the libraries
+(PCL's voxel filter, UfoMap) but not the update; this module restates the
+standard occupancy-grid insertion in UfoMap's discrete form:
+
+* voxel filter: each point is represented by the map voxel that contains it
+  (leaf size = s_Vox); each distinct endpoint voxel inside the map is
+  observed as occupied once per scan ("hit");
+* free space: a ray from the sensor position to the centre of each point's
+  voxel (the FP32 reference walk of the IG path, clipped to the map) marks
+  every voxel it visits as observed free ("miss"), at most once per scan;
+  a voxel that is also a hit in the same scan is only a hit;
+* update of an FP32 probability map: the Bayes / log-odds update written as
+  a ratio, P' = P p / (P p + (1 - P)(1 - p)) with p = p_hit or p_miss,
+  clamped to [P_min, P_max]; state maps: hit -> occupied (2), miss -> free (1);
+* points that are not finite, or farther than max_range from the sensor
+  (when max_range > 0), are ignored.
+
+Readings (the paper is silent): p_hit 0.7, p_miss 0.4, clamping [0.1192,
+0.971] (the defaults of the OctoMap / UfoMap family); the ratio form keeps
+every step an IEEE basic operation, so this oracle and the GPU agree bit for
+bit (numpy float32 rounds every operation).  The walk is the oracle's FP32
+reference walk (``oracle.trace``), pinned separately against brute force.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import trace
+
+P_HIT, P_MISS, P_MIN, P_MAX = 0.7, 0.4, 0.1192, 0.971
+f32 = np.float32
+
+
+def update_f32(P, p, p_min=P_MIN, p_max=P_MAX):
+    """One observation with likelihood p of P, FP32 in a fixed order, clamped."""
+    P, p = f32(P), f32(p)
+    a = f32(P * p)
+    b = f32(f32(f32(1.0) - P) * f32(f32(1.0) - p))
+    q = f32(a / f32(a + b))
+    lo, hi = f32(p_min), f32(p_max)
+    return lo if q < lo else (hi if q > hi else q)
+
+
+def _voxel_units(v, origin, inv_s):
+    return [f32(f32(f32(v[a]) - f32(origin[a])) * inv_s) for a in range(3)]
+
+
+def scan_sets(points, sensor, dims, voxel_size, origin=(0.0, 0.0, 0.0), max_range=0.0):
+    """(hit set, miss set) of linear voxel indices for one scan (miss excludes hits)."""
+    nx, ny, nz = dims
+    inv_s = f32(1.0 / float(f32(voxel_size)))
+    o = _voxel_units(sensor, origin, inv_s)
+    mr2 = f32(f32(max_range) * f32(max_range))
+    hits, misses, seen = set(), set(), set()
+    for p in np.asarray(points, np.float32).reshape(-1, 3):
+        if not np.all(np.isfinite(p)):
+            continue
+        if max_range > 0:
+            dd = [f32(p[a] - f32(sensor[a])) for a in range(3)]
+            r2 = f32(f32(f32(dd[0] * dd[0]) + f32(dd[1] * dd[1])) + f32(dd[2] * dd[2]))
+            if not r2 <= mr2:
+                continue
+        q = _voxel_units(p, origin, inv_s)
+        idx = tuple(int(math.floor(float(q[a]))) for a in range(3))
+        if 0 <= idx[0] < nx and 0 <= idx[1] < ny and 0 <= idx[2] < nz:
+            hits.add((idx[2] * ny + idx[1]) * nx + idx[0])
+        if idx in seen:
+            continue          # same endpoint voxel: same ray
+        seen.add(idx)
+        d = [f32(f32(f32(idx[a]) + f32(0.5)) - o[a]) for a in range(3)]
+        misses.update(int(v) for v in trace(dims, o, d, "f32"))
+    return hits, misses - hits
+
+
+def insert(grid, points, sensor, voxel_size, origin=(0.0, 0.0, 0.0), p_hit=P_HIT, p_miss=P_MISS, p_min=P_MIN,
+           p_max=P_MAX, max_range=0.0):
+    """The map after one scan.  ``grid`` (nz, ny, nx): float32 P or uint8 states (not modified)."""
+    nz, ny, nx = grid.shape
+    hits, misses = scan_sets(points, sensor, (nx, ny, nz), voxel_size, origin, max_range)
+    out = grid.copy()
+    flat = out.reshape(-1)
+    if grid.dtype == np.float32:
+        for v in hits:
+            flat[v] = update_f32(flat[v], p_hit, p_min, p_max)
+        for v in misses:
+            flat[v] = update_f32(flat[v], p_miss, p_min, p_max)
+    else:
+        for v in hits:
+            flat[v] = 2
+        for v in misses:
+            flat[v] = 1
+    return out
