@@ -16,8 +16,9 @@ standard occupancy-grid insertion in UfoMap's discrete form:
 * update of an FP32 probability map: the Bayes / log-odds update written as
   a ratio, P' = P p / (P p + (1 - P)(1 - p)) with p = p_hit or p_miss,
   clamped to [P_min, P_max]; state maps: hit -> occupied (2), miss -> free (1);
-* points that are not finite, or farther than max_range from the sensor
-  (when max_range > 0), are ignored.
+* points that are not finite, farther than max_range from the sensor (when
+  max_range > 0), or 2^22 voxels or more from the map origin on some axis
+  (where voxel centres stop being exact in FP32), are ignored.
 
 Readings (the paper is silent): p_hit 0.7, p_miss 0.4, clamping [0.1192,
 0.971] (the defaults of the OctoMap / UfoMap family); the ratio form keeps
@@ -68,6 +69,8 @@ def scan_sets(points, sensor, dims, voxel_size, origin=(0.0, 0.0, 0.0), max_rang
             if not r2 <= mr2:
                 continue
         q = _voxel_units(p, origin, inv_s)
+        if not all(abs(float(q[a])) < 2.0 ** 22 for a in range(3)):
+            continue
         idx = tuple(int(math.floor(float(q[a]))) for a in range(3))
         if 0 <= idx[0] < nx and 0 <= idx[1] < ny and 0 <= idx[2] < nz:
             hits.add((idx[2] * ny + idx[1]) * nx + idx[0])

@@ -77,6 +77,9 @@ def test_max_range_and_non_finite_points_are_ignored():
     assert np.all(g == 0.5)
     g = I.insert(UNKNOWN, [[4.5, 1.5, 1.5]], SENSOR, 1.0, max_range=5.0)
     assert _row(g)[4] == f32(0.7)
+    assert np.all(I.insert(UNKNOWN, [[2.0 ** 22, 1.5, 1.5]], SENSOR, 1.0) == 0.5)   # too far from the origin
+    g = I.insert(UNKNOWN, [[2.0 ** 22 - 1.0, 1.5, 1.5]], SENSOR, 1.0)
+    assert np.all(_row(g) == f32(0.4))
 
 
 def test_state_maps_take_the_latest_observation():
