@@ -153,6 +153,48 @@ int nbt_map_upload(nbt_map map, const void *src, int64_t bytes, int32_t src_on_d
 /* Description and device bytes held by the map (either output may be NULL). */
 int nbt_map_info(nbt_map map, nbt_map_desc *desc, int64_t *device_bytes);
 
+/* Copy the map back out as the dense x-fastest grid nbt_map_upload takes:
+ * uint8 states (2-bit maps unpacked to 0..3) or float probabilities, into
+ * the device buffer dst of exactly nx*ny*nz elements (bytes must match).
+ * Asynchronous on stream.  Errors: NBT_EINVAL, NBT_ECUDA. */
+int nbt_map_download(nbt_map map, void *dst, int64_t bytes, void *stream);
+
+/* Occupancy update from one depth scan (Section III: every captured point
+ * cloud is voxel-filtered and inserted into the probabilistic voxel map),
+ * in the discrete form of occupancy-grid insertion:
+ *   - voxel filter: each point stands for the voxel that contains it; every
+ *     distinct such voxel inside the map is observed occupied once ("hit");
+ *   - free space: a ray from the sensor to the centre of each distinct
+ *     endpoint voxel (inside the map or not), walked with the FP32 reference
+ *     walk of nbt_trace_segments and clipped to the map, observes every voxel
+ *     it visits free ("miss"), at most once per scan; a voxel that is also a
+ *     hit in the scan takes only the hit;
+ *   - NBT_F32_PROB maps: P <- P p / (P p + (1 - P)(1 - p)) with p = prob_hit
+ *     or prob_miss, each operation rounded in FP32 in this order, then
+ *     clamped to [clamp_min, clamp_max]; state maps: hit -> 2 (occupied),
+ *     miss -> 1 (free).
+ * Points that are not finite, farther than max_range from the sensor (if
+ * max_range > 0) or 2^22 voxels or more from the map origin on an axis are
+ * ignored.  points: device float[n][3], world metres; sensor: host float[3]
+ * (within 2^22 voxels of the origin); stats_out: NULL or device uint64[3],
+ * written with the number of distinct endpoint voxels inside the map (hits),
+ * the number of rays cast and the number of voxel steps they walked.  Only the linear layout (brick 1) is
+ * supported (NBT_EUNSUPPORTED otherwise).  The map allocates its insertion
+ * scratch on the first call and when n exceeds every earlier n (two voxel
+ * bitmaps and endpoint lists; cudaMalloc synchronises); inserts into one map
+ * must be ordered on one stream.  Derived gains of an FP32 map are rebuilt
+ * before its next IG call.  Errors: NBT_EINVAL, NBT_EUNSUPPORTED,
+ * NBT_ENOMEM, NBT_ECUDA. */
+typedef struct {
+  float prob_hit;                /* p_hit in (0.5, 1), e.g. 0.7 */
+  float prob_miss;               /* p_miss in (0, 0.5), e.g. 0.4 */
+  float clamp_min, clamp_max;    /* 0 < clamp_min < clamp_max < 1, e.g. 0.1192, 0.971 */
+  float max_range;               /* metres; <= 0: no range limit */
+} nbt_insert_params;
+
+int nbt_map_insert_points(nbt_map map, const float *points, int64_t n, const float *sensor,
+                          const nbt_insert_params *params, uint64_t *stats_out, void *stream);
+
 /* The paper's endpoint grid for grid factor s_G (Section III "Endpoint
  * Calculation": corner rays on the far plane at d_Cam, grid spacing
  * s_G * s_Vox): fills *cam with fov_h, fov_v, max_range, corner grid mode,

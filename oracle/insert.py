@@ -29,8 +29,6 @@ reference walk (``oracle.trace``), pinned separately against brute force.
 
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 from . import trace
@@ -40,45 +38,40 @@ f32 = np.float32
 
 
 def update_f32(P, p, p_min=P_MIN, p_max=P_MAX):
-    """One observation with likelihood p of P, FP32 in a fixed order, clamped."""
-    P, p = f32(P), f32(p)
-    a = f32(P * p)
-    b = f32(f32(f32(1.0) - P) * f32(f32(1.0) - p))
-    q = f32(a / f32(a + b))
+    """One observation with likelihood p of P (scalar or array), FP32 in a fixed order, clamped."""
+    P, p = np.asarray(P, np.float32), f32(p)
+    a = P * p
+    b = (f32(1.0) - P) * (f32(1.0) - p)
+    q = a / (a + b)
     lo, hi = f32(p_min), f32(p_max)
-    return lo if q < lo else (hi if q > hi else q)
-
-
-def _voxel_units(v, origin, inv_s):
-    return [f32(f32(f32(v[a]) - f32(origin[a])) * inv_s) for a in range(3)]
+    return np.where(q < lo, lo, np.where(q > hi, hi, q)).astype(np.float32)
 
 
 def scan_sets(points, sensor, dims, voxel_size, origin=(0.0, 0.0, 0.0), max_range=0.0):
-    """(hit set, miss set) of linear voxel indices for one scan (miss excludes hits)."""
+    """(hit set, miss set) of linear voxel indices for one scan (miss excludes hits).
+
+    Array arithmetic: numpy rounds every float32 element operation exactly as
+    the scalar operation would.
+    """
     nx, ny, nz = dims
     inv_s = f32(1.0 / float(f32(voxel_size)))
-    o = _voxel_units(sensor, origin, inv_s)
-    mr2 = f32(f32(max_range) * f32(max_range))
-    hits, misses, seen = set(), set(), set()
-    for p in np.asarray(points, np.float32).reshape(-1, 3):
-        if not np.all(np.isfinite(p)):
-            continue
-        if max_range > 0:
-            dd = [f32(p[a] - f32(sensor[a])) for a in range(3)]
-            r2 = f32(f32(f32(dd[0] * dd[0]) + f32(dd[1] * dd[1])) + f32(dd[2] * dd[2]))
-            if not r2 <= mr2:
-                continue
-        q = _voxel_units(p, origin, inv_s)
-        if not all(abs(float(q[a])) < 2.0 ** 22 for a in range(3)):
-            continue
-        idx = tuple(int(math.floor(float(q[a]))) for a in range(3))
-        if 0 <= idx[0] < nx and 0 <= idx[1] < ny and 0 <= idx[2] < nz:
-            hits.add((idx[2] * ny + idx[1]) * nx + idx[0])
-        if idx in seen:
-            continue          # same endpoint voxel: same ray
-        seen.add(idx)
-        d = [f32(f32(f32(idx[a]) + f32(0.5)) - o[a]) for a in range(3)]
-        misses.update(int(v) for v in trace(dims, o, d, "f32"))
+    org = np.asarray(origin, np.float32)
+    o = (np.asarray(sensor, np.float32) - org) * inv_s
+    p = np.asarray(points, np.float32).reshape(-1, 3)
+    p = p[np.all(np.isfinite(p), axis=1)]
+    if max_range > 0:
+        dd = p - np.asarray(sensor, np.float32)
+        r2 = (dd[:, 0] * dd[:, 0] + dd[:, 1] * dd[:, 1]) + dd[:, 2] * dd[:, 2]
+        p = p[r2 <= f32(max_range) * f32(max_range)]
+    q = (p - org) * inv_s
+    q = q[np.all(np.abs(q) < f32(2.0 ** 22), axis=1)]
+    idx = np.unique(np.floor(q).astype(np.int64), axis=0)       # distinct endpoint voxels: one ray each
+    inside = np.all((idx >= 0) & (idx < np.array([nx, ny, nz])), axis=1)
+    hits = set(((idx[inside, 2] * ny + idx[inside, 1]) * nx + idx[inside, 0]).tolist())
+    misses = set()
+    for e in idx:
+        d = (e.astype(np.float32) + f32(0.5)) - o
+        misses.update(trace(dims, o, d, "f32").tolist())
     return hits, misses - hits
 
 
@@ -89,14 +82,12 @@ def insert(grid, points, sensor, voxel_size, origin=(0.0, 0.0, 0.0), p_hit=P_HIT
     hits, misses = scan_sets(points, sensor, (nx, ny, nz), voxel_size, origin, max_range)
     out = grid.copy()
     flat = out.reshape(-1)
+    h = np.array(sorted(hits), np.int64)
+    m = np.array(sorted(misses), np.int64)
     if grid.dtype == np.float32:
-        for v in hits:
-            flat[v] = update_f32(flat[v], p_hit, p_min, p_max)
-        for v in misses:
-            flat[v] = update_f32(flat[v], p_miss, p_min, p_max)
+        flat[h] = update_f32(flat[h], p_hit, p_min, p_max)
+        flat[m] = update_f32(flat[m], p_miss, p_min, p_max)
     else:
-        for v in hits:
-            flat[v] = 2
-        for v in misses:
-            flat[v] = 1
+        flat[h] = 2
+        flat[m] = 1
     return out

@@ -46,6 +46,11 @@ class IgParams(C.Structure):
                 ("include_hit", C.c_int32), ("reduce", C.c_int32)]
 
 
+class InsertParams(C.Structure):
+    _fields_ = [("prob_hit", C.c_float), ("prob_miss", C.c_float), ("clamp_min", C.c_float), ("clamp_max", C.c_float),
+                ("max_range", C.c_float)]
+
+
 class CostParams(C.Structure):
     _fields_ = [("power", C.c_float), ("w_info", C.c_float), ("eps", C.c_float)]
 
@@ -60,6 +65,8 @@ SIGNATURES = {
     "nbt_map_destroy": (C.c_int, [_vp]),
     "nbt_map_upload": (C.c_int, [_vp, _vp, _i64, _i32, _vp]),
     "nbt_map_info": (C.c_int, [_vp, P(MapDesc), P(C.c_int64)]),
+    "nbt_map_download": (C.c_int, [_vp, _vp, _i64, _vp]),
+    "nbt_map_insert_points": (C.c_int, [_vp, _vp, _i64, P(_f), P(InsertParams), _vp, _vp]),
     "nbt_workspace_size": (C.c_int, [_i64, P(Camera), P(C.c_int64)]),
     "nbt_camera_from_grid_scale": (C.c_int, [_f, _f, _f, _f, _f, P(Camera)]),
     "nbt_views_ig": (C.c_int, [_vp, _vp, _i64, P(Camera), P(IgParams), _vp, _vp, _vp, _i64, _vp]),

@@ -12,7 +12,7 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import ENCODINGS, GRID, METRICS, RANGE, REDUCE, Camera, IgParams, MapDesc, Tuning, check, lib
+from ._lib import ENCODINGS, GRID, METRICS, RANGE, REDUCE, Camera, IgParams, InsertParams, MapDesc, Tuning, check, lib
 
 
 def _stream(stream) -> int:
@@ -109,6 +109,30 @@ class Map:
         nbytes = C.c_int64()
         check(lib().nbt_map_info(self.handle, C.byref(desc), C.byref(nbytes)), "nbt_map_info")
         return desc, nbytes.value
+
+    def download(self, stream=None) -> torch.Tensor:
+        """nbt_map_download: the dense (nz, ny, nx) grid (uint8 states or float32 P) on the map's device."""
+        d, _ = self.info()
+        dt = torch.float32 if self.encoding == "f32" else torch.uint8
+        out = torch.empty((d.nz, d.ny, d.nx), dtype=dt, device=torch.device("cuda", torch.cuda.current_device()))
+        check(lib().nbt_map_download(self.handle, out.data_ptr(), out.numel() * out.element_size(), _stream(stream)),
+              "nbt_map_download")
+        return out
+
+    def insert_points(self, points: torch.Tensor, sensor, prob_hit: float = 0.7, prob_miss: float = 0.4,
+                      clamp_min: float = 0.1192, clamp_max: float = 0.971, max_range: float = 0.0,
+                      stats: torch.Tensor | None = None, stream=None) -> None:
+        """nbt_map_insert_points: one depth scan, points (n, 3) float32 world metres on the device.
+
+        ``stats``: optional device int64 tensor of 3, written with (distinct
+        endpoint voxels inside the map, rays cast, voxel steps walked).
+        """
+        n = points.shape[0]
+        prm = InsertParams(float(prob_hit), float(prob_miss), float(clamp_min), float(clamp_max), float(max_range))
+        s = (C.c_float * 3)(*[float(v) for v in sensor])
+        st = _dev(stats, torch.int64, "stats") if stats is not None else None
+        check(lib().nbt_map_insert_points(self.handle, _dev(points, torch.float32, "points", (3,)) if n else None, n,
+                                          s, C.byref(prm), st, _stream(stream)), "nbt_map_insert_points")
 
     def set_tuning(self, packet_w: int = 8) -> None:
         """nbt_map_set_tuning: warp ray-packet width (4, 8, 16 or 32 pixels)."""

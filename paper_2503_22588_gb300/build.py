@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libnbt.so")
-SOURCES = ["nbt_map.cu", "nbt_raycast.cu", "nbt_plan.cu", "nbt_surrogate.cu", "nbt_idw.cu"]
+SOURCES = ["nbt_map.cu", "nbt_raycast.cu", "nbt_plan.cu", "nbt_surrogate.cu", "nbt_idw.cu", "nbt_insert.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", os.path.join(ROOT, "include")]

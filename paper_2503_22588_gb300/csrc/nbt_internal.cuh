@@ -64,6 +64,14 @@ struct nbt_map_s {
   int gain_metric = -1;
   float gain_occ = 0.0f, gain_free = 0.0f;
   uint64_t gain_version = 0;
+  // point-cloud insertion scratch (nbt_map_insert_points), allocated on first use
+  uint32_t *ins_hit = nullptr;       // hit bitmap, one bit per voxel, zero between calls
+  uint32_t *ins_miss = nullptr;      // miss bitmap, likewise
+  uint32_t *ins_count = nullptr;     // [0] distinct in-map endpoints, [1] endpoints outside the map,
+                                     // [2..3] voxel steps walked (uint64)
+  uint32_t *ins_list = nullptr;      // distinct in-map endpoint voxels
+  void *ins_outside = nullptr;       // int4 voxel coordinates of endpoints outside the map
+  int64_t ins_cap = 0;               // points the lists hold
   std::mutex mu;
 };
 
@@ -322,6 +330,7 @@ int check_map(nbt_map map);
 int prepare_gain(nbt_map map, const nbt_ig_params *params, cudaStream_t stream);
 int payload_kind(nbt_map map, const nbt_ig_params *params, PayloadKind *kind, const void **payload);
 int sm_count();
+int ensure_insert_scratch(nbt_map map, int64_t n_points);  // defined in nbt_insert.cu
 
 }  // namespace nbt
 

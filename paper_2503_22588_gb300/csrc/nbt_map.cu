@@ -131,6 +131,26 @@ __global__ void pack_u2_linear_kernel(const uint8_t *__restrict__ src, uint8_t *
   }
 }
 
+// Device layout -> dense x-fastest grid (the inverse of the upload): uint8
+// states (2-bit maps unpacked) or float probabilities.
+template <int ENC>
+__global__ void gather_dense_kernel(const void *__restrict__ payload, const int32_t *__restrict__ tab, int nx, int ny,
+                                    int64_t n, void *__restrict__ dst) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx);
+    const int64_t r = k / nx;
+    const int y = (int)(r % ny);
+    const int z = (int)(r / ny);
+    const int32_t off = voxel_offset(tab, nx, ny, x, y, z);
+    if (ENC == NBT_F32_PROB)
+      ((float *)dst)[k] = ((const float *)payload)[off];
+    else if (ENC == NBT_U8_STATE)
+      ((uint8_t *)dst)[k] = ((const uint8_t *)payload)[off];
+    else
+      ((uint8_t *)dst)[k] = (uint8_t)((((const uint8_t *)payload)[off >> 2] >> ((off & 3) << 1)) & 3u);
+  }
+}
+
 __device__ __forceinline__ float entropy_bits(float p) {
   if (!(p > 0.0f && p < 1.0f)) return 0.0f;
   const float q = 1.0f - p;
@@ -333,6 +353,11 @@ int nbt_map_destroy(nbt_map map) {
   if (map->d_gain) cudaFree(map->d_gain);
   if (map->d_tab) cudaFree(map->d_tab);
   if (map->d_stage) cudaFree(map->d_stage);
+  if (map->ins_hit) cudaFree(map->ins_hit);
+  if (map->ins_miss) cudaFree(map->ins_miss);
+  if (map->ins_count) cudaFree(map->ins_count);
+  if (map->ins_list) cudaFree(map->ins_list);
+  if (map->ins_outside) cudaFree(map->ins_outside);
   (void)cudaGetLastError();
   if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
   delete map;
@@ -378,6 +403,23 @@ int nbt_map_upload(nbt_map map, const void *src, int64_t bytes, int32_t src_on_d
   }
   map->version += 1;
   map->gain_valid = false;
+  return NBT_OK;
+}
+
+int nbt_map_download(nbt_map map, void *dst, int64_t bytes, void *stream_) {
+  int rc = check_map(map);
+  if (rc != NBT_OK) return rc;
+  const nbt_map_desc &d = map->desc;
+  const int64_t n = (int64_t)d.nx * d.ny * d.nz;
+  if (!dst || bytes != n * elem_size(d.encoding)) return NBT_EINVAL;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (d.encoding == NBT_F32_PROB)
+    gather_dense_kernel<NBT_F32_PROB><<<grid_for(n), 256, 0, stream>>>(map->d_payload, map->d_tab, d.nx, d.ny, n, dst);
+  else if (d.encoding == NBT_U8_STATE)
+    gather_dense_kernel<NBT_U8_STATE><<<grid_for(n), 256, 0, stream>>>(map->d_payload, map->d_tab, d.nx, d.ny, n, dst);
+  else
+    gather_dense_kernel<NBT_U2_STATE><<<grid_for(n), 256, 0, stream>>>(map->d_payload, map->d_tab, d.nx, d.ny, n, dst);
+  NBT_CUDA_TRY(cudaGetLastError());
   return NBT_OK;
 }
 

@@ -22,6 +22,9 @@ Names (sizes in the name, as the workloads are referred to everywhere):
   N_P perspectives from Eq. 1 in a ball of r_S = 1 m around the PoI, the
   endpoint grid of grid factor s_G (Section III), Eq. 2, mean per
   perspective -- swept over s_G x N_P like the paper's Fig. 3.
+* ``insert`` (``insert_scans``): the map update -- 640 x 576 depth scans
+  (Azure Kinect NFOV geometry) of an analytic tabletop inserted into a 256^3
+  FP32 probability map of 1 cm voxels.
 * ``idw_cost`` : IG cost of candidate trajectories (no map): a buffer of
   N_B = 10 IDs of N_P = 500 perspectives each (Eq. 1 in a ball of r_S = 1 m
   around the PoI; the paper's Section IV settings), and 16,384 candidate
@@ -141,6 +144,24 @@ def fig3_scene(seed: int = 0, n: int = 256, n_prims: int = 200):
     poi = np.full(3, n * VOXEL / 2)
     poses = _poses.ball_views(poi, max(FIG3_VIEW_COUNTS), 1.0, seed)
     return grid, poi, poses
+
+
+def insert_scans(seed: int = 0, n_scans: int = 8, width: int = 640, height: int = 576):
+    """Depth scans for the map update: (scans [(sensor pose, points)], map size n, voxel size).
+
+    Azure Kinect NFOV geometry (640 x 576 pixels, 75 x 65 degrees, range
+    3.86 m, 2 mm range noise) looking at the analytic tabletop from 0.6-1.2 m
+    above it; the map is the 256^3 cube of 1 cm voxels around the table.
+    """
+    from . import sensor as _sensor
+    scene = _sensor.tabletop_scene(seed)
+    poi = np.array([1.28, 1.28, 0.8])
+    scans = []
+    for k, pose in enumerate(_sensor.scan_poses(poi, n_scans, seed)):
+        pts = _sensor.depth_points(scene, pose, width, height, math.radians(75.0), math.radians(65.0), 3.86,
+                                   0.002, seed * 100 + k)
+        scans.append((pose, pts))
+    return scans, 256, VOXEL
 
 
 @dataclass
