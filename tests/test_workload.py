@@ -94,3 +94,40 @@ def test_workload_presets_small():
     assert w.grid.shape == (64, 64, 64) and w.poses.shape == (64, 7) and w.rays_per_pose == 3072
     d = np.linalg.norm(w.poses[:, :3] - w.pois[0], axis=1)
     assert np.allclose(d, 0.5, atol=1e-6)
+
+
+def test_depth_scan_points_lie_on_the_scene_and_in_range():
+    import math
+    from workload import sensor
+    sc = sensor.tabletop_scene(2, n_objects=10)
+    poi = np.array([1.28, 1.28, 0.8])
+    pose = sensor.scan_poses(poi, 1, 4)[0]
+    pts = sensor.depth_points(sc, pose, 48, 36, math.radians(75), math.radians(65), 3.0).astype(np.float64)
+    assert len(pts) > 1000
+    o = pose[:3].astype(np.float64)
+    assert np.all(np.linalg.norm(pts - o, axis=1) <= 3.0 + 1e-5)
+    # every point is on the floor, on a box face or on a sphere (float32 rounding aside)
+    tol = 2e-5
+    on = np.abs(pts[:, 2] - sc.floor_z) < tol
+    for lo, hi in sc.boxes:
+        inside = np.all((pts >= lo - tol) & (pts <= hi + tol), axis=1)
+        face = np.any((np.abs(pts - lo) < tol) | (np.abs(pts - hi) < tol), axis=1)
+        on |= inside & face
+    for cx, cy, cz, r in sc.spheres:
+        on |= np.abs(np.linalg.norm(pts - [cx, cy, cz], axis=1) - r) < tol
+    assert on.all()
+    # points are in front of the camera, inside its field of view
+    w, x, y, z = pose[3:].astype(np.float64)
+    axis = np.array([2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)])
+    v = (pts - o) / np.linalg.norm(pts - o, axis=1, keepdims=True)
+    assert np.all(v @ axis > math.cos(math.radians(55)))
+
+
+def test_horizon_trajectories_shape_and_radii():
+    from workload import trajectories
+    poi = np.array([0.5, 0.4, 0.3])
+    p, off = trajectories.horizon_trajectories(poi, 20, 31, 0, r_min=0.3, r_max=0.8, jitter_deg=10.0)
+    assert p.shape == (620, 7) and off[0] == 0 and off[-1] == 620 and np.all(np.diff(off) == 31)
+    r = np.linalg.norm(p[:, :3] - poi, axis=1)
+    assert r.min() >= 0.3 - 1e-5 and r.max() <= 0.8 + 1e-5
+    assert np.allclose(np.linalg.norm(p[:, 3:], axis=1), 1.0, atol=1e-6)
