@@ -126,6 +126,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest per-rank value over all ranks (the slowest rank sets the job's time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, total_ms: float) -> float:
+    """Whole-job units per second: every rank processes units_per_rank in at most total_ms."""
+    return world * units_per_rank / (total_ms * 1e-3)
+
+
 def build_workload(name: str, rank: int):
     from workload import configs
     if name == "idw_cost":
@@ -352,10 +367,7 @@ def main() -> None:
     upload_ms = float(np.mean([a.elapsed_time(b) for a, b, c in ev]))
     total_ms = float(sum(step_ms))
     ig_mean_ms = float(np.mean(ig_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
 
     # end to end through the public API with host buffers: pinned host grid and
     # poses in, per-perspective IG out, copies inside the timed region
@@ -383,19 +395,15 @@ def main() -> None:
         c.synchronize()
         e_ms.append(a.elapsed_time(c))
     e2e_total = float(sum(e_ms))
-    if dist is not None:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, dist, dev)
 
     peak, peak_kind = load_peaks()
     bps = BYTES_PER_STEP[w.encoding]
     achieved = n_steps_voxel * bps / (ig_mean_ms * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload)
-    views_total = world * w.n_poses * args.steps
     line = {
         "metric": METRIC,
-        "value": views_total / (total_ms * 1e-3),
+        "value": job_throughput(w.n_poses * args.steps, world, total_ms),
         "unit": "views/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -418,7 +426,7 @@ def main() -> None:
                      "traffic": traffic, "kernel": "ig_tiles_kernel (+views_reduce)",
                      "algorithmic": f"{bps} B per voxel step x {n_steps_voxel} steps",
                      "peak_kind": f"{peak_kind} (hbm_gbs)"},
-        "e2e": {"value": views_total / (e2e_total * 1e-3), "unit": "views/s",
+        "e2e": {"value": job_throughput(w.n_poses * args.steps, world, e2e_total), "unit": "views/s",
                 "h2d_bytes_per_step": int(grid_host.numel() * grid_host.element_size()
                                           + poses_host.numel() * 4),
                 "d2h_bytes_per_step": int(ig_host.numel() * 4)},
@@ -475,10 +483,7 @@ def run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist) -> None
     clk = clocks.stop()
     total_ms = float(sum(a.elapsed_time(c) for a, b, c in ev))
     ig_ms = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     # end to end: host grid, poses and offsets in, trajectory IG out
     grid_host = torch.from_numpy(np.ascontiguousarray(w.grid)).pin_memory()
     poses_host = torch.from_numpy(w.poses).pin_memory()
@@ -497,11 +502,11 @@ def run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist) -> None
         c.synchronize()
         e_ms.append(a.elapsed_time(c))
     e2e_total = float(sum(e_ms))
+    e2e_total = max_over_ranks(e2e_total, dist, dev)
     peak, peak_kind = load_peaks()
     bps = BYTES_PER_STEP[w.encoding]
-    poses_total = world * w.n_poses * args.steps
     line = {
-        "metric": METRIC, "value": poses_total / (total_ms * 1e-3), "unit": "views/s", "n_gpus": world,
+        "metric": METRIC, "value": job_throughput(w.n_poses * args.steps, world, total_ms), "unit": "views/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": describe(w), "poses_per_gpu": w.n_poses, "trajectories": len(w.offsets) - 1,
@@ -515,7 +520,7 @@ def run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist) -> None
                      "traffic": ncu_traffic(args.workload), "kernel": "ig_tiles_kernel (+traj_reduce)",
                      "algorithmic": f"{bps} B per voxel step x {n_steps_voxel} steps",
                      "peak_kind": f"{peak_kind} (hbm_gbs)"},
-        "e2e": {"value": poses_total / (e2e_total * 1e-3), "unit": "views/s",
+        "e2e": {"value": job_throughput(w.n_poses * args.steps, world, e2e_total), "unit": "views/s",
                 "h2d_bytes_per_step": int(grid_host.numel() + poses_host.numel() * 4 + off_host.numel() * 4),
                 "d2h_bytes_per_step": int(out_host.numel() * 4)},
         "gpu_launches": 3 * args.steps,
@@ -573,10 +578,7 @@ def run_cost(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     cost_ms = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
     total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     # end to end: pinned host poses and offsets in, per-trajectory cost out
     poses_host = torch.from_numpy(w.poses).pin_memory()
     off_host = torch.from_numpy(w.offsets).pin_memory()
@@ -593,11 +595,11 @@ def run_cost(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
         c.synchronize()
         e_ms.append(a.elapsed_time(c))
     e2e_total = float(sum(e_ms))
+    e2e_total = max_over_ranks(e2e_total, dist, dev)
     peak = MUFU_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9   # Gpair/s at one MUFU op per pair
     achieved = pairs / (cost_ms * 1e-3) / 1e9
-    states_total = world * n_states * args.steps
     line = {
-        "metric": COST_METRIC, "value": states_total / (total_ms * 1e-3), "unit": "states/s", "n_gpus": world,
+        "metric": COST_METRIC, "value": job_throughput(n_states * args.steps, world, total_ms), "unit": "states/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": describe(w), "states_per_gpu": n_states, "trajectories": n_traj,
@@ -611,7 +613,7 @@ def run_cost(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
                                     "pairs",
                      "peak_kind": f"derived: {MUFU_PER_CLK_PER_SM} MUFU/clk/SM (= 128 FP32 lanes / 8) x {SM_COUNT} "
                                   f"SMs x {SM_MAX_MHZ} MHz"},
-        "e2e": {"value": states_total / (e2e_total * 1e-3), "unit": "states/s",
+        "e2e": {"value": job_throughput(n_states * args.steps, world, e2e_total), "unit": "states/s",
                 "h2d_bytes_per_step": int(poses_host.numel() * 4 + off_host.numel() * 4),
                 "d2h_bytes_per_step": int(cost_host.numel() * 4)},
         "gpu_launches": 3 * args.steps,
@@ -783,10 +785,7 @@ def run_insert(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
     clk = clocks.stop()
     ms = [a.elapsed_time(c) for a, c in ev]
     total_ms = float(sum(ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     sh = st_hist.cpu().numpy()
     points = sum(len(scans[k % len(scans)][1]) for k in range(args.steps))
     # end to end: points from pinned host memory, the scan statistics back to the host
@@ -805,13 +804,14 @@ def run_insert(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
         c.synchronize()
         e_ms.append(a.elapsed_time(c))
     e2e_total = float(sum(e_ms))
+    e2e_total = max_over_ranks(e2e_total, dist, dev)
     peak, peak_kind = load_peaks()
     mean_s = total_ms * 1e-3 / args.steps
     steps_walked = float(sh[:, 2].mean())
     algo_bytes = points / args.steps * 12.0 + steps_walked * 4.0 + 2 * (n ** 3 / 8) * 2
     achieved = algo_bytes / mean_s / 1e9
     line = {
-        "metric": INSERT_METRIC, "value": world * points / (total_ms * 1e-3), "unit": "points/s", "n_gpus": world,
+        "metric": INSERT_METRIC, "value": job_throughput(points, world, total_ms), "unit": "points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "insert: 640x576 depth scans (Azure Kinect NFOV geometry, 75x65 deg, 3.86 m, 2 mm "
@@ -825,7 +825,7 @@ def run_insert(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
                      "traffic": None, "kernel": "nbt_map_insert_points (free_rays_kernel dominant)",
                      "algorithmic": "12 B per point + 4 B (miss-bitmap word) per voxel step + 2 bitmaps read and "
                                     "cleared per scan", "peak_kind": f"{peak_kind} (hbm_gbs)"},
-        "e2e": {"value": world * points / (e2e_total * 1e-3), "unit": "points/s",
+        "e2e": {"value": job_throughput(points, world, e2e_total), "unit": "points/s",
                 "h2d_bytes_per_step": int(np.mean([p.numel() * 4 for p in host_pts])), "d2h_bytes_per_step": 24},
         "gpu_launches": 6 * args.steps,
         "clocks": clk,
