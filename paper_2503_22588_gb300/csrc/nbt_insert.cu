@@ -33,8 +33,9 @@ using namespace nbt;
 namespace {
 
 constexpr float kMaxVoxelCoord = 4194304.0f;  // 2^22: beyond, index + 1/2 is not exact in FP32
-constexpr int kRayChunk = 8;                   // voxels a free-space ray walks ahead of its bitmap reads
 constexpr int kPointRun = 8;                   // consecutive points one thread files
+constexpr int kRayChunk = 4;                   // voxels a lane walks ahead of its bitmap reads
+constexpr int kRayLanes = 8;                   // lanes that share one free-space ray
 
 struct InsertConst {
   float ox, oy, oz;        // map origin (world)
@@ -97,14 +98,22 @@ __global__ void enumerate_kernel(const uint32_t *__restrict__ hit, int64_t n_wor
 }
 
 // 3. Free space: one ray per distinct endpoint (in-map list, then the
-// outside list), sensor to the endpoint voxel's centre.
+// outside list), sensor to the endpoint voxel's centre.  kRayLanes lanes walk
+// one ray: lane l takes its share of the crossings (walk_lane_part), so a
+// ray of a few hundred voxels costs each lane only its own part and many
+// more walks are in flight than there are rays (a scan has ~75k rays, too
+// few to hide the read latency one thread per ray).
 __global__ void free_rays_kernel(const uint32_t *__restrict__ list, const uint32_t *__restrict__ n_list,
                                  const int4 *__restrict__ outside, const uint32_t *__restrict__ n_outside,
                                  InsertConst c, uint32_t *__restrict__ miss, unsigned long long *__restrict__ steps) {
   const int64_t n_in = *n_list, total = n_in + *n_outside;
   const float o[3] = {c.vx, c.vy, c.vz};
-  unsigned long long steps_thread = 0ull;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & (kRayLanes - 1);
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kRayLanes;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) / kRayLanes;
+  const int guard = c.nx + c.ny + c.nz + 3;
+  unsigned long long steps_lane = 0ull;
+  for (int64_t r = warp0; r < total; r += n_warps) {
     int x, y, z;
     if (r < n_in) {
       const uint32_t v = list[r];
@@ -123,19 +132,35 @@ __global__ void free_rays_kernel(const uint32_t *__restrict__ list, const uint32
     if (!walk_init(w, o, d, c.nx, c.ny, c.nz)) continue;
     walk_linear_steps(w, c.nx, c.ny);
     int lin = walk_linear_index(w, c.nx, c.ny);
-    // Walk kRayChunk voxels ahead, read their bitmap words together, then
-    // set the bits that are still clear (most are: neighbouring rays cross
-    // the same voxels, so the read saves most atomics).
-    bool alive = true;
-    while (alive) {
+    bool first, split_end;
+    int A;
+    if (!walk_lane_part(w, lin, lane, kRayLanes, c.nx, c.ny, c.nz, first, split_end, A)) continue;
+    // The lane's voxels in groups of kRayChunk: walk ahead, read the group's
+    // bitmap words together, then set the bits that are still clear (most
+    // are set already: neighbouring rays cross the same voxels).
+    bool pending = first, more = true;
+    int g = 0;
+    while (more) {
       uint32_t v[kRayChunk], word[kRayChunk];
       int n = 0;
 #pragma unroll
       for (int k = 0; k < kRayChunk; ++k) {
         v[k] = (uint32_t)lin;
-        if (alive) {
-          n = k + 1;
-          alive = walk_advance_lin(w, lin);
+        if (more) {
+          if (pending) {
+            pending = false;
+            n = k + 1;
+          } else {
+            float t;
+            const int ax = walk_next_axis(w, t);
+            if (g++ < guard && (t < w.tmax || (split_end && t == w.tmax && ax < A))) {
+              walk_advance_lin(w, lin);   // takes exactly that crossing; its own end test is not needed
+              v[k] = (uint32_t)lin;
+              n = k + 1;
+            } else {
+              more = false;
+            }
+          }
         }
       }
 #pragma unroll
@@ -145,13 +170,13 @@ __global__ void free_rays_kernel(const uint32_t *__restrict__ list, const uint32
         const uint32_t m = 1u << (v[k] & 31u);
         if (k < n && !(word[k] & m)) atomicOr(miss + (v[k] >> 5), m);
       }
-      steps_thread += (unsigned long long)n;
+      steps_lane += (unsigned long long)n;
     }
   }
   // voxel steps walked, one atomic per warp
 #pragma unroll
-  for (int s = 16; s > 0; s >>= 1) steps_thread += __shfl_xor_sync(0xffffffffu, steps_thread, s);
-  if ((threadIdx.x & 31) == 0 && steps_thread) atomicAdd(steps, steps_thread);
+  for (int s = 16; s > 0; s >>= 1) steps_lane += __shfl_xor_sync(0xffffffffu, steps_lane, s);
+  if ((threadIdx.x & 31) == 0 && steps_lane) atomicAdd(steps, steps_lane);
 }
 
 // Bayes update of an occupancy probability by one observation of
@@ -325,8 +350,8 @@ extern "C" int nbt_map_insert_points(nbt_map map, const float *points, int64_t n
   const int64_t grid_w = std::min<int64_t>((words + 255) / 256, (int64_t)sms * 16);
   enumerate_kernel<<<(unsigned)grid_w, 256, 0, stream>>>(map->ins_hit, words, map->ins_list, n_list);
   NBT_CUDA_TRY(cudaGetLastError());
-  const int64_t grid_r = std::min<int64_t>((n + 127) / 128, (int64_t)sms * 16);
-  free_rays_kernel<<<(unsigned)grid_r, 128, 0, stream>>>(map->ins_list, n_list, (const int4 *)map->ins_outside,
+  const int64_t grid_r = std::min<int64_t>((n * kRayLanes + 255) / 256, (int64_t)sms * 8);   // kRayLanes per ray
+  free_rays_kernel<<<(unsigned)grid_r, 256, 0, stream>>>(map->ins_list, n_list, (const int4 *)map->ins_outside,
                                                           n_out, c, map->ins_miss, steps);
   NBT_CUDA_TRY(cudaGetLastError());
   UpdateConst u;

@@ -325,6 +325,123 @@ __device__ __forceinline__ bool walk_advance_lin(Walk &w, int &addr) {
   return end == 0u;
 }
 
+// ---------------------------------------------------------------------------
+// One ray walked by a whole warp (linear layout), bit-identical to the
+// sequential walk.  On axis a the k-th crossing ahead of the start has the
+// parameter t_a(k) = ((b_a + k s_a) - o_a) * (1/d_a) -- the walk's own two
+// rounded operations, non-decreasing in k -- and the walk takes crossings in
+// (t, axis) order (ties: x, then y, then z) while t < t_max.  So the state
+// after any prefix of that order is known from counts alone: with the split
+// key (T, A) = the j-th crossing of axis A, axis a has taken the crossings
+// with t_a(k) < T, or t_a(k) == T when a < A.  Lane l takes axis A's
+// crossings [l L, (l + 1) L) and the other axes' crossings in between
+// (L = the crossings of A before t_max divided among the ray's lanes).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float walk_axis_t(float b, float s, float o, float v, int k) {
+  return fmul(fsub(fadd(b, (float)k * s), o), v);
+}
+
+// Crossings k >= 0 of one axis that precede the key (T, A): the predicate
+// "t_a(k) < T, or t_a(k) == T when tie_before" holds on a prefix of k, and
+// at most `limit` crossings exist.  A real-arithmetic estimate is corrected
+// by exact evaluations; a binary search takes over if it is more than a few
+// crossings off.
+__device__ __forceinline__ int walk_axis_count(float b, float s, float o, float v, float T, bool tie_before,
+                                               int limit) {
+  if (s == 0.0f) return 0;
+  auto before = [&](int k) {
+    const float t = walk_axis_t(b, s, o, v, k);
+    return t < T || (tie_before && t == T);
+  };
+  const float est = fmaf(__fdividef(T, v), s, (o - b) * s);   // real k with t(k) = T
+  int k = est > 0.0f ? (est < (float)limit ? (int)est : limit) : 0;
+  for (int it = 0; it < 4; ++it) {
+    const bool in_k = k < limit && before(k);
+    const bool in_prev = k > 0 && before(k - 1);
+    if (!in_k && (k == 0 || in_prev)) return k;   // first k outside the prefix
+    k += in_k ? 1 : -1;
+  }
+  int lo = 0, hi = limit;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (before(mid))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// The walk's next crossing without taking it: axis (0 x, 1 y, 2 z) and t.
+__device__ __forceinline__ int walk_next_axis(const Walk &w, float &t) {
+  const bool mx = (w.tx <= w.ty) & (w.tx <= w.tz);
+  const bool my = !mx & (w.ty <= w.tz);
+  t = mx ? w.tx : (my ? w.ty : w.tz);
+  return mx ? 0 : (my ? 1 : 2);
+}
+
+// Take crossing `axis` (linear layout): same operations as walk_advance_lin.
+__device__ __forceinline__ void walk_take_lin(Walk &w, int axis, int &lin) {
+  if (axis == 0) {
+    w.bx = fadd(w.bx, w.sx);
+    w.tx = fmul(fsub(w.bx, w.ox), w.vx);
+    lin += w.qx;
+  } else if (axis == 1) {
+    w.by = fadd(w.by, w.sy);
+    w.ty = fmul(fsub(w.by, w.oy), w.vy);
+    lin += w.qy;
+  } else {
+    w.bz = fadd(w.bz, w.sz);
+    w.tz = fmul(fsub(w.bz, w.oz), w.vz);
+    lin += w.qz;
+  }
+}
+
+// Set up part `lane` of n_parts of a ray whose walk w starts at linear index
+// lin (walk_init + walk_linear_steps done).  On return w / lin hold the
+// lane's start state and w.tmax its end; first is true for the lane that
+// visits the start voxel itself; split_end tells whether the part ends at a
+// split (then crossings tied with it on a lower axis still belong to it);
+// axis_a is the split axis.  Returns false if the lane has nothing to walk.
+__device__ __forceinline__ bool walk_lane_part(Walk &w, int &lin, int lane, int n_parts, int nx, int ny, int nz,
+                                               bool &first, bool &split_end, int &axis_a) {
+  const float ax = fabsf(w.vx), ay = fabsf(w.vy), az = fabsf(w.vz);   // smaller |1/d|: more crossings
+  const bool sx = w.sx != 0.0f, sy = w.sy != 0.0f, sz = w.sz != 0.0f;
+  int A = -1;
+  float best = __int_as_float(0x7f800000);
+  if (sx && ax < best) { A = 0; best = ax; }
+  if (sy && ay < best) { A = 1; best = ay; }
+  if (sz && az < best) { A = 2; best = az; }
+  axis_a = A;
+  first = lane == 0;
+  split_end = false;
+  if (A < 0) return lane == 0;   // no crossing at all: one voxel
+  const float bA = A == 0 ? w.bx : (A == 1 ? w.by : w.bz), sA = A == 0 ? w.sx : (A == 1 ? w.sy : w.sz);
+  const float oA = A == 0 ? w.ox : (A == 1 ? w.oy : w.oz), vA = A == 0 ? w.vx : (A == 1 ? w.vy : w.vz);
+  const int dimA = A == 0 ? nx : (A == 1 ? ny : nz);
+  const int nA = walk_axis_count(bA, sA, oA, vA, w.tmax, false, dimA + 1);   // crossings before t_max
+  const int L = (nA + n_parts - 1) / n_parts;
+  const int j0 = lane * L, j1 = j0 + L;
+  if (lane > 0 && j0 >= nA) return false;
+  if (j1 < nA) {
+    w.tmax = walk_axis_t(bA, sA, oA, vA, j1);
+    split_end = true;
+  }
+  if (lane == 0) return true;
+  const float T = walk_axis_t(bA, sA, oA, vA, j0);
+  const int cx = A == 0 ? j0 : walk_axis_count(w.bx, w.sx, w.ox, w.vx, T, 0 < A, nx + 1);
+  const int cy = A == 1 ? j0 : walk_axis_count(w.by, w.sy, w.oy, w.vy, T, 1 < A, ny + 1);
+  const int cz = A == 2 ? j0 : walk_axis_count(w.bz, w.sz, w.oz, w.vz, T, 2 < A, nz + 1);
+  w.bx = fadd(w.bx, (float)cx * w.sx);
+  w.by = fadd(w.by, (float)cy * w.sy);
+  w.bz = fadd(w.bz, (float)cz * w.sz);
+  w.tx = fmul(fsub(w.bx, w.ox), w.vx);
+  w.ty = fmul(fsub(w.by, w.oy), w.vy);
+  w.tz = fmul(fsub(w.bz, w.oz), w.vz);
+  lin += cx * w.qx + cy * w.qy + cz * w.qz;
+  return true;
+}
+
 // Host helpers (defined in nbt_map.cu).
 int check_map(nbt_map map);
 int prepare_gain(nbt_map map, const nbt_ig_params *params, cudaStream_t stream);
