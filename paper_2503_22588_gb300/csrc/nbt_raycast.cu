@@ -306,6 +306,157 @@ __global__ void __launch_bounds__(kThreads, CHUNK ? 4 : (LINEAR ? 6 : 5))
   }
 }
 
+// Few rays (the paper's operating point: a few thousand rays per call):
+// LANES lanes walk each ray (walk_lane_part), each its share of the
+// crossings, kSplitChunk voxels ahead of its reads.  A lane stops at its
+// first occupied voxel; the ray's IG is the sum of its lanes up to and
+// including the first lane that found one (the lanes are in walk order).
+// Items as ig_tiles_kernel: (pose, 32 x 8 tile), one partial per item; the
+// tile's rays are taken 32 at a time.
+constexpr int kSplitChunk = 4;
+
+template <int KIND, bool HIT, int LANES>
+__device__ __forceinline__ void lane_ray_ig(const void *payload, uint32_t addr_max, int nx, int ny, int nz,
+                                            const float o[3], const float d[3], int part, float &facc,
+                                            uint32_t &iacc, uint32_t &steps, bool &occ_found) {
+  Walk w;
+  if (!walk_init(w, o, d, nx, ny, nz)) return;
+  walk_linear_steps(w, nx, ny);
+  int lin = walk_linear_index(w, nx, ny);
+  bool first, split_end;
+  int A;
+  if (!walk_lane_part(w, lin, part, LANES, nx, ny, nz, first, split_end, A)) return;
+  const int guard = nx + ny + nz + 3;
+  bool pending = first, more = true;
+  int g = 0;
+  while (more) {
+    uint32_t a[kSplitChunk], r[kSplitChunk];
+    int n = 0;
+#pragma unroll
+    for (int k = 0; k < kSplitChunk; ++k) {
+      a[k] = min((uint32_t)lin, addr_max);
+      if (more) {
+        if (pending) {
+          pending = false;
+          n = k + 1;
+        } else {
+          float t;
+          const int ax = walk_next_axis(w, t);
+          if (g++ < guard && (t < w.tmax || (split_end && t == w.tmax && ax < A))) {
+            walk_advance_lin(w, lin);   // takes exactly that crossing
+            a[k] = min((uint32_t)lin, addr_max);
+            n = k + 1;
+          } else {
+            more = false;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kSplitChunk; ++k) r[k] = k < n ? raw_load<KIND>(payload, a[k]) : 0u;
+#pragma unroll
+    for (int k = 0; k < kSplitChunk; ++k) {
+      if (k < n && !occ_found) {
+        steps += 1u;
+        bool occ;
+        if (KIND == PAYLOAD_GAIN_F32) {
+          occ = (int32_t)r[k] < 0;
+          const float gk = fabsf(__uint_as_float(r[k]));
+          if (HIT || !occ) facc += gk;
+        } else {
+          uint32_t st = r[k];
+          if (KIND == PAYLOAD_U2) st = (st >> ((a[k] & 3u) << 1)) & 3u;
+          occ = st >= 2u;
+          iacc += st == 0u ? 1u : 0u;
+        }
+        occ_found = occ;
+      }
+    }
+    if (occ_found) return;
+  }
+}
+
+template <int KIND, bool HIT, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    ig_split_kernel(DevMap m, CamConst cc, const float *__restrict__ poses, int64_t n_items, uint32_t addr_max,
+                    unsigned long long *queue, Partial *partials) {
+  __shared__ float s_pose[8];
+  __shared__ float s_f[kThreads / 32];
+  __shared__ uint32_t s_i[kThreads / 32], s_s[kThreads / 32];
+  __shared__ long long s_item;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int part = threadIdx.x % LANES;   // position of this lane in its ray's group
+  const int slot = threadIdx.x / LANES;   // ray of the pass
+  const unsigned group = (LANES == 32 ? 0xffffffffu : ((1u << LANES) - 1u)) << (lane & ~(LANES - 1));
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(queue, 1ull);
+      s_item = it;
+      if (it < n_items) {
+        const long long pose = it / cc.tiles_per_pose;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s_pose[k] = __ldg(poses + pose * 7 + k);
+      }
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= n_items) break;
+    const long long pose = item / cc.tiles_per_pose;
+    const int tile = (int)(item - pose * cc.tiles_per_pose);
+    const int x0 = (tile % cc.tiles_x) * kTileW, y0 = (tile / cc.tiles_x) * kTileH;
+    const int tw = min(kTileW, cc.W - x0), th = min(kTileH, cc.H - y0);
+    const int n_rays = tw * th;
+    float facc = 0.0f;
+    uint32_t iacc = 0u, steps = 0u;
+    for (int r0 = 0; r0 < n_rays; r0 += kThreads / LANES) {
+      const int r = r0 + slot;
+      float f = 0.0f;
+      uint32_t ic = 0u, st = 0u;
+      bool occ = false;
+      if (r < n_rays) {
+        float o[3], d[3];
+        ray_segment(cc, s_pose, x0 + r % tw, y0 + r / tw, o, d);
+        lane_ray_ig<KIND, HIT, LANES>(m.payload, addr_max, m.nx, m.ny, m.nz, o, d, part, f, ic, st, occ);
+      }
+      // lanes past the first one that met an occupied voxel contribute nothing
+      const unsigned hit = __ballot_sync(0xffffffffu, occ) & group;
+      if (hit && lane > __ffs(hit) - 1) {
+        f = 0.0f;
+        ic = 0u;
+        st = 0u;
+      }
+      facc += f;
+      iacc += ic;
+      steps += st;
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      facc += __shfl_xor_sync(0xffffffffu, facc, s);
+      iacc += __shfl_xor_sync(0xffffffffu, iacc, s);
+      steps += __shfl_xor_sync(0xffffffffu, steps, s);
+    }
+    if (lane == 0) {
+      s_f[warp] = facc;
+      s_i[warp] = iacc;
+      s_s[warp] = steps;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Partial p;
+      p.fsum = 0.0f;
+      p.isum = 0u;
+      p.steps = 0u;
+      p.pad = 0u;
+      for (int k = 0; k < kThreads / 32; ++k) {
+        p.fsum += s_f[k];
+        p.isum += s_i[k];
+        p.steps += s_s[k];
+      }
+      partials[item] = p;
+    }
+  }
+}
+
 // One warp per perspective: fixed-order FP64 sum of its tiles' partials.
 __global__ void views_reduce_kernel(const Partial *__restrict__ partials, int64_t n_views, int tiles, int mean,
                                     double n_rays, float *__restrict__ ig_out, uint64_t *__restrict__ steps_out) {
@@ -472,10 +623,41 @@ int launch_tiles_t(nbt_map map, const void *payload, const CamConst &cc, const f
 // Voxels the latency-bound variant walks ahead of its reads.
 constexpr int kChunk = 8;
 
-// Linear layout: few rays (at most two per thread slot of the throughput
-// kernel's resident CTAs) cannot hide the per-step read latency, so they
-// take the walk-ahead kernel; more rays take the rolling one-voxel prefetch,
-// which issues fewer instructions per step.
+// Calls with at most this many rays (linear layout) take the split-ray
+// kernel: 16 lanes per ray up to kSplit16Rays, 8 up to kSplit8Rays (measured
+// on the paper-mode sweep; beyond, more rays than lanes hide the latency).
+constexpr int64_t kSplit16Rays = 4096;
+constexpr int64_t kSplit8Rays = 32768;
+
+template <int KIND, bool HIT, int LANES>
+int launch_split(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
+                 void *workspace, cudaStream_t stream) {
+  static int cached[64] = {0};
+  const int dev = map->device;
+  int per_sm = dev >= 0 && dev < 64 ? cached[dev] : 0;
+  if (per_sm <= 0) {
+    NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ig_split_kernel<KIND, HIT, LANES>, kThreads,
+                                                               0));
+    per_sm = std::max(per_sm, 1);
+    if (dev >= 0 && dev < 64) cached[dev] = per_sm;
+  }
+  const int64_t grid = std::min<int64_t>(n_items, (int64_t)sm_count() * per_sm);
+  unsigned long long *queue = (unsigned long long *)workspace;
+  Partial *partials = (Partial *)((char *)workspace + 256);
+  NBT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream));
+  ig_split_kernel<KIND, HIT, LANES><<<(unsigned)grid, kThreads, 0, stream>>>(
+      dev_map(map, payload), cc, poses, n_items, addr_max_of(map), queue, partials);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+// Linear layout, by the number of rays in the call: a few thousand take the
+// split-ray kernel (several lanes per ray); up to two per thread slot of the
+// throughput kernel's resident CTAs, the walk-ahead kernel (neither can hide
+// the per-step read latency otherwise); more take the rolling one-voxel
+// prefetch, which issues the fewest instructions per step.  The split
+// kernel adds each ray's gains lane part by lane part, so its FP32 sums may
+// differ from the other kernels' in the last bits (counts and steps equal).
 template <int KIND, bool HIT>
 int launch_tiles_linear(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
                         void *workspace, cudaStream_t stream) {
@@ -483,6 +665,8 @@ int launch_tiles_linear(nbt_map map, const void *payload, const CamConst &cc, co
   int rc = tiles_per_sm<KIND, HIT, true, 0>(map, 0, &per_sm);
   if (rc != NBT_OK) return rc;
   const int64_t n_rays = n_items / cc.tiles_per_pose * cc.W * cc.H;
+  if (n_rays <= kSplit16Rays) return launch_split<KIND, HIT, 16>(map, payload, cc, poses, n_items, workspace, stream);
+  if (n_rays <= kSplit8Rays) return launch_split<KIND, HIT, 8>(map, payload, cc, poses, n_items, workspace, stream);
   if (n_rays <= 2 * (int64_t)sm_count() * per_sm * kThreads)
     return launch_tiles_t<KIND, HIT, true, kChunk>(map, payload, cc, poses, n_items, workspace, stream);
   return launch_tiles_t<KIND, HIT, true, 0>(map, payload, cc, poses, n_items, workspace, stream);

@@ -192,7 +192,9 @@ def test_views_ig_degenerate_maps_and_poses():
 
 @pytest.mark.parametrize("encoding,metric", [("u8", "count"), ("u2", "count"), ("f32", "entropy"), ("f32", "eq2")])
 def test_latency_and_throughput_kernels_agree(encoding, metric):
-    """Few rays take the walk-ahead kernel, many the rolling-prefetch kernel: identical results."""
+    """The call size picks the kernel -- many rays: rolling prefetch; fewer: walk-ahead; a few
+    thousand: rays split over 8 or 16 lanes.  Steps and counts are identical; FP32 gains are
+    identical except that the split kernel sums a ray lane part by lane part (<= 1e-6)."""
     w = configs.exact64(seed=5, n_views=512)
     grid = w.grid
     if encoding == "f32":
@@ -200,15 +202,29 @@ def test_latency_and_throughput_kernels_agree(encoding, metric):
     gm = nbt.Map.from_grid(torch.from_numpy(np.ascontiguousarray(grid)).cuda(), w.voxel_size, w.origin, encoding)
     cam, prm = gpu_camera(w.camera), nbt.ig_params(metric)
     p = torch.from_numpy(w.poses).cuda()
-    big_ig, big_st = nbt.views_ig(gm, p, cam, prm)                      # 1.57M rays: rolling prefetch
-    parts = [nbt.views_ig(gm, p[k:k + 32], cam, prm) for k in range(0, 512, 32)]   # 98k rays: walk-ahead
+
+    def batched(k):
+        parts = [nbt.views_ig(gm, p[i:i + k], cam, prm) for i in range(0, 512, k)]
+        return torch.cat([a for a, _ in parts]), torch.cat([b for _, b in parts])
+
+    big_ig, big_st = nbt.views_ig(gm, p, cam, prm)     # 1.57M rays: rolling prefetch
+    mid_ig, mid_st = batched(32)                        # 98k rays: walk-ahead
+    sm_ig, sm_st = batched(4)                           # 12k rays: 8 lanes per ray
+    one_ig, one_st = batched(1)                         # 3k rays: 16 lanes per ray
     torch.cuda.synchronize()
-    assert torch.equal(big_ig, torch.cat([a for a, _ in parts]))
-    assert torch.equal(big_st, torch.cat([b for _, b in parts]))
+    for st in (mid_st, sm_st, one_st):
+        assert torch.equal(big_st, st)
+    assert torch.equal(big_ig, mid_ig)
+    for ig in (sm_ig, one_ig):
+        if metric == "count":
+            assert torch.equal(big_ig, ig)
+        else:
+            assert rel_err(ig.cpu().numpy(), big_ig.cpu().numpy().astype(np.float64)).max() <= 1e-6
     rig, rst = oracle.views_ig(oracle.Map(grid, w.voxel_size, w.origin), w.poses[:64], oracle_camera(w.camera),
                                oracle.params(metric), "f32", 8)
-    assert np.array_equal(big_st.cpu().numpy()[:64], rst)
-    assert rel_err(big_ig.cpu().numpy()[:64], rig).max() <= RTOL
+    for ig, st in ((big_ig, big_st), (one_ig, one_st)):
+        assert np.array_equal(st.cpu().numpy()[:64], rst)
+        assert rel_err(ig.cpu().numpy()[:64], rig).max() <= RTOL
     gm.close()
 
 
