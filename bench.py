@@ -284,7 +284,8 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="prob256",
-                    choices=["prob256", "exact64", "room512", "traj256", "room512-pruned", "idw_cost", "fig3", "insert"])
+                    choices=["prob256", "exact64", "room512", "traj256", "room512-pruned", "idw_cost", "fig3", "insert",
+                             "surrogate"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -318,6 +319,9 @@ def main() -> None:
         return
     if args.workload == "insert":
         run_insert(args, nbt, torch, dev, stream, world, rank, local, dist)
+        return
+    if args.workload == "surrogate":
+        run_surrogate(args, nbt, torch, dev, stream, world, rank, local, dist)
         return
     w = build_workload(args.workload, rank)
     if w.offsets is not None:
@@ -837,6 +841,132 @@ def run_insert(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
     m.close()
 
 
+SURROGATE_METRIC = "surrogate inference views/s (frustum crops + 3D-CNN forward on tcgen05), 16,384 candidates per step"
+
+
+def surrogate_flops_per_view() -> int:
+    """Multiply-adds x 2 of one forward pass: the four 3^3 convolutions, fc1 and fc2."""
+    from paper_2503_22588_gb300.surrogate import CROP, FC_IN, HIDDEN, LAYERS
+    flops, size = 0, CROP
+    for cin, cout, stride in LAYERS:
+        size = (size - 1) // stride + 1
+        flops += 2 * size ** 3 * cout * 27 * cin
+    return flops + 2 * FC_IN * HIDDEN + 2 * HIDDEN
+
+
+def surrogate_cpu_baseline(crops, feats, params, budget_s: float = 10.0) -> dict:
+    """The oracle's FP64 forward (numpy, BF16-rounded as on the GPU) on a bounded number of the same crops
+    (class codes, expanded to the one-hot input the oracle takes)."""
+    from oracle import surrogate as S
+    q = {k: np.asarray(v, np.float64) for k, v in params.items()}
+    n, t0 = 0, time.perf_counter()
+    while n < len(crops) and (n == 0 or time.perf_counter() - t0 < budget_s):
+        S.forward(q, S.codes_to_onehot(crops[n:n + 8]), feats[n:n + 8], bf16_activations=True)
+        n += len(crops[n:n + 8])
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "views/s", "cores": 1, "kind": "oracle",
+            "sample": f"forward of the first {n} crops of the same step (crops given)"}
+
+
+def run_surrogate(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
+    """Surrogate inference: crops and predictions for 16,384 candidate views per step."""
+    import math
+    from paper_2503_22588_gb300 import surrogate as gs
+    from workload import configs, poses as wp
+    w = configs.traj256(seed=rank)
+    m = nbt.Map.from_grid(torch.from_numpy(np.ascontiguousarray(w.grid)).to(dev), w.voxel_size, w.origin, "u8")
+    cam = nbt.camera(128, 96, math.radians(60), math.radians(45), 1.0)
+    prm = nbt.ig_params("count")
+    pz_np = np.concatenate([wp.shell_views(p, 4096, 0.3, 0.8, 100 * rank + k) for k, p in enumerate(w.pois)])
+    pz = torch.from_numpy(pz_np).to(dev)
+    n, batch = len(pz_np), 4096
+    net = gs.Surrogate(max_batch=batch, params=gs.he_init(rank))
+    scores = torch.empty(n, dtype=torch.float32, device=dev)
+    cr = torch.empty((batch, gs.CROP, gs.CROP, gs.CROP), dtype=torch.uint8, device=dev)
+    ft = torch.empty((batch, gs.FEATS), dtype=torch.bfloat16, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(poses_dev, fwd_events=None):
+        for b0 in range(0, n, batch):
+            c_b, f_b = gs.crops(m, poses_dev[b0:b0 + batch], cam, prm, stream, out=(cr, ft))
+            if fwd_events is not None:
+                fwd_events[b0 // batch][0].record(stream)
+            net.forward(c_b, f_b, scores[b0:b0 + batch], stream)
+            if fwd_events is not None:
+                fwd_events[b0 // batch][1].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        step(pz)
+    n_b = (n + batch - 1) // batch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_b)]
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, c = ev[k]
+        a.record(stream)
+        step(pz, fev[k])
+        c.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(float(sum(a.elapsed_time(c) for a, c in ev)), dist, dev)
+    fwd_ms = float(np.mean([sum(x.elapsed_time(y) for x, y in f) for f in fev]))
+    # end to end: candidate poses from pinned host memory, scores back to the host
+    pz_host = torch.from_numpy(pz_np).pin_memory()
+    sc_host = torch.empty(n, dtype=torch.float32).pin_memory()
+    e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, c = ev[k]
+        a.record(stream)
+        pz.copy_(pz_host, non_blocking=True)
+        step(pz)
+        sc_host.copy_(scores, non_blocking=True)
+        c.record(stream)
+        c.synchronize()
+        e_ms.append(a.elapsed_time(c))
+    e2e_total = max_over_ranks(float(sum(e_ms)), dist, dev)
+    fl = surrogate_flops_per_view()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    achieved = fl * n / (fwd_ms * 1e-3) / 1e12
+    line = {
+        "metric": SURROGATE_METRIC, "value": job_throughput(n * args.steps, world, total_ms), "unit": "views/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "surrogate: 16,384 candidate views (4 PoIs x 4096 on a 0.3-0.8 m shell) of the 256^3 "
+                               "uint8 tabletop; 32^3 class-code crops (one-hot over 8 channels), convs 8-16-32-64-64, "
+                               "MLP 4104-128-1, batches of 4096; random-init weights", "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB write)", "step": "nbt_surrogate_crops + forward"},
+        "forward_ms_per_step": fwd_ms, "flops_per_view": fl,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "surrogate forward (implicit-GEMM convolutions + MLP on tcgen05)",
+                     "algorithmic": f"{fl} FLOP per view x {n} views", "peak_kind": "measured (bf16_tflops, burst)"},
+        "e2e": {"value": job_throughput(n * args.steps, world, e2e_total), "unit": "views/s",
+                "h2d_bytes_per_step": int(pz_host.numel() * 4), "d2h_bytes_per_step": int(sc_host.numel() * 4)},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = surrogate_cpu_baseline(cr[:64].cpu().numpy(), ft.float().cpu().numpy()[:64],
+                                                      net.get_params())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    net.close()
+    m.close()
+
+
 def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
     """room512 next-best-view selection, exact vs surrogate-pruned.
 
@@ -848,7 +978,6 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
     speedup and how often the two choices agree.
     """
     import math
-    from oracle import surrogate as S  # initial weights only (seeded He init)
     from paper_2503_22588_gb300 import planning as P, surrogate as gs
     from workload import configs, poses as wp, scenes
 
@@ -865,7 +994,7 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         maps.append(m)
         poses.append(pt)
         targets.append(P.label_views(m, pt, cam, prm))
-    net = gs.Surrogate(max_batch=4096, params=S.init_params(0))
+    net = gs.Surrogate(max_batch=4096, params=gs.he_init(0))
     t0 = time.perf_counter()
     losses = P.train(net, maps, poses, targets, cam, prm, epochs=12, lr=1e-3, batch=256)
     torch.cuda.synchronize(dev)

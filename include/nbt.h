@@ -327,11 +327,12 @@ int nbt_tc_error(int32_t *flag);
  * candidate perspectives before the exact Section III raycast re-scores
  * them).  Input per perspective: a view-aligned crop -- 32 x 32 x 32
  * samples on the rays through the pixel centres of a 32 x 32 image of the
- * field of view, at depth fractions (k + 1/2) / 32 of d_Cam, each the
- * one-hot class (unknown / free / occupied in channels 0 / 1 / 2 of 8,
- * zero outside the map) of the voxel holding it, BF16 NDHWC [n][32][32][32]
- * [8] -- and 8 BF16 pose features ((position - origin) / map extent, the
- * quaternion, 1).  Output: the predicted mean ray IG (the training target
+ * field of view, at depth fractions (k + 1/2) / 32 of d_Cam, each the class
+ * of the voxel holding it as a uint8 code (0 outside the map, 1 unknown,
+ * 2 free, 3 occupied), [n][32 (depth k)][32 (row j)][32 (column i)] -- and 8
+ * BF16 pose features ((position - origin) / map extent, the quaternion, 1).
+ * The network sees code c as the one-hot vector with a 1 in channel c - 1 of
+ * 8 (all zero for code 0).  Output: the predicted mean ray IG (the training target
  * the caller chooses, e.g. g_P / 100).  Network: 3^3 convolutions 8->16,
  * 16->32, 32->64 (stride 2) and 64->64 (stride 1), ReLU; 4096 + 8 -> 128
  * (ReLU) -> 1; BF16 weights and activations, FP32 accumulation on tcgen05
@@ -354,9 +355,9 @@ int nbt_surrogate_destroy(nbt_surrogate net);
 int nbt_surrogate_set_params(nbt_surrogate net, const float *host, int64_t n);
 int nbt_surrogate_get_params(nbt_surrogate net, float *host, int64_t n);
 
-/* Crops and pose features of n poses (device arrays as described above;
- * crops 16-byte aligned).  params supplies the occupancy thresholds of
- * probability maps.  Asynchronous on stream. */
+/* Crops and pose features of n poses (device arrays as described above).
+ * params supplies the occupancy thresholds of probability maps.
+ * Asynchronous on stream. */
 int nbt_surrogate_crops(nbt_map map, const nbt_pose *poses, int64_t n, const nbt_camera *cam,
                         const nbt_ig_params *params, void *crops, void *feats, void *stream);
 

@@ -99,6 +99,20 @@ def frustum_crop(grid, voxel_size, origin, pose, cc, occ_threshold=0.7, free_thr
     return out, pose_features(pose, voxel_size, origin, dims)
 
 
+def crop_codes(onehot):
+    """One-hot crops (..., 8) -> class codes (...,): 0 no channel set (outside the map), else 1 + channel."""
+    oh = np.asarray(onehot)
+    return np.where(oh.any(axis=-1), oh.argmax(axis=-1) + 1, 0).astype(np.uint8)
+
+
+def codes_to_onehot(codes, dtype=np.float64):
+    """Class codes (...,) -> one-hot (..., 8): code c sets channel c - 1, code 0 nothing."""
+    c = np.asarray(codes).astype(np.int64)
+    out = np.zeros(c.shape + (C0,), dtype)
+    np.put_along_axis(out, np.maximum(c - 1, 0)[..., None], (c > 0)[..., None].astype(dtype), axis=-1)
+    return out
+
+
 def pose_features(pose, voxel_size, origin, dims):
     """(position - origin) / map extent per axis, the quaternion, and a constant 1."""
     f32 = np.float32

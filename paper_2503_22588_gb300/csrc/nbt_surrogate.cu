@@ -276,67 +276,215 @@ struct CropConst {
 };
 
 template <int KIND>
-__global__ void crop_kernel(DevMap m, CropConst cc, const float *__restrict__ poses, int64_t n, bf16 *__restrict__ crops,
-                            bf16 *__restrict__ feats) {
-  const int64_t total = n * (int64_t)kCrop * kCrop * kCrop;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = t >> 15;
-    const int cell = (int)(t & 32767);
-    const int i = cell & 31, j = (cell >> 5) & 31, k = cell >> 10;
-    float pz[7];
+__global__ void __launch_bounds__(256) crop_kernel(DevMap m, CropConst cc, const float *__restrict__ poses, int64_t n,
+                                                   uint8_t *__restrict__ crops, bf16 *__restrict__ feats) {
+  // one CTA per perspective: the rotation is formed once, then every sample
+  // of the crop uses it (same operations, same order as per sample)
+  __shared__ float s_r[9], s_o[3], s_pz[7];
+  const float org[3] = {cc.ox, cc.oy, cc.oz};
+  for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < 7; ++q) pz[q] = __ldg(poses + v * 7 + q);
-    float r[9];
-    quat_rot_f32(pz + 3, r);
-    const float fr = __fdiv_rn((float)k + 0.5f, 32.0f);
-    const float cx = fadd(cc.x0, fmul((float)i, cc.xs));
-    const float cy = fadd(cc.y0, fmul((float)j, cc.ys));
-    const float p[3] = {fmul(cx, fr), fmul(cy, fr), fmul(cc.zc, fr)};
-    const float org[3] = {cc.ox, cc.oy, cc.oz};
+      for (int q = 0; q < 7; ++q) s_pz[q] = __ldg(poses + v * 7 + q);
+      float r[9];
+      quat_rot_f32(s_pz + 3, r);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) s_r[q] = r[q];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) s_o[a] = fmul(fsub(s_pz[a], org[a]), cc.inv_s);
+    }
+    __syncthreads();
+    float r[9], o[3];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) r[q] = s_r[q];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) o[a] = s_o[a];
     const int dims[3] = {m.nx, m.ny, m.nz};
-    int idx[3];
-    bool inside = true;
+    uint8_t *cv = crops + v * (int64_t)(kCrop * kCrop * kCrop);
+    for (int cell = threadIdx.x; cell < kCrop * kCrop * kCrop; cell += blockDim.x) {
+      const int i = cell & 31, j = (cell >> 5) & 31, k = cell >> 10;
+      const float fr = fmul(fadd((float)k, 0.5f), 0.03125f);   // (k + 1/2) / 32, exact
+      const float cx = fadd(cc.x0, fmul((float)i, cc.xs));
+      const float cy = fadd(cc.y0, fmul((float)j, cc.ys));
+      const float p[3] = {fmul(cx, fr), fmul(cy, fr), fmul(cc.zc, fr)};
+      int idx[3];
+      bool inside = true;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float w = fadd(fadd(fmul(r[3 * a], p[0]), fmul(r[3 * a + 1], p[1])), fmul(r[3 * a + 2], p[2]));
-      const float o = fmul(fsub(pz[a], org[a]), cc.inv_s);
-      const float q = fadd(o, fmul(w, cc.inv_s));
-      const float fl = floorf(q);
-      inside = inside && fl >= 0.0f && fl < (float)dims[a];
-      idx[a] = inside ? (int)fl : 0;
-    }
-    uint32_t cls = 3u;  // 3 = outside: no channel set
-    if (inside) {
-      const int32_t off = m.tab[idx[0]] + m.tab[m.nx + idx[1]] + m.tab[m.nx + m.ny + idx[2]];
-      if (KIND == PAYLOAD_GAIN_F32) {
-        const float pv = __ldg((const float *)m.payload + off);
-        cls = pv > cc.occ_thr ? 2u : (pv < cc.free_thr ? 1u : 0u);
-      } else if (KIND == PAYLOAD_U8) {
-        const uint32_t st = __ldg((const uint8_t *)m.payload + off);
-        cls = st >= 2u ? 2u : st;
-      } else {
-        const uint32_t byte = __ldg((const uint8_t *)m.payload + (off >> 2));
-        const uint32_t st = (byte >> ((off & 3) << 1)) & 3u;
-        cls = st >= 2u ? 2u : st;
+      for (int a = 0; a < 3; ++a) {
+        const float w = fadd(fadd(fmul(r[3 * a], p[0]), fmul(r[3 * a + 1], p[1])), fmul(r[3 * a + 2], p[2]));
+        const float q = fadd(o[a], fmul(w, cc.inv_s));
+        const float fl = floorf(q);
+        inside = inside && fl >= 0.0f && fl < (float)dims[a];
+        idx[a] = inside ? (int)fl : 0;
       }
+      uint32_t cls = 3u;  // 3 = outside: no channel set
+      if (inside) {
+        const int32_t off = m.tab[idx[0]] + m.tab[m.nx + idx[1]] + m.tab[m.nx + m.ny + idx[2]];
+        if (KIND == PAYLOAD_GAIN_F32) {
+          const float pv = __ldg((const float *)m.payload + off);
+          cls = pv > cc.occ_thr ? 2u : (pv < cc.free_thr ? 1u : 0u);
+        } else if (KIND == PAYLOAD_U8) {
+          const uint32_t st = __ldg((const uint8_t *)m.payload + off);
+          cls = st >= 2u ? 2u : st;
+        } else {
+          const uint32_t byte = __ldg((const uint8_t *)m.payload + (off >> 2));
+          const uint32_t st = (byte >> ((off & 3) << 1)) & 3u;
+          cls = st >= 2u ? 2u : st;
+        }
+      }
+      // code: 0 outside the map, else 1 + class (unknown, free, occupied)
+      cv[cell] = (uint8_t)(cls < 3u ? cls + 1u : 0u);
     }
-    // BF16 1.0 (0x3F80) in channel cls of the first four, nothing for outside
-    const unsigned long long bits = cls < 3u ? (0x3F80ull << (16u * cls)) : 0ull;
-    uint4 onehot;
-    onehot.x = (uint32_t)bits;
-    onehot.y = (uint32_t)(bits >> 32);
-    onehot.z = 0u;
-    onehot.w = 0u;
-    *(uint4 *)(crops + (size_t)t * kC0) = onehot;
-    if (cell == 0) {
+    if (threadIdx.x == 0) {
       const float ext[3] = {cc.ext_x, cc.ext_y, cc.ext_z};
 #pragma unroll
-      for (int a = 0; a < 3; ++a) feats[v * kFeat + a] = __float2bfloat16_rn(__fdiv_rn(fsub(pz[a], org[a]), ext[a]));
+      for (int a = 0; a < 3; ++a) feats[v * kFeat + a] = __float2bfloat16_rn(__fdiv_rn(fsub(s_pz[a], org[a]), ext[a]));
 #pragma unroll
-      for (int a = 0; a < 4; ++a) feats[v * kFeat + 3 + a] = __float2bfloat16_rn(pz[3 + a]);
+      for (int a = 0; a < 4; ++a) feats[v * kFeat + 3 + a] = __float2bfloat16_rn(s_pz[3 + a]);
       feats[v * kFeat + 7] = __float2bfloat16_rn(1.0f);
     }
   }
+}
+
+// Layer 0 sees one-hot crops, so it needs no multiplications: output
+// channel co of an output voxel is b0[co] plus, over the 27 taps, the weight
+// W0[co][tap][class] of the class of the tap's input sample (a sample
+// outside the map, or a tap in the zero padding, adds nothing); then ReLU.
+// The [tap][code][channel] table of BF16-rounded weights sits in shared
+// memory (code 0, outside the map, is a zero row).
+constexpr int kCodes = 4;
+constexpr int kC1 = 16;      // layer 0 output channels
+constexpr int kRowPad = 20;  // table row stride in floats: the four class rows of a tap fall in different banks
+
+__device__ __forceinline__ unsigned long long add_f32x2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+__global__ void __launch_bounds__(256) conv0_lookup_kernel(const uint8_t *__restrict__ codes, const bf16 *__restrict__ w0,
+                                                           const float *__restrict__ b0, int64_t n_views,
+                                                           bf16 *__restrict__ act0) {
+  __shared__ __align__(16) float tab[27 * kCodes * kRowPad];
+  __shared__ __align__(16) uint8_t s_code[kCrop * kCrop * kCrop];
+  __shared__ __align__(16) float bias[kC1];
+  for (int e = threadIdx.x; e < 27 * kCodes * kC1; e += blockDim.x) {
+    const int co = e % kC1, code = (e / kC1) % kCodes, tap = e / (kC1 * kCodes);
+    tab[(tap * kCodes + code) * kRowPad + co] =
+        code == 0 ? 0.0f : __bfloat162float(w0[co * (27 * kC0) + tap * kC0 + (code - 1)]);
+  }
+  if (threadIdx.x < kC1) bias[threadIdx.x] = b0[threadIdx.x];
+  constexpr int kIn = kCrop * kCrop * kCrop, kOut = 16 * 16 * 16;
+  for (int64_t v = blockIdx.x; v < n_views; v += gridDim.x) {
+    __syncthreads();
+    const uint4 *src = (const uint4 *)(codes + v * (int64_t)kIn);
+    for (int e = threadIdx.x; e < kIn / 16; e += blockDim.x) ((uint4 *)s_code)[e] = src[e];
+    __syncthreads();
+    for (int cell = threadIdx.x; cell < kOut; cell += blockDim.x) {
+      const int ox = cell & 15, oy = (cell >> 4) & 15, oz = cell >> 8;
+      unsigned long long acc[kC1 / 2];
+#pragma unroll
+      for (int q = 0; q < kC1 / 2; ++q) acc[q] = ((const unsigned long long *)bias)[q];
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz) {
+        const int iz = 2 * oz + dz - 1;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          const int iy = 2 * oy + dy - 1;
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) {
+            const int ix = 2 * ox + dx - 1;
+            const bool in = iz >= 0 && iz < kCrop && iy >= 0 && iy < kCrop && ix >= 0 && ix < kCrop;
+            const int code = in ? s_code[(iz * kCrop + iy) * kCrop + ix] : 0;
+            const float4 *row = (const float4 *)(tab + ((dz * 9 + dy * 3 + dx) * kCodes + code) * kRowPad);
+#pragma unroll
+            for (int q = 0; q < kC1 / 4; ++q) {
+              const float4 w = row[q];
+              const ulonglong2 wp = *(const ulonglong2 *)&w;
+              acc[2 * q] = add_f32x2(acc[2 * q], wp.x);
+              acc[2 * q + 1] = add_f32x2(acc[2 * q + 1], wp.y);
+            }
+          }
+        }
+      }
+      uint4 out[2];
+      uint32_t *u = (uint32_t *)out;
+#pragma unroll
+      for (int q = 0; q < kC1 / 2; ++q) {
+        const float2 f = *(const float2 *)&acc[q];
+        const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(f.x, 0.0f), fmaxf(f.y, 0.0f));
+        u[q] = *(const uint32_t *)&h;
+      }
+      uint4 *dst = (uint4 *)(act0 + (v * (int64_t)kOut + cell) * kC1);
+      dst[0] = out[0];
+      dst[1] = out[1];
+    }
+  }
+}
+
+// Layer 0 weight gradient on one-hot crops: dW0[co][tap][class] is the sum
+// of dy[o][co] over the output voxels o whose tap input has that class.  CTA
+// c reduces output voxels [c chunk, (c + 1) chunk) in order into
+// part[c][tap][class][co]; conv0_wgrad_reduce_kernel adds the chunks in
+// order (deterministic).
+constexpr int kW0Sub = 128;   // output voxels staged in shared memory at a time
+
+__global__ void __launch_bounds__(256) conv0_wgrad_kernel(const uint8_t *__restrict__ codes,
+                                                          const bf16 *__restrict__ dy, int64_t n_out, int64_t chunk,
+                                                          float *__restrict__ part) {
+  __shared__ uint8_t s_code[kW0Sub][28];
+  __shared__ float s_dy[kW0Sub][kC1];
+  const int64_t o0 = blockIdx.x * chunk, o1 = min(n_out, o0 + chunk);
+  float acc[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};   // pairs (tap, co) = threadIdx.x, + 256
+  for (int64_t b = o0; b < o1; b += kW0Sub) {
+    const int nb = (int)min((int64_t)kW0Sub, o1 - b);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * 27; e += blockDim.x) {
+      const int k = e / 27, tap = e % 27;
+      const int64_t o = b + k;
+      const int cell = (int)(o & 4095);
+      const int ox = cell & 15, oy = (cell >> 4) & 15, oz = cell >> 8;
+      const int iz = 2 * oz + tap / 9 - 1, iy = 2 * oy + (tap / 3) % 3 - 1, ix = 2 * ox + tap % 3 - 1;
+      const bool in = iz >= 0 && iz < kCrop && iy >= 0 && iy < kCrop && ix >= 0 && ix < kCrop;
+      s_code[k][tap] = in ? codes[(o >> 12) * (int64_t)(kCrop * kCrop * kCrop) + (iz * kCrop + iy) * kCrop + ix] : 0;
+    }
+    for (int e = threadIdx.x; e < nb * kC1; e += blockDim.x) s_dy[e / kC1][e % kC1] = __bfloat162float(dy[b * kC1 + e]);
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int pidx = threadIdx.x + 256 * h;
+      if (pidx < 27 * kC1) {
+        const int tap = pidx / kC1, co = pidx % kC1;
+        for (int k = 0; k < nb; ++k) {
+          const int code = s_code[k][tap];
+          const float g = s_dy[k][co];
+          acc[h][0] += code == 1 ? g : 0.0f;
+          acc[h][1] += code == 2 ? g : 0.0f;
+          acc[h][2] += code == 3 ? g : 0.0f;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int pidx = threadIdx.x + 256 * h;
+    if (pidx < 27 * kC1) {
+      const int tap = pidx / kC1, co = pidx % kC1;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) part[((int64_t)blockIdx.x * 27 * 3 + tap * 3 + c) * kC1 + co] = acc[h][c];
+    }
+  }
+}
+
+__global__ void conv0_wgrad_reduce_kernel(const float *__restrict__ part, int chunks, float *__restrict__ dw) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;   // e = co * 27 * kC0 + tap * kC0 + c
+  if (e >= kC1 * 27 * kC0) return;
+  const int co = e / (27 * kC0), tap = (e / kC0) % 27, c = e % kC0;
+  float acc = 0.0f;
+  if (c < 3)
+    for (int z = 0; z < chunks; ++z) acc += part[((int64_t)z * 27 * 3 + tap * 3 + c) * kC1 + co];
+  dw[e] = acc;
 }
 
 // X[:, 4096:4104] = feats.
@@ -664,9 +812,15 @@ int check_net(nbt_surrogate n) {
 }
 
 // Forward pass of n <= max_batch samples: crops [n, 32^3, 8], feats [n, 8].
-int forward_batch(nbt_surrogate net, const bf16 *crops, const bf16 *feats, int n, float *pred, cudaStream_t s) {
-  const bf16 *in = crops;
-  for (int l = 0; l < kLayers; ++l) {
+int forward_batch(nbt_surrogate net, const uint8_t *crops, const bf16 *feats, int n, float *pred, cudaStream_t s) {
+  {
+    const int64_t grid = std::min<int64_t>(n, (int64_t)sm_count() * 4);
+    conv0_lookup_kernel<<<(unsigned)grid, 256, 0, s>>>(crops, net->wb + kP.w[0], net->params + kP.b[0], n,
+                                                       net->act[0]);
+    NBT_CUDA_TRY(cudaGetLastError());
+  }
+  const bf16 *in = net->act[0];
+  for (int l = 1; l < kLayers; ++l) {
     const LayerDims &L = kL[l];
     const int M = n * L.dout * L.dout * L.dout;
     const ConvFwdLoader la{in, M, L.din, L.stride, ilog2(L.dout), ilog2(L.cin / 8), L.cin};
@@ -702,7 +856,7 @@ int sync_weights(nbt_surrogate net, cudaStream_t s) {
 }
 
 // Forward + backward of one batch; gradients into net->grads, loss into net->loss.
-int backward_batch(nbt_surrogate net, const bf16 *crops, const bf16 *feats, const float *targets, int n,
+int backward_batch(nbt_surrogate net, const uint8_t *crops, const bf16 *feats, const float *targets, int n,
                    cudaStream_t s) {
   int rc = forward_batch(net, crops, feats, n, net->y, s);
   if (rc != NBT_OK) return rc;
@@ -731,11 +885,23 @@ int backward_batch(nbt_surrogate net, const bf16 *crops, const bf16 *feats, cons
   for (int l = kLayers - 1; l >= 0; --l) {
     const LayerDims &L = kL[l];
     const int Mout = n * L.dout * L.dout * L.dout;
-    const bf16 *in = l == 0 ? crops : net->act[l - 1];
     const bf16 *dy = net->dact[l];
     // bias gradient
     colsum_kernel<<<(L.cout * 32 + 255) / 256, 256, 0, s>>>(dy, Mout, L.cout, net->grads + kP.b[l]);
     NBT_CUDA_TRY(cudaGetLastError());
+    if (l == 0) {
+      // one-hot input: a table reduction instead of a GEMM
+      const int64_t max_chunks = kSplitBytes / (27 * 3 * kC1 * 4);
+      const int64_t chunk = std::max<int64_t>(kW0Sub, (Mout + max_chunks - 1) / max_chunks);
+      const int chunks = (int)((Mout + chunk - 1) / chunk);
+      conv0_wgrad_kernel<<<chunks, 256, 0, s>>>(crops, dy, Mout, chunk, net->part);
+      NBT_CUDA_TRY(cudaGetLastError());
+      conv0_wgrad_reduce_kernel<<<(kC1 * 27 * kC0 + 255) / 256, 256, 0, s>>>(net->part, chunks,
+                                                                            net->grads + kP.w[0]);
+      NBT_CUDA_TRY(cudaGetLastError());
+      break;
+    }
+    const bf16 *in = net->act[l - 1];
     // weight gradient: split-K over output voxels, then a fixed-order reduction
     const int krows = 27 * L.cin;
     const int mtiles = (krows + tc::kBM - 1) / tc::kBM;
@@ -878,7 +1044,7 @@ int nbt_surrogate_crops(nbt_map map, const nbt_pose *poses, int64_t n, const nbt
   if (rc != NBT_OK) return rc;
   if (n < 0 || !cam || !params) return NBT_EINVAL;
   if (n == 0) return NBT_OK;
-  if (!poses || !crops || !feats || ((uintptr_t)crops & 15u)) return NBT_EINVAL;
+  if (!poses || !crops || !feats) return NBT_EINVAL;
   if (!(cam->fov_h > 0.0f && cam->fov_h < 3.14159f) || !(cam->fov_v > 0.0f && cam->fov_v < 3.14159f) ||
       !(cam->max_range > 0.0f))
     return NBT_EINVAL;
@@ -906,16 +1072,17 @@ int nbt_surrogate_crops(nbt_map map, const nbt_pose *poses, int64_t n, const nbt
   m.ny = map->desc.ny;
   m.nz = map->desc.nz;
   cudaStream_t s = (cudaStream_t)stream;
-  const int grid = grid_1d(n * kCrop * kCrop * kCrop);
+  const int grid = (int)std::min<int64_t>(n, (int64_t)sm_count() * 8);
   switch (map->desc.encoding) {
     case NBT_F32_PROB:
-      crop_kernel<PAYLOAD_GAIN_F32><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (bf16 *)crops, (bf16 *)feats);
+      crop_kernel<PAYLOAD_GAIN_F32><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (uint8_t *)crops,
+                                                         (bf16 *)feats);
       break;
     case NBT_U2_STATE:
-      crop_kernel<PAYLOAD_U2><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (bf16 *)crops, (bf16 *)feats);
+      crop_kernel<PAYLOAD_U2><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (uint8_t *)crops, (bf16 *)feats);
       break;
     default:
-      crop_kernel<PAYLOAD_U8><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (bf16 *)crops, (bf16 *)feats);
+      crop_kernel<PAYLOAD_U8><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (uint8_t *)crops, (bf16 *)feats);
       break;
   }
   NBT_CUDA_TRY(cudaGetLastError());
@@ -928,12 +1095,12 @@ int nbt_surrogate_forward(nbt_surrogate net, const void *crops, const void *feat
   if (rc != NBT_OK) return rc;
   if (n < 0) return NBT_EINVAL;
   if (n == 0) return NBT_OK;
-  if (!crops || !feats || !pred || ((uintptr_t)crops & 15u)) return NBT_EINVAL;
+  if (!crops || !feats || !pred) return NBT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t per = (int64_t)kCrop * kCrop * kCrop * kC0;
+  const int64_t per = (int64_t)kCrop * kCrop * kCrop;
   for (int64_t b0 = 0; b0 < n; b0 += net->max_batch) {
     const int nb = (int)std::min<int64_t>(net->max_batch, n - b0);
-    rc = forward_batch(net, (const bf16 *)crops + b0 * per, (const bf16 *)feats + b0 * kFeat, nb, pred + b0, s);
+    rc = forward_batch(net, (const uint8_t *)crops + b0 * per, (const bf16 *)feats + b0 * kFeat, nb, pred + b0, s);
     if (rc != NBT_OK) return rc;
   }
   return NBT_OK;
@@ -945,7 +1112,7 @@ int nbt_surrogate_backward(nbt_surrogate net, const void *crops, const void *fea
   if (rc != NBT_OK) return rc;
   if (n < 1 || n > net->max_batch || n > 1024 || !crops || !feats || !targets) return NBT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  rc = backward_batch(net, (const bf16 *)crops, (const bf16 *)feats, targets, n, s);
+  rc = backward_batch(net, (const uint8_t *)crops, (const bf16 *)feats, targets, n, s);
   if (rc != NBT_OK) return rc;
   if (grads_out) NBT_CUDA_TRY(cudaMemcpyAsync(grads_out, net->grads, kP.total * 4, cudaMemcpyDeviceToDevice, s));
   if (loss_out) NBT_CUDA_TRY(cudaMemcpyAsync(loss_out, net->loss, 4, cudaMemcpyDeviceToDevice, s));

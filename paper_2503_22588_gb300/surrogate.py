@@ -22,6 +22,20 @@ SHAPES = ([item for i, (ci, co, _) in enumerate(LAYERS) for item in ((f"w{i}", (
           + [("f1", (HIDDEN, FC_IN)), ("g1", (HIDDEN,)), ("f2", (HIDDEN,)), ("g2", (1,))])
 
 
+def he_init(seed: int) -> dict:
+    """Seeded starting parameters: He-normal weights (std sqrt(2 / fan_in)), zero biases."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for k, shp in SHAPES:
+        if len(shp) == 2:
+            out[k] = (rng.standard_normal(shp) * np.sqrt(2.0 / shp[1])).astype(np.float32)
+        elif k == "f2":
+            out[k] = (rng.standard_normal(shp) * np.sqrt(1.0 / shp[0])).astype(np.float32)
+        else:
+            out[k] = np.zeros(shp, np.float32)
+    return out
+
+
 def param_count() -> int:
     n = C.c_int64()
     check(lib().nbt_surrogate_param_count(C.byref(n)), "nbt_surrogate_param_count")
@@ -44,11 +58,22 @@ def unpack(flat: np.ndarray) -> dict:
     return out
 
 
-def crops(m: Map, poses: torch.Tensor, cam: Camera, params: IgParams, stream=None):
-    """nbt_surrogate_crops: (crops bf16 [n, 32, 32, 32, 8], feats bf16 [n, 8]) on the poses' device."""
+def crops(m: Map, poses: torch.Tensor, cam: Camera, params: IgParams, stream=None, out=None):
+    """nbt_surrogate_crops: (crop codes uint8 [n, 32, 32, 32], feats bf16 [n, 8]) on the poses' device.
+
+    Code 0: outside the map; 1 unknown, 2 free, 3 occupied (one-hot channel code - 1).
+
+    ``out``: optional preallocated (crops, feats) with room for at least n
+    rows; the first n rows are written and returned.
+    """
     n = poses.shape[0]
-    cr = torch.empty((n, CROP, CROP, CROP, C0), dtype=torch.bfloat16, device=poses.device)
-    ft = torch.empty((n, FEATS), dtype=torch.bfloat16, device=poses.device)
+    if out is None:
+        cr = torch.empty((n, CROP, CROP, CROP), dtype=torch.uint8, device=poses.device)
+        ft = torch.empty((n, FEATS), dtype=torch.bfloat16, device=poses.device)
+    else:
+        cr, ft = out[0][:n], out[1][:n]
+        _dev(cr, torch.uint8, "crops")
+        _dev(ft, torch.bfloat16, "feats")
     if n:
         check(lib().nbt_surrogate_crops(m.handle, _dev(poses, torch.float32, "poses", (7,)), n, C.byref(cam),
                                         C.byref(params), cr.data_ptr(), ft.data_ptr(), _stream(stream)),
@@ -85,7 +110,7 @@ class Surrogate:
         n = crops_t.shape[0]
         out = out if out is not None else torch.empty(n, dtype=torch.float32, device=crops_t.device)
         if n:
-            check(lib().nbt_surrogate_forward(self.handle, _dev(crops_t, torch.bfloat16, "crops"),
+            check(lib().nbt_surrogate_forward(self.handle, _dev(crops_t, torch.uint8, "crops"),
                                               _dev(feats, torch.bfloat16, "feats"), n,
                                               _dev(out, torch.float32, "pred"), _stream(stream)),
                   "nbt_surrogate_forward")
@@ -96,7 +121,7 @@ class Surrogate:
         n = crops_t.shape[0]
         grads = torch.empty(self.n_params, dtype=torch.float32, device=crops_t.device)
         loss = torch.empty(1, dtype=torch.float32, device=crops_t.device)
-        check(lib().nbt_surrogate_backward(self.handle, _dev(crops_t, torch.bfloat16, "crops"),
+        check(lib().nbt_surrogate_backward(self.handle, _dev(crops_t, torch.uint8, "crops"),
                                            _dev(feats, torch.bfloat16, "feats"),
                                            _dev(targets, torch.float32, "targets"), n, grads.data_ptr(),
                                            loss.data_ptr(), _stream(stream)), "nbt_surrogate_backward")
@@ -105,7 +130,7 @@ class Surrogate:
     def train_step(self, crops_t, feats, targets, lr: float, loss: torch.Tensor | None = None, stream=None):
         n = crops_t.shape[0]
         loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=crops_t.device)
-        check(lib().nbt_surrogate_train_step(self.handle, _dev(crops_t, torch.bfloat16, "crops"),
+        check(lib().nbt_surrogate_train_step(self.handle, _dev(crops_t, torch.uint8, "crops"),
                                              _dev(feats, torch.bfloat16, "feats"),
                                              _dev(targets, torch.float32, "targets"), n, float(lr),
                                              loss.data_ptr(), _stream(stream)), "nbt_surrogate_train_step")

@@ -1,6 +1,6 @@
 """The learned surrogate's CUDA kernels against the FP64 oracle (GPU required).
 
-Crops: byte-exact.  Forward: relative 2e-2 against the oracle evaluated with
+Crops: the class codes byte-exact (the oracle's one-hot crops, coded).  Forward: relative 2e-2 against the oracle evaluated with
 the same BF16 rounding of weights and activations (the only remaining
 differences are FP32-vs-FP64 accumulation and the BF16 roundings that flips
 in it cause).  Gradients: relative L2 error per tensor <= 5e-2 (the GPU also
@@ -71,14 +71,15 @@ def test_crops_bitexact(enc):
     prm = nbt.ig_params("count" if enc != "f32" else "entropy")
     m = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01, (0.0, 0.0, 0.0), enc)
     cr, ft = gs.crops(m, torch.from_numpy(p).cuda(), cam, prm)
-    cr = cr.float().cpu().numpy()
+    assert cr.dtype == torch.uint8 and cr.shape == (len(p), 32, 32, 32)
+    cr = cr.cpu().numpy()
     ft = ft.float().cpu().numpy()
     cc = S.crop_consts(math.radians(60), math.radians(45), 0.5)
     for v in range(3):
         oc, of = S.frustum_crop(grid, 0.01, (0, 0, 0), p[v], cc)
-        assert np.array_equal(cr[v].astype(np.uint8), oc), v
+        assert np.array_equal(cr[v], S.crop_codes(oc)), v
         assert np.array_equal(ft[v], S._bf16(of).astype(np.float32)), v
-        assert oc[..., 0].any() and oc[..., 1].any()
+        assert oc[..., 0].any() and oc[..., 1].any() and (cr[v] == 0).any()
 
 
 def _batch(n_views=6, seed=2):
@@ -96,7 +97,8 @@ def test_forward_matches_oracle():
     params["g1"] += 0.02
     net = gs.Surrogate(max_batch=4, params=params)   # 6 samples: two passes
     pred = net.forward(cr, ft).cpu().numpy().astype(np.float64)
-    y, _ = S.forward(as_used_by_gpu(params), cr.float().cpu().numpy(), ft.float().cpu().numpy(), bf16_activations=True)
+    y, _ = S.forward(as_used_by_gpu(params), S.codes_to_onehot(cr.cpu().numpy()), ft.float().cpu().numpy(),
+                     bf16_activations=True)
     assert no_device_timeout()
     assert np.allclose(pred, y, rtol=2e-2, atol=2e-2 * np.abs(y).max()), (pred, y)
     net.close()
@@ -112,8 +114,8 @@ def test_backward_matches_oracle_gradients():
     torch.cuda.synchronize()
     assert no_device_timeout()
     g = gs.unpack(grads.cpu().numpy())
-    oloss, og = S.loss_and_grads(as_used_by_gpu(params), cr.float().cpu().numpy(), ft.float().cpu().numpy(),
-                                 t.cpu().numpy(), bf16_activations=True)
+    oloss, og = S.loss_and_grads(as_used_by_gpu(params), S.codes_to_onehot(cr.cpu().numpy()),
+                                 ft.float().cpu().numpy(), t.cpu().numpy(), bf16_activations=True)
     assert abs(loss.item() - oloss) <= 2e-2 * abs(oloss)
     for k in og:
         err = rel_l2(g[k], og[k])

@@ -160,3 +160,12 @@ def test_frustum_crop_probability_classes():
     ok = np.all(np.abs(pts - np.round(pts)) > 1e-4, axis=-1)
     cls = np.where(x < 10, 1, np.where(x < 15, 0, 2))
     assert np.all((crop.argmax(-1) == cls)[ok])
+
+
+def test_crop_codes_round_trip():
+    rng = np.random.default_rng(9)
+    codes = rng.integers(0, 4, (3, 5, 5, 5)).astype(np.uint8)
+    oh = S.codes_to_onehot(codes)
+    assert oh.shape == (3, 5, 5, 5, 8) and np.all(oh.sum(-1) == (codes > 0))
+    assert np.all(oh[codes == 2][:, 1] == 1.0) and np.all(oh[..., 3:] == 0.0)
+    assert np.array_equal(S.crop_codes(oh), codes)
