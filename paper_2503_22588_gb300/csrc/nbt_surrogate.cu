@@ -84,12 +84,17 @@ __device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
 
 // Row-major K-major BF16 matrix [rows, K], row stride ld elements.
 struct MatLoader {
+  static constexpr bool kAsync = true;
   const bf16 *p;
   int rows, K, ld;
-  __device__ __forceinline__ uint4 chunk(int r, int kc) const {
+  __device__ __forceinline__ const void *src(int r, int kc) const {
     const int k = kc * 8;
-    if (r >= rows || k >= K) return zero4();
-    return __ldg((const uint4 *)(p + (size_t)r * ld + k));
+    return (r >= rows || k >= K) ? nullptr : (const void *)(p + (size_t)r * ld + k);
+  }
+  __device__ __forceinline__ const void *base() const { return p; }
+  __device__ __forceinline__ uint4 chunk(int r, int kc) const {
+    const void *q = src(r, kc);
+    return q ? __ldg((const uint4 *)q) : zero4();
   }
   template <int ROWS>
   __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
@@ -100,19 +105,25 @@ struct MatLoader {
 // Implicit im2col of a 3^3 convolution (padding 1): row m = output voxel
 // (b, oz, oy, ox), K index = tap * cin + ci with tap = (dz*3 + dy)*3 + dx.
 struct ConvFwdLoader {
+  static constexpr bool kAsync = true;
   const bf16 *x;
   int M, D, stride, sh_do, sh_cg, cin;
-  __device__ __forceinline__ uint4 chunk(int m, int kc) const {
-    if (m >= M) return zero4();
+  __device__ __forceinline__ const void *src(int m, int kc) const {
+    if (m >= M) return nullptr;
     const int tap = kc >> sh_cg;
-    if (tap >= 27) return zero4();
+    if (tap >= 27) return nullptr;
     const int cg = kc & ((1 << sh_cg) - 1);
     const int dmask = (1 << sh_do) - 1;
     const int ox = m & dmask, oy = (m >> sh_do) & dmask, oz = (m >> (2 * sh_do)) & dmask, b = m >> (3 * sh_do);
     const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
     const int iz = oz * stride + dz - 1, iy = oy * stride + dy - 1, ix = ox * stride + dx - 1;
-    if ((unsigned)iz >= (unsigned)D || (unsigned)iy >= (unsigned)D || (unsigned)ix >= (unsigned)D) return zero4();
-    return __ldg((const uint4 *)(x + ((((size_t)b * D + iz) * D + iy) * D + ix) * cin + cg * 8));
+    if ((unsigned)iz >= (unsigned)D || (unsigned)iy >= (unsigned)D || (unsigned)ix >= (unsigned)D) return nullptr;
+    return x + ((((size_t)b * D + iz) * D + iy) * D + ix) * cin + cg * 8;
+  }
+  __device__ __forceinline__ const void *base() const { return x; }
+  __device__ __forceinline__ uint4 chunk(int m, int kc) const {
+    const void *q = src(m, kc);
+    return q ? __ldg((const uint4 *)q) : zero4();
   }
   template <int ROWS>
   __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
@@ -125,22 +136,28 @@ struct ConvFwdLoader {
 // tap d reads i from is o = (i + 1 - d) / s when that is integral and in
 // range (forward: i = o*s + d - 1).
 struct ConvBwdDataLoader {
+  static constexpr bool kAsync = true;
   const bf16 *dy;
   int M, Di, Do, sh_s, sh_di, sh_cg, cout;
-  __device__ __forceinline__ uint4 chunk(int m, int kc) const {
-    if (m >= M) return zero4();
+  __device__ __forceinline__ const void *src(int m, int kc) const {
+    if (m >= M) return nullptr;
     const int tap = kc >> sh_cg;
-    if (tap >= 27) return zero4();
+    if (tap >= 27) return nullptr;
     const int cg = kc & ((1 << sh_cg) - 1);
     const int dmask = (1 << sh_di) - 1;
     const int ix = m & dmask, iy = (m >> sh_di) & dmask, iz = (m >> (2 * sh_di)) & dmask, b = m >> (3 * sh_di);
     const int dz = tap / 9, dy_ = (tap / 3) % 3, dx = tap % 3;
     const int tz = iz + 1 - dz, ty = iy + 1 - dy_, tx = ix + 1 - dx;
     const int smask = (1 << sh_s) - 1;
-    if (tz < 0 || ty < 0 || tx < 0 || (tz & smask) || (ty & smask) || (tx & smask)) return zero4();
+    if (tz < 0 || ty < 0 || tx < 0 || (tz & smask) || (ty & smask) || (tx & smask)) return nullptr;
     const int oz = tz >> sh_s, oy = ty >> sh_s, ox = tx >> sh_s;
-    if (oz >= Do || oy >= Do || ox >= Do) return zero4();
-    return __ldg((const uint4 *)(dy + ((((size_t)b * Do + oz) * Do + oy) * Do + ox) * cout + cg * 8));
+    if (oz >= Do || oy >= Do || ox >= Do) return nullptr;
+    return dy + ((((size_t)b * Do + oz) * Do + oy) * Do + ox) * cout + cg * 8;
+  }
+  __device__ __forceinline__ const void *base() const { return dy; }
+  __device__ __forceinline__ uint4 chunk(int m, int kc) const {
+    const void *q = src(m, kc);
+    return q ? __ldg((const uint4 *)q) : zero4();
   }
   template <int ROWS>
   __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
@@ -152,6 +169,7 @@ struct ConvBwdDataLoader {
 // voxels m.  Each thread loads the 8 channels of one input voxel (16 bytes)
 // and writes them transposed into 8 stage rows at K position m.
 struct WgradColLoader {
+  static constexpr bool kAsync = false;
   const bf16 *x;
   int Mout, D, stride, sh_do, cin;
   template <int ROWS>
@@ -185,6 +203,7 @@ struct WgradColLoader {
 // Weight gradient, operand B: rows = output channels co, K = output voxels
 // m, from the NDHWC output gradient (16-byte vectors transposed into rows).
 struct WgradDyLoader {
+  static constexpr bool kAsync = false;
   const bf16 *dy;
   int Mout, cout;
   template <int ROWS>
@@ -745,8 +764,16 @@ int launch_gemm(const LA &la, const LB &lb, const EP &ep, int M, int N, int K, i
   int *err = nullptr;
   int rc = dev_err_word(&err);
   if (rc != NBT_OK) return rc;
-  const size_t smem = tc::gemm_smem_bytes(BN);
-  auto kern = tc::gemm_kernel<BN, LA, LB, EP>;
+  // loaders that name a 16-byte source per chunk get the cp.async pipeline
+  void (*kern)(LA, LB, EP, int, int, int, int *);
+  size_t smem;
+  if constexpr (LA::kAsync && LB::kAsync) {
+    kern = tc::gemm_async_kernel<BN, LA, LB, EP>;
+    smem = tc::gemm_async_smem_bytes(BN);
+  } else {
+    kern = tc::gemm_kernel<BN, LA, LB, EP>;
+    smem = tc::gemm_smem_bytes(BN);
+  }
   NBT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int kt_all = (K + tc::kBK - 1) / tc::kBK;
   splits = std::max(1, std::min(splits, kt_all));

@@ -246,5 +246,134 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(LoadA la, LoadB lb, Epi 
   if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous variant for loaders whose chunks are plain 16-byte copies
+// (`const void *src(int row, int kchunk)`, nullptr where the operand is
+// zero, and `const void *base()`, any valid address of the operand): the
+// stages are filled with cp.async, kAsyncStages deep, so the gathers of the
+// next stages are in flight while the tensor core works on the current one.
+// A stage is refilled only after the mbarrier of the MMAs that read it has
+// completed.
+// ---------------------------------------------------------------------------
+constexpr int kAsyncStages = 4;
+
+__host__ __device__ constexpr size_t gemm_async_smem_bytes(int bn) { return kAsyncStages * stage_bytes(bn) + 1024; }
+
+// 16-byte global -> shared copy; zero-fills when !valid (no bytes are read).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int ROWS, class L>
+__device__ __forceinline__ void fill_async(const L &l, uint8_t *stage, int row0, int kc0, int tid) {
+  const uint32_t base = smem_u32(stage);
+  for (int c = tid; c < ROWS * 8; c += kThreads) {
+    const int r = c % ROWS, kc = c / ROWS;
+    const void *p = l.src(row0 + r, kc0 + kc);
+    cp_async16(base + stage_off(r, kc, ROWS), p ? p : l.base(), p != nullptr);
+  }
+}
+
+template <int BN, class LoadA, class LoadB, class Epi>
+__global__ void __launch_bounds__(kThreads) gemm_async_kernel(LoadA la, LoadB lb, Epi epi, int M, int K,
+                                                              int kt_split, int *err) {
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
+  constexpr int S = kAsyncStages;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t mbar[S];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN, z = blockIdx.z;
+  constexpr uint32_t NCOLS = (uint32_t)tmem_cols(BN);
+  if (warp == 0) tmem_alloc(&tmem_base, NCOLS);
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < S; ++i) mbar_init(&mbar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+  const int kt_all = (K + kBK - 1) / kBK;
+  const int kt_begin = z * kt_split;
+  const int nk = max(0, min(kt_all, kt_begin + kt_split) - kt_begin);
+  auto load_stage = [&](int it) {
+    uint8_t *sa = smem + (it % S) * stage_bytes(BN);
+    const int kc0 = (kt_begin + it) * (kBK / 8);
+    fill_async<kBM>(la, sa, m0, kc0, tid);
+    fill_async<BN>(lb, sa + kBM * kBK * 2, n0, kc0, tid);
+  };
+#pragma unroll
+  for (int it = 0; it < S - 1; ++it) {
+    if (it < nk) load_stage(it);
+    cp_async_commit();
+  }
+  bool ok = true;
+  int issued = 0;
+  for (int it = 0; it < nk; ++it) {
+    cp_async_wait<S - 2>();   // this thread's copies of k-tile `it` have landed
+    fence_smem_async();
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    if (tid == 0) {
+      fence_after_sync();
+      const uint32_t a0 = smem_u32(smem + (it % S) * stage_bytes(BN));
+      const uint32_t b0 = a0 + kBM * kBK * 2;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t ad = sdesc(a0 + kk * (kBM * 32), 128, 256);
+        const uint64_t bd = sdesc(b0 + kk * (BN * 32), 128, 256);
+        mma_bf16(tmem, ad, bd, idesc, (it | kk) != 0 ? 1u : 0u);
+      }
+      mma_commit(&mbar[it % S]);
+    }
+    ++issued;
+    // refill the stage the MMAs of k-tile it - 1 read, once they are done
+    const int nxt = it + S - 1;
+    if (nxt < nk) {
+      if (it >= 1) ok = mbar_wait(&mbar[(it - 1) % S], (uint32_t)((it - 1) / S) & 1u);
+      if (ok) load_stage(nxt);
+    }
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
+  if (ok && issued > 0) {
+    const int kl = issued - 1;
+    ok = mbar_wait(&mbar[kl % S], (uint32_t)(kl / S) & 1u);
+  }
+  ok = __syncthreads_and(ok) != 0;
+  fence_after_sync();
+  if (ok) {
+    const int row = m0 + warp * 32 + (tid & 31);
+#pragma unroll 1
+    for (int nn = 0; nn < BN; nn += 16) {
+      float v[16];
+      if (issued > 0) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)nn, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.0f;  // empty K split: contributes zeros
+      }
+      if (row < M) epi.row(row, n0 + nn, v, z);
+    }
+  } else {
+    if (tid == 0) atomicExch(err, 1);
+    // wait (bounded) for every committed stage before freeing the accumulator
+    for (int k = (issued > S ? issued - S : 0); k < issued; ++k) (void)mbar_wait(&mbar[k % S], (uint32_t)(k / S) & 1u);
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
 }  // namespace tc
 }  // namespace nbt
