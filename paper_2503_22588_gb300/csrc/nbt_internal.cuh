@@ -121,11 +121,10 @@ __device__ __forceinline__ void quat_rot_f32(const float *q, float r[9]) {
   r[8] = fsub(1.0f, fmul(2.0f, fadd(xx, yy)));
 }
 
-// Segment (voxel units) of ray (i, j) for a pose: Section III endpoint grid.
-__device__ __forceinline__ void ray_segment(const CamConst &cc, const float *pose, int i, int j, float o[3],
-                                            float d[3]) {
-  float r[9];
-  quat_rot_f32(pose + 3, r);
+// Segment (voxel units) of ray (i, j) for a pose whose rotation r =
+// quat_rot_f32(pose + 3) is given: Section III endpoint grid.
+__device__ __forceinline__ void ray_segment_rot(const CamConst &cc, const float *pose, const float *r, int i, int j,
+                                                float o[3], float d[3]) {
   float cx = fadd(cc.x0, fmul((float)i, cc.xstep));
   float cy = fadd(cc.y0, fmul((float)j, cc.ystep));
   float cz = cc.zc;
@@ -143,6 +142,13 @@ __device__ __forceinline__ void ray_segment(const CamConst &cc, const float *pos
     o[a] = fmul(fsub(pose[a], org[a]), cc.inv_s);
     d[a] = fmul(wa, cc.inv_s);
   }
+}
+
+__device__ __forceinline__ void ray_segment(const CamConst &cc, const float *pose, int i, int j, float o[3],
+                                            float d[3]) {
+  float r[9];
+  quat_rot_f32(pose + 3, r);
+  ray_segment_rot(cc, pose, r, i, j, o, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -196,7 +202,7 @@ __device__ __forceinline__ bool walk_init(Walk &w, const float o[3], const float
   for (int a = 0; a < 3; ++a) {
     const float n = (float)dims[a];
     if (d[a] != 0.0f) {
-      inv[a] = __fdiv_rn(1.0f, d[a]);
+      inv[a] = __frcp_rn(d[a]);  // correctly rounded 1 / d_a
       const float t0 = fmul(fsub(0.0f, o[a]), inv[a]);
       const float t1 = fmul(fsub(n, o[a]), inv[a]);
       const float lo = inv[a] > 0.0f ? t0 : t1;

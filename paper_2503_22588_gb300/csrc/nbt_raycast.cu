@@ -121,6 +121,96 @@ __device__ __forceinline__ uint32_t raw_load(const void *payload, uint32_t off) 
   return __ldg((const uint8_t *)payload + (off >> 2));
 }
 
+// FP32-gain walk on the linear layout as one PTX loop (two voxels per pass,
+// registers r0 / r1 alternating as current and prefetched voxel).  Per voxel:
+// the walk_advance_lin step (same selection, same rounded operations; the
+// axis is the first of x, y, z whose crossing equals the three-input min,
+// which is walk_advance's tie-break since crossings are never NaN), the
+// read of the next voxel unless the walk ends there (that read does not wait
+// for the current voxel's value), then the current voxel's gain.  The walk
+// stops when the chosen crossing is not before t_max or the current voxel is
+// occupied (sign bit of its gain entry).
+// Gains are added in visit order, one rounding each, as in ray_ig; the walk
+// state advances once per visited voxel, so the plane travel counts them.
+__constant__ int c_unit = 1;
+
+template <bool HIT>
+__device__ __forceinline__ void walk_gain_f32(Walk &w, int &lin, uint32_t raw, const float *payload,
+                                              uint32_t addr_max, float &facc) {
+#define NBT_GAIN_BODY(CUR, NXT)                                                                  \
+  "min.f32 ts, %0, %1, %2;\n\t"                                                                 \
+  "setp.geu.f32 pm, ts, %18;\n\t"                                                               \
+  "setp.eq.f32 px, %0, ts;\n\t"                                                                 \
+  "setp.eq.and.f32 py, %1, ts, !px;\n\t"                                                        \
+  "setp.neu.and.f32 pz, %1, ts, !px;\n\t"                                                       \
+  "@px add.rn.f32 %3, %3, %9;\n\t"                                                              \
+  "@px sub.rn.f32 u, %3, %12;\n\t"                                                              \
+  "@px mul.rn.f32 %0, u, %15;\n\t"                                                              \
+  "@px mad.lo.s32 %6, %19, %24, %6;\n\t"                                                        \
+  "@py add.rn.f32 %4, %4, %10;\n\t"                                                             \
+  "@py sub.rn.f32 u, %4, %13;\n\t"                                                              \
+  "@py mul.rn.f32 %1, u, %16;\n\t"                                                              \
+  "@py mad.lo.s32 %6, %20, %24, %6;\n\t"                                                        \
+  "@pz add.rn.f32 %5, %5, %11;\n\t"                                                             \
+  "@pz sub.rn.f32 u, %5, %14;\n\t"                                                              \
+  "@pz mul.rn.f32 %2, u, %17;\n\t"                                                              \
+  "@pz mad.lo.s32 %6, %21, %24, %6;\n\t"                                                        \
+  "min.u32 lc, %6, %23;\n\t"                                                                    \
+  "mad.wide.u32 a, lc, 4, %22;\n\t"                                                             \
+  "@!pm ld.global.nc.b32 " NXT ", [a];\n\t"                                                     \
+  "abs.f32 g, " CUR ";\n\t"
+  // The index steps are multiply-adds by a unit read from constant memory
+  // (opaque to the compiler), so they run on the FMA pipe next to the
+  // float work instead of adding to the compare/select ALU pipe.
+  const int unit = c_unit;
+  if (HIT) {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred px, py, pz, pm, pe;\n\t"
+        ".reg .f32 ts, u, g;\n\t"
+        ".reg .b32 r0, r1, lc;\n\t"
+        ".reg .b64 a;\n\t"
+        "mov.b32 r0, %8;\n\t"
+        "LOOP:\n\t" NBT_GAIN_BODY("r0", "r1")
+        "setp.lt.or.s32 pe, r0, 0, pm;\n\t"
+        "add.rn.f32 %7, %7, g;\n\t"
+        "@pe bra DONE;\n\t" NBT_GAIN_BODY("r1", "r0")
+        "setp.lt.or.s32 pe, r1, 0, pm;\n\t"
+        "add.rn.f32 %7, %7, g;\n\t"
+        "@!pe bra LOOP;\n\t"
+        "DONE:\n\t"
+        "}"
+        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+f"(facc)
+        : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
+          "f"(w.vz), "f"(w.tmax), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred px, py, pz, pm, po, pe;\n\t"
+        ".reg .f32 ts, u, g;\n\t"
+        ".reg .b32 r0, r1, lc;\n\t"
+        ".reg .b64 a;\n\t"
+        "mov.b32 r0, %8;\n\t"
+        "LOOP:\n\t" NBT_GAIN_BODY("r0", "r1")
+        "setp.lt.s32 po, r0, 0;\n\t"
+        "or.pred pe, pm, po;\n\t"
+        "@!po add.rn.f32 %7, %7, g;\n\t"
+        "@pe bra DONE;\n\t" NBT_GAIN_BODY("r1", "r0")
+        "setp.lt.s32 po, r1, 0;\n\t"
+        "or.pred pe, pm, po;\n\t"
+        "@!po add.rn.f32 %7, %7, g;\n\t"
+        "@!pe bra LOOP;\n\t"
+        "DONE:\n\t"
+        "}"
+        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+f"(facc)
+        : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
+          "f"(w.vz), "f"(w.tmax), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit)
+        : "memory");
+  }
+#undef NBT_GAIN_BODY
+}
+
 // IG of one ray: walk, read, accumulate, stop after the first occupied voxel.
 // HIT: the occupied voxel adds its gain (the Section III sum runs to N_O).
 // LINEAR: linear layout with stride steps; else bricked with table reads.
@@ -144,9 +234,14 @@ __device__ __forceinline__ void ray_ig(const void *payload, const int32_t *tab, 
   uint32_t addr = min(LINEAR ? (uint32_t)lin : (uint32_t)(offx + offy + offz), addr_max);
   uint32_t raw = raw_load<KIND>(payload, addr);
   const float bx0 = w.bx, by0 = w.by, bz0 = w.bz;
-  // Three voxels per iteration for FP32 gains (fewer register moves and
-  // back-edges: 6 % faster on the 256^3 probability workload); the 1-byte
-  // and 2-bit payloads measured no gain from it.
+  if constexpr (LINEAR && KIND == PAYLOAD_GAIN_F32) {
+    walk_gain_f32<HIT>(w, lin, raw, (const float *)payload, addr_max, facc);
+    steps += (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
+    return;
+  }
+  // Three voxels per iteration for FP32 gains on bricked layouts (fewer
+  // register moves and back-edges; the linear FP32 case returned above);
+  // the 1-byte and 2-bit payloads measured no gain from it.
 #pragma unroll(KIND == PAYLOAD_GAIN_F32 ? 3 : 1)
   for (;;) {
     bool more;
@@ -239,10 +334,11 @@ __global__ void __launch_bounds__(kThreads, CHUNK ? 4 : (LINEAR ? 6 : 5))
     ig_tiles_kernel(DevMap m, CamConst cc, const float *__restrict__ poses, int64_t n_items, uint32_t addr_max,
                     unsigned long long *queue, Partial *partials) {
   extern __shared__ int32_t stab[];
-  __shared__ float s_pose[8];
+  __shared__ float s_pose[8], s_rot[9];
   __shared__ float s_f[kThreads / 32];
   __shared__ uint32_t s_i[kThreads / 32], s_s[kThreads / 32];
   __shared__ long long s_item;
+  __shared__ int s_x0, s_y0;
   if (!LINEAR) {
     const int ntab = m.nx + m.ny + m.nz;
     for (int k = threadIdx.x; k < ntab; k += blockDim.x) stab[k] = m.tab[k];
@@ -256,23 +352,29 @@ __global__ void __launch_bounds__(kThreads, CHUNK ? 4 : (LINEAR ? 6 : 5))
       const long long it = (long long)atomicAdd(queue, 1ull);
       s_item = it;
       if (it < n_items) {
+        // the item's pose, its rotation and the tile's first pixel, once per CTA
         const long long pose = it / cc.tiles_per_pose;
+        const int tile = (int)(it - pose * cc.tiles_per_pose);
+        float q[7], r[9];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) s_pose[k] = __ldg(poses + pose * 7 + k);
+        for (int k = 0; k < 7; ++k) s_pose[k] = q[k] = __ldg(poses + pose * 7 + k);
+        quat_rot_f32(q + 3, r);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s_rot[k] = r[k];
+        s_x0 = (tile % cc.tiles_x) * kTileW;
+        s_y0 = (tile / cc.tiles_x) * kTileH;
       }
     }
     __syncthreads();
     const long long item = s_item;
     if (item >= n_items) break;
-    const long long pose = item / cc.tiles_per_pose;
-    const int tile = (int)(item - pose * cc.tiles_per_pose);
-    const int i = (tile % cc.tiles_x) * kTileW + di;
-    const int j = (tile / cc.tiles_x) * kTileH + dj;
+    const int i = s_x0 + di;
+    const int j = s_y0 + dj;
     float facc = 0.0f;
     uint32_t iacc = 0u, steps = 0u;
     if (i < cc.W && j < cc.H) {
       float o[3], d[3];
-      ray_segment(cc, s_pose, i, j, o, d);
+      ray_segment_rot(cc, s_pose, s_rot, i, j, o, d);
       if constexpr (CHUNK > 0)
         ray_ig_chunked<KIND, HIT, CHUNK>(m.payload, addr_max, m.nx, m.ny, m.nz, o, d, facc, iacc, steps);
       else
