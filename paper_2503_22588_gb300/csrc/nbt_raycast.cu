@@ -137,7 +137,7 @@ __constant__ int c_unit = 1;
 template <bool HIT>
 __device__ __forceinline__ void walk_gain_f32(Walk &w, int &lin, uint32_t raw, const float *payload,
                                               uint32_t addr_max, float &facc) {
-#define NBT_GAIN_BODY(CUR, NXT)                                                                  \
+#define NBT_WALK_PART                                                                            \
   "min.f32 ts, %0, %1, %2;\n\t"                                                                 \
   "setp.geu.f32 pm, ts, %18;\n\t"                                                               \
   "setp.eq.f32 px, %0, ts;\n\t"                                                                 \
@@ -155,7 +155,9 @@ __device__ __forceinline__ void walk_gain_f32(Walk &w, int &lin, uint32_t raw, c
   "@pz sub.rn.f32 u, %5, %14;\n\t"                                                              \
   "@pz mul.rn.f32 %2, u, %17;\n\t"                                                              \
   "@pz mad.lo.s32 %6, %21, %24, %6;\n\t"                                                        \
-  "min.u32 lc, %6, %23;\n\t"                                                                    \
+  "min.u32 lc, %6, %23;\n\t"
+#define NBT_GAIN_BODY(CUR, NXT)                                                                  \
+  NBT_WALK_PART                                                                                  \
   "mad.wide.u32 a, lc, 4, %22;\n\t"                                                             \
   "@!pm ld.global.nc.b32 " NXT ", [a];\n\t"                                                     \
   "abs.f32 g, " CUR ";\n\t"
@@ -208,6 +210,81 @@ __device__ __forceinline__ void walk_gain_f32(Walk &w, int &lin, uint32_t raw, c
 #undef NBT_GAIN_BODY
 }
 
+// Count IG on 1-byte and 2-bit state maps (linear layout): the same PTX walk
+// as walk_gain_f32 (same selection, operations, clamp and three-voxel pass);
+// per voxel the unknown count grows by one for state 0 and the walk stops
+// after an occupied voxel (state >= 2).  2-bit states: four voxels per byte,
+// voxel v in bits 2 (v & 3) of byte v / 4; the byte is replicated into all
+// four byte lanes of a word (multiply by 0x01010101) so that a funnel shift
+// by 2 v (taken mod 32) brings bits 2 (v & 3) of one copy to bit 0.  The
+// +1 of the count and the 2 v are multiply-adds by opaque units, like the
+// index steps.
+template <int KIND>
+__device__ __forceinline__ void walk_count(Walk &w, int &lin, uint32_t raw, uint32_t addr, const uint8_t *payload,
+                                           uint32_t addr_max, uint32_t &iacc) {
+  const int unit = c_unit, two = unit + unit;
+  if constexpr (KIND == PAYLOAD_U8) {
+#define NBT_U8_BODY(CUR, NXT)                                                                    \
+  NBT_WALK_PART                                                                                  \
+  "mad.wide.u32 a, lc, %24, %22;\n\t"                                                           \
+  "@!pm ld.global.nc.u8 " NXT ", [a];\n\t"                                                      \
+  "setp.eq.u32 pu, " CUR ", 0;\n\t"                                                             \
+  "@pu mad.lo.s32 %7, %24, %24, %7;\n\t"                                                        \
+  "setp.gt.or.u32 pe, " CUR ", 1, pm;\n\t"
+    asm volatile(
+        "{\n\t"
+        ".reg .pred px, py, pz, pm, pu, pe;\n\t"
+        ".reg .f32 ts, u;\n\t"
+        ".reg .b32 r0, r1, r2, lc;\n\t"
+        ".reg .b64 a;\n\t"
+        "mov.b32 r0, %8;\n\t"
+        "LOOP:\n\t" NBT_U8_BODY("r0", "r1") "@pe bra DONE;\n\t"
+        NBT_U8_BODY("r1", "r2") "@pe bra DONE;\n\t"
+        NBT_U8_BODY("r2", "r0") "@!pe bra LOOP;\n\t"
+        "DONE:\n\t"
+        "}"
+        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+r"(iacc)
+        : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
+          "f"(w.vz), "f"(w.tmax), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit)
+        : "memory");
+#undef NBT_U8_BODY
+  } else {
+#define NBT_U2_BODY(CUR, SC, NXT, SN)                                                            \
+  NBT_WALK_PART                                                                                  \
+  "shr.u32 wb, lc, 2;\n\t"                                                                       \
+  "mad.wide.u32 a, wb, %24, %22;\n\t"                                                           \
+  "@!pm ld.global.nc.u8 " NXT ", [a];\n\t"                                                      \
+  "mad.lo.s32 " SN ", lc, %25, 0;\n\t"                                                          \
+  "mul.lo.u32 st, " CUR ", 16843009;\n\t"                                                       \
+  "shf.r.wrap.b32 st, st, st, " SC ";\n\t"                                                      \
+  "and.b32 st, st, 3;\n\t"                                                                      \
+  "setp.eq.u32 pu, st, 0;\n\t"                                                                  \
+  "@pu mad.lo.s32 %7, %24, %24, %7;\n\t"                                                        \
+  "setp.gt.or.u32 pe, st, 1, pm;\n\t"
+    const uint32_t s_first = addr * 2u;
+    asm volatile(
+        "{\n\t"
+        ".reg .pred px, py, pz, pm, pu, pe;\n\t"
+        ".reg .f32 ts, u;\n\t"
+        ".reg .b32 r0, r1, r2, s0, s1, s2, lc, wb, st;\n\t"
+        ".reg .b64 a;\n\t"
+        "mov.b32 r0, %8;\n\t"
+        "mov.b32 s0, %26;\n\t"
+        "LOOP:\n\t" NBT_U2_BODY("r0", "s0", "r1", "s1") "@pe bra DONE;\n\t"
+        NBT_U2_BODY("r1", "s1", "r2", "s2") "@pe bra DONE;\n\t"
+        NBT_U2_BODY("r2", "s2", "r0", "s0") "@!pe bra LOOP;\n\t"
+        "DONE:\n\t"
+        "}"
+        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+r"(iacc)
+        : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
+          "f"(w.vz), "f"(w.tmax), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit),
+          "r"(two), "r"(s_first)
+        : "memory");
+#undef NBT_U2_BODY
+  }
+}
+#undef NBT_WALK_PART
+
 // IG of one ray: walk, read, accumulate, stop after the first occupied voxel.
 // HIT: the occupied voxel adds its gain (the Section III sum runs to N_O).
 // LINEAR: linear layout with stride steps; else bricked with table reads.
@@ -231,14 +308,17 @@ __device__ __forceinline__ void ray_ig(const void *payload, const int32_t *tab, 
   uint32_t addr = min(LINEAR ? (uint32_t)lin : (uint32_t)(offx + offy + offz), addr_max);
   uint32_t raw = raw_load<KIND>(payload, addr);
   const float bx0 = w.bx, by0 = w.by, bz0 = w.bz;
-  if constexpr (LINEAR && KIND == PAYLOAD_GAIN_F32) {
-    walk_gain_f32<HIT>(w, lin, raw, (const float *)payload, addr_max, facc);
+  if constexpr (LINEAR) {
+    if constexpr (KIND == PAYLOAD_GAIN_F32)
+      walk_gain_f32<HIT>(w, lin, raw, (const float *)payload, addr_max, facc);
+    else
+      walk_count<KIND>(w, lin, raw, addr, (const uint8_t *)payload, addr_max, iacc);
     steps += (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
     return;
   }
-  // Three voxels per iteration for FP32 gains on bricked layouts (fewer
-  // register moves and back-edges; the linear FP32 case returned above);
-  // the 1-byte and 2-bit payloads measured no gain from it.
+  // Bricked layouts (the linear layout returned above): three voxels per
+  // iteration for FP32 gains (fewer register moves and back-edges); the
+  // 1-byte and 2-bit payloads measured no gain from it.
 #pragma unroll(KIND == PAYLOAD_GAIN_F32 ? 3 : 1)
   for (;;) {
     bool more;
