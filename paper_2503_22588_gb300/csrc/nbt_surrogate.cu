@@ -75,6 +75,7 @@ constexpr ParamLayout make_layout() {
 constexpr ParamLayout kP = make_layout();
 // scalar copies for device code (arrays of a host constexpr are not visible there)
 constexpr int64_t kW0 = kP.w[0], kW1 = kP.w[1], kW2 = kP.w[2], kW3 = kP.w[3];
+constexpr int64_t kB0 = kP.b[0], kB1 = kP.b[1];
 
 __device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
 
@@ -440,6 +441,310 @@ __global__ void __launch_bounds__(256) conv0_lookup_kernel(const uint8_t *__rest
       dst[1] = out[1];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Layers 0 and 1 fused for inference: one CTA of 8 warps per crop at a
+// time (persistent, one CTA per SM), both layers on tcgen05 with every
+// operand in shared memory; only layer 1's output goes to global memory.
+//
+// Layer 0 as a GEMM over one-hot inputs: rows = output voxels (16^3 per
+// crop, 32 tiles of 128), K = 28 taps x 4 slots (tap 27 and slot 3 are
+// zero), slot s of a tap = 1.0 where the tap's input class code is s + 1;
+// B = W0 on the three class channels.  The crop's codes are repacked to 2
+// bits (one 64-bit word per x-row); the three codes a tap row needs (x =
+// 2 ox - 1 .. 2 ox + 1) come out of one shift, and a 16-byte chunk of A
+// (two taps) is one entry of a 16-entry table indexed by the two codes.
+// Two A tiles in flight.  Bias and ReLU in the epilogue, which writes the
+// layer-0 activation into shared memory as [channel group 0..1][z][y][x']
+// 16-byte vectors with x' = (x & 1) * 8 + x / 2: the stride-2 reads of
+// layer 1 then hit consecutive vectors.
+// Layer 1: rows = 8^3 output voxels (4 tiles of 128), K = 27 taps x 16
+// channels (padded to 7 stages of 64), three stages in flight, copied
+// shared -> shared: the source of (row, chunk) is a per-row offset plus a
+// per-chunk offset, zero where the tap falls in the padding (a 3-bit mask
+// test); W1 stays resident.  Accumulators: layer 0 in 8 TMEM slots of 16
+// columns, layer 1 in 4 x 32.  Every mbarrier wait is bounded.
+// ---------------------------------------------------------------------------
+namespace fz {
+constexpr int kThreads = 256;
+constexpr int kK0 = 112;                       // layer-0 K: 28 taps x 4 slots
+constexpr int kTile0 = 128 * kK0 * 2;          // 28,672 B
+constexpr int kTiles0 = 32;                    // 16^3 / 128
+constexpr int kTiles1 = 4;                     // 8^3 / 128
+constexpr int kStages1 = 7;                    // layer-1 K stages of 64 per tile
+constexpr int kStage1 = 128 * 64 * 2;          // 16,384 B
+constexpr int kBuf1 = 3;
+constexpr int kOffCodes = 0;                   // 32 x 32 x-rows x 8 B
+constexpr int kOffAct0 = kOffCodes + 8192;     // 2 x 16^3 x 16 B
+constexpr int kOffW0 = kOffAct0 + 131072;      // 7 K16 blocks x 16 rows x 32 B
+constexpr int kOffW1 = kOffW0 + 3584;          // 28 K16 blocks x 32 rows x 32 B
+constexpr int kOffStage = kOffW1 + 28672;      // 2 layer-0 tiles / 3 layer-1 stages
+constexpr int kOffLut = kOffStage + 2 * kTile0;
+constexpr int kOffTap = kOffLut + 256;         // 64 x (offset, mask) for layer-1 chunks
+constexpr int kSmem = kOffTap + 512;           // 229,632 B
+constexpr uint32_t kTmemCols = 256;
+static_assert(kBuf1 * kStage1 <= 2 * kTile0, "layer-1 stages reuse the layer-0 tile space");
+
+// Offset of 16-byte chunk (row r, chunk kc) in a 128-row stage.
+__device__ __forceinline__ uint32_t a_off(int r, int kc) {
+  return (uint32_t)((kc >> 1) * (128 * 32) + (r >> 3) * 256 + (kc & 1) * 128 + (r & 7) * 16);
+}
+
+// One-hot slots of class code c (0: none) as four BF16 values.
+__host__ __device__ constexpr uint64_t onehot4(uint32_t c) { return (0x3F80ull << (16u * c)) >> 16; }
+
+// Chunks [7 H, 7 H + 7) of layer-0 A row r (output voxel (ox, oy, oz)),
+// i.e. taps 14 H .. 14 H + 13: per tap row (dz, dy) the codes of x = 2 ox
+// - 1 .. 2 ox + 1 at bits 0, 2, 4 of one word (x = -1 and rows outside the
+// crop read as 0), then one table entry per pair of taps.
+template <int H>
+__device__ __forceinline__ void build0(const uint64_t *codes, const uint4 *lut, uint8_t *tile, int r, int ox, int oy,
+                                       int oz) {
+  constexpr int t0 = 14 * H;
+  uint32_t cd[14];
+  uint32_t rowv = 0u;
+  int row = -1;
+#pragma unroll
+  for (int i = 0; i < 14; ++i) {
+    const int tap = t0 + i;
+    if (tap >= 27) {
+      cd[i] = 0u;
+      continue;
+    }
+    const int rw = tap / 3;  // (dz, dy) row, compile-time
+    if (rw != row) {
+      const int iz = 2 * oz + rw / 3 - 1, iy = 2 * oy + rw % 3 - 1;
+      const uint64_t R = (iz | iy) < 0 ? 0ull : codes[iz * 32 + iy];  // upper bounds always hold
+      rowv = ox == 0 ? (uint32_t)R << 2 : (uint32_t)(R >> (4 * ox - 2));
+      row = rw;
+    }
+    cd[i] = (rowv >> (2 * (tap % 3))) & 3u;
+  }
+#pragma unroll
+  for (int j = 0; j < 7; ++j) *(uint4 *)(tile + a_off(r, 7 * H + j)) = lut[cd[2 * j] | (cd[2 * j + 1] << 2)];
+}
+}  // namespace fz
+
+__global__ void __launch_bounds__(fz::kThreads, 1)
+    conv01_kernel(const uint8_t *__restrict__ codes, const bf16 *__restrict__ wb, const float *__restrict__ params,
+                  int64_t n_views, bf16 *__restrict__ act1, int *err) {
+  using namespace fz;
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  __shared__ uint64_t mbar0[2], mbar1[kBuf1];
+  __shared__ uint32_t tmem_base;
+  __shared__ float bias0[16], bias1[32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint64_t *codes64 = (uint64_t *)(sm + kOffCodes);
+  uint8_t *act0 = sm + kOffAct0;
+  uint8_t *w0s = sm + kOffW0, *w1s = sm + kOffW1, *stg = sm + kOffStage;
+  uint4 *lut = (uint4 *)(sm + kOffLut);
+  int2 *tapinfo = (int2 *)(sm + kOffTap);
+
+  // resident operands: W0 on the class channels (K = 4 tap + slot), W1, biases, tables
+  for (int e = tid; e < 16 * kK0; e += kThreads) {
+    const int co = e / kK0, k = e % kK0, tap = k >> 2, sl = k & 3;
+    const bf16 v = (tap < 27 && sl < 3) ? wb[kW0 + co * (27 * kC0) + tap * kC0 + sl] : __float2bfloat16(0.0f);
+    const int kc = k >> 3;
+    *(bf16 *)(w0s + (kc >> 1) * (16 * 32) + (co >> 3) * 256 + (kc & 1) * 128 + (co & 7) * 16 + (k & 7) * 2) = v;
+  }
+  for (int e = tid; e < 32 * 448; e += kThreads) {
+    const int co = e / 448, k = e % 448;
+    const bf16 v = k < 27 * 16 ? wb[kW1 + co * (27 * 16) + k] : __float2bfloat16(0.0f);
+    const int kc = k >> 3;
+    *(bf16 *)(w1s + (kc >> 1) * (32 * 32) + (co >> 3) * 256 + (kc & 1) * 128 + (co & 7) * 16 + (k & 7) * 2) = v;
+  }
+  if (tid < 16) {
+    const uint64_t a = onehot4(tid & 3), b = onehot4(tid >> 2);
+    lut[tid] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+    bias0[tid] = params[kB0 + tid];
+  }
+  if (tid < 32) bias1[tid] = params[kB1 + tid];
+  if (tid < 64) {
+    // layer-1 chunk kc = 2 tap + channel group: act0 offset relative to the
+    // output voxel's own, and which low-side paddings it falls into
+    const int kc = tid, tap = kc >> 1, cg = kc & 1;
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+    const int xoff = dx == 0 ? 7 : (dx == 1 ? 0 : 8);
+    const int off = cg * 65536 + (dz - 1) * 4096 + (dy - 1) * 256 + xoff * 16;
+    const int mask = kc < 54 ? ((dx == 0) | ((dy == 0) << 1) | ((dz == 0) << 2)) : 8;
+    tapinfo[kc] = make_int2(off, mask);
+  }
+  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+  if (tid == 0) {
+    tc::mbar_init(&mbar0[0], 1);
+    tc::mbar_init(&mbar0[1], 1);
+    for (int i = 0; i < kBuf1; ++i) tc::mbar_init(&mbar1[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_smem_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc0 = tc::idesc_bf16(128, 16);
+  constexpr uint32_t idesc1 = tc::idesc_bf16(128, 32);
+  const uint32_t stg_a = tc::smem_u32(stg), w0_a = tc::smem_u32(w0s), w1_a = tc::smem_u32(w1s);
+  const int quarter = warp & 3, half = warp >> 2;   // TMEM lane quarter; half of the row's chunks / columns
+  const int r = quarter * 32 + lane;                // A row (TMEM lane) of this thread
+  const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+  bool ok = true;
+  uint32_t g0 = 0, g1 = 0;  // layer-0 tiles / layer-1 stages issued so far by this CTA
+  uint64_t *last_bar = nullptr;  // barrier and phase of the last commit (it covers all earlier MMAs)
+  uint32_t last_par = 0;
+
+  // bounded wait with a warp-uniform result (the epilogue's tcgen05.ld needs the whole warp)
+  auto wait_warp = [&](uint64_t *bar, uint32_t par) { return __all_sync(0xffffffffu, tc::mbar_wait(bar, par)) != 0; };
+  // layer-0 epilogue of tile t (slot t & 7): 8 channels per thread, bias, ReLU, BF16 into act0
+  auto epi0 = [&](int t) {
+    tc::fence_after_sync();
+    float v[8];
+    tc::tmem_ld8(tmem + lane_base + (uint32_t)((t & 7) * 16 + half * 8), v);
+    const int cell = t * 128 + r;
+    const int ox = cell & 15, oy = (cell >> 4) & 15, oz = cell >> 8;
+    uint32_t u[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(v[2 * q] + bias0[half * 8 + 2 * q], 0.0f),
+                                                     fmaxf(v[2 * q + 1] + bias0[half * 8 + 2 * q + 1], 0.0f));
+      u[q] = *(const uint32_t *)&h;
+    }
+    const int xp = (ox & 1) * 8 + (ox >> 1);
+    *(uint4 *)(act0 + (((half * 16 + oz) * 16 + oy) * 16 + xp) * 16) = make_uint4(u[0], u[1], u[2], u[3]);
+  };
+
+  for (int64_t view = blockIdx.x; view < n_views && ok; view += gridDim.x) {
+    // codes of this crop, 2 bits each: 16 codes (16 bytes) -> 32 bits
+    {
+      const uint4 *src = (const uint4 *)(codes + view * (int64_t)(kCrop * kCrop * kCrop));
+      for (int c = tid; c < 2048; c += kThreads) {
+        const uint4 v = __ldg(src + c);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        uint32_t p = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t b = (w[q] & 3u) | ((w[q] >> 6) & 0xCu) | ((w[q] >> 12) & 0x30u) | ((w[q] >> 18) & 0xC0u);
+          p |= b << (8 * q);
+        }
+        ((uint32_t *)codes64)[c] = p;
+      }
+    }
+    __syncthreads();
+    // ---- layer 0: 32 tiles of 128 output voxels, two A tiles in flight ----
+    const int ox0 = r & 15;  // the same for every tile
+    for (int t = 0; t < kTiles0; ++t) {
+      const uint32_t g = g0 + (uint32_t)t, b = g & 1u;
+      if (t >= 2 && ok) {
+        ok = wait_warp(&mbar0[b], ((g - 2u) >> 1) & 1u);
+        if (ok) epi0(t - 2);
+      }
+      if (ok) {
+        const int oy = (8 * t + (r >> 4)) & 15, oz = t >> 1;
+        uint8_t *tile = stg + b * kTile0;
+        if (half == 0)
+          build0<0>(codes64, lut, tile, r, ox0, oy, oz);
+        else
+          build0<1>(codes64, lut, tile, r, ox0, oy, oz);
+      }
+      tc::fence_smem_async();
+      tc::fence_before_sync();
+      ok = __syncthreads_and(ok) != 0;
+      if (!ok) break;
+      if (tid == 0) {
+        tc::fence_after_sync();
+        const uint32_t a0 = stg_a + b * kTile0;
+#pragma unroll
+        for (int kk = 0; kk < kK0 / 16; ++kk)
+          tc::mma_bf16(tmem + (uint32_t)((t & 7) * 16), tc::sdesc(a0 + kk * (128 * 32), 128, 256),
+                       tc::sdesc(w0_a + kk * (16 * 32), 128, 256), idesc0, kk > 0 ? 1u : 0u);
+        tc::mma_commit(&mbar0[b]);
+      }
+      last_bar = &mbar0[b];
+      last_par = (g >> 1) & 1u;
+    }
+    if (!ok) break;
+    ok = wait_warp(last_bar, last_par);  // every layer-0 MMA done
+    if (ok) {
+      epi0(kTiles0 - 2);
+      epi0(kTiles0 - 1);
+    }
+    g0 += kTiles0;
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok) != 0;  // act0 complete; layer-0 tiles free
+    if (!ok) break;
+    tc::fence_after_sync();
+    // ---- layer 1: 4 M tiles x 7 K stages, three stages in flight ----
+    {
+      const int jj = tid >> 7;  // this thread's chunks of a stage: jj, jj + 2, jj + 4, jj + 6 (warp-uniform)
+      const int ox = r & 7, oy = (r >> 3) & 7, ozl = r >> 6;
+      for (int s = 0; s < kTiles1 * kStages1; ++s) {
+        const int mt = s / kStages1, ks = s % kStages1;
+        const uint32_t g = g1 + (uint32_t)s, b = g % kBuf1;
+        if (s >= kBuf1 && ok) ok = wait_warp(&mbar1[b], ((g - kBuf1) / kBuf1) & 1u);
+        if (ok) {
+          const int oz = 2 * mt + ozl;
+          const int base = oz * 8192 + oy * 512 + ox * 16;
+          const int low = (ox == 0) | ((oy == 0) << 1) | ((oz == 0) << 2) | 8;
+          uint8_t *st = stg + b * kStage1;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int j = jj + 2 * i;
+            const int2 ti = tapinfo[ks * 8 + j];
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if ((low & ti.y) == 0) v = *(const uint4 *)(act0 + base + ti.x);
+            *(uint4 *)(st + a_off(r, j)) = v;
+          }
+        }
+        tc::fence_smem_async();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok) != 0;
+        if (!ok) break;
+        if (tid == 0) {
+          tc::fence_after_sync();
+          const uint32_t a0 = stg_a + b * kStage1;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_bf16(tmem + 128u + (uint32_t)(mt * 32), tc::sdesc(a0 + kk * (128 * 32), 128, 256),
+                         tc::sdesc(w1_a + (ks * 4 + kk) * (32 * 32), 128, 256), idesc1, (ks | kk) != 0 ? 1u : 0u);
+          tc::mma_commit(&mbar1[b]);
+        }
+        last_bar = &mbar1[b];
+        last_par = (g / kBuf1) & 1u;
+      }
+    }
+    if (!ok) break;
+    ok = wait_warp(last_bar, last_par);  // every layer-1 MMA done
+    g1 += kTiles1 * kStages1;
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    tc::fence_after_sync();
+    for (int mt = 0; mt < kTiles1; ++mt) {
+      float v[16];
+      tc::tmem_ld16(tmem + lane_base + 128u + (uint32_t)(mt * 32 + half * 16), v);
+      const int o = mt * 128 + r;
+      uint32_t u[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(fmaxf(v[2 * q] + bias1[half * 16 + 2 * q], 0.0f),
+                                                        fmaxf(v[2 * q + 1] + bias1[half * 16 + 2 * q + 1], 0.0f));
+        u[q] = *(const uint32_t *)&hh;
+      }
+      uint4 *dst = (uint4 *)(act1 + ((size_t)view * 512 + o) * 32 + half * 16);
+      dst[0] = make_uint4(u[0], u[1], u[2], u[3]);
+      dst[1] = make_uint4(u[4], u[5], u[6], u[7]);
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // accumulators read and codes consumed before the next crop
+    tc::fence_after_sync();
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    if (last_bar) (void)tc::mbar_wait(last_bar, last_par);  // bounded: MMAs done before TMEM is freed
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 // Layer 0 weight gradient on one-hot crops: dW0[co][tap][class] is the sum
@@ -839,15 +1144,36 @@ int check_net(nbt_surrogate n) {
 }
 
 // Forward pass of n <= max_batch samples: crops [n, 32^3, 8], feats [n, 8].
-int forward_batch(nbt_surrogate net, const uint8_t *crops, const bf16 *feats, int n, float *pred, cudaStream_t s) {
-  {
+// Layers 0 and 1 fused (inference): one persistent CTA per SM.
+int launch_conv01(nbt_surrogate net, const uint8_t *crops, int n, cudaStream_t s) {
+  int *err = nullptr;
+  int rc = dev_err_word(&err);
+  if (rc != NBT_OK) return rc;
+  constexpr size_t smem = (size_t)fz::kSmem + 128;
+  NBT_CUDA_TRY(cudaFuncSetAttribute(conv01_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = std::min(n, sm_count());
+  conv01_kernel<<<(unsigned)grid, fz::kThreads, smem, s>>>(crops, net->wb, net->params, n, net->act[1], err);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
+// fused: layers 0 and 1 in one kernel (inference; training keeps the layer-0
+// activation for the backward pass and runs them separately).
+int forward_batch(nbt_surrogate net, const uint8_t *crops, const bf16 *feats, int n, float *pred, cudaStream_t s,
+                  bool fused = false) {
+  int first = 1;
+  if (fused) {
+    const int rc = launch_conv01(net, crops, n, s);
+    if (rc != NBT_OK) return rc;
+    first = 2;
+  } else {
     const int64_t grid = std::min<int64_t>(n, (int64_t)sm_count() * 4);
     conv0_lookup_kernel<<<(unsigned)grid, 256, 0, s>>>(crops, net->wb + kP.w[0], net->params + kP.b[0], n,
                                                        net->act[0]);
     NBT_CUDA_TRY(cudaGetLastError());
   }
-  const bf16 *in = net->act[0];
-  for (int l = 1; l < kLayers; ++l) {
+  const bf16 *in = net->act[first - 1];
+  for (int l = first; l < kLayers; ++l) {
     const LayerDims &L = kL[l];
     const int M = n * L.dout * L.dout * L.dout;
     const ConvFwdLoader la{in, M, L.din, L.stride, ilog2(L.dout), ilog2(L.cin / 8), L.cin};
@@ -1127,7 +1453,8 @@ int nbt_surrogate_forward(nbt_surrogate net, const void *crops, const void *feat
   const int64_t per = (int64_t)kCrop * kCrop * kCrop;
   for (int64_t b0 = 0; b0 < n; b0 += net->max_batch) {
     const int nb = (int)std::min<int64_t>(net->max_batch, n - b0);
-    rc = forward_batch(net, (const uint8_t *)crops + b0 * per, (const bf16 *)feats + b0 * kFeat, nb, pred + b0, s);
+    rc = forward_batch(net, (const uint8_t *)crops + b0 * per, (const bf16 *)feats + b0 * kFeat, nb, pred + b0, s,
+                       true);
     if (rc != NBT_OK) return rc;
   }
   return NBT_OK;

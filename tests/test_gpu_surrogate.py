@@ -104,6 +104,28 @@ def test_forward_matches_oracle():
     net.close()
 
 
+def test_forward_many_views_matches_oracle_on_a_sample():
+    """160 views: more crops than SMs, so the persistent layer-0/1 kernel takes a second crop
+    on some CTAs; a sample of first- and second-pass views against the oracle."""
+    cr, ft = _batch(4, seed=3)
+    cr = cr.repeat(40, 1, 1, 1)                       # 160 crops: 4 scenes' crops, rolled per copy
+    for k in range(40):
+        cr[4 * k:4 * k + 4] = torch.roll(cr[4 * k:4 * k + 4], shifts=(k % 5, 3 * k % 7, k % 3), dims=(1, 2, 3))
+    ft = ft.repeat(40, 1)
+    params = S.init_params(4)
+    params["b0"] += 0.03
+    params["b1"] += 0.03
+    net = gs.Surrogate(max_batch=160, params=params)
+    pred = net.forward(cr, ft).cpu().numpy().astype(np.float64)
+    sample = [0, 1, 77, 151, 152, 155, 159]
+    y, _ = S.forward(as_used_by_gpu(params), S.codes_to_onehot(cr[sample].cpu().numpy()),
+                     ft[sample].float().cpu().numpy(), bf16_activations=True)
+    assert no_device_timeout()
+    assert np.allclose(pred[sample], y, rtol=2e-2, atol=2e-2 * np.abs(y).max()), (pred[sample], y)
+    assert len(np.unique(np.round(pred, 6))) > 20          # the rolled crops really differ
+    net.close()
+
+
 def test_backward_matches_oracle_gradients():
     cr, ft = _batch(8, seed=5)
     params = S.init_params(4)
