@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(256) conv0_lookup_kernel(const uint8_t *__rest
 }
 
 // ---------------------------------------------------------------------------
-// Layers 0 and 1 fused for inference: one CTA of 8 warps per crop at a
+// Layers 0 and 1 fused for inference: one CTA of 17 warps per crop at a
 // time (persistent, one CTA per SM), both layers on tcgen05 with every
 // operand in shared memory; only layer 1's output goes to global memory.
 //
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(256) conv0_lookup_kernel(const uint8_t *__rest
 // columns, layer 1 in 4 x 32.  Every mbarrier wait is bounded.
 // ---------------------------------------------------------------------------
 namespace fz {
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;                  // builder threads (plus one MMA warp)
 constexpr int kK0 = 112;                       // layer-0 K: 28 taps x 4 slots
 constexpr int kTile0 = 128 * kK0 * 2;          // 28,672 B
 constexpr int kTiles0 = 32;                    // 16^3 / 128
@@ -494,20 +494,21 @@ __device__ __forceinline__ uint32_t a_off(int r, int kc) {
 // One-hot slots of class code c (0: none) as four BF16 values.
 __host__ __device__ constexpr uint64_t onehot4(uint32_t c) { return (0x3F80ull << (16u * c)) >> 16; }
 
-// Chunks [7 H, 7 H + 7) of layer-0 A row r (output voxel (ox, oy, oz)),
-// i.e. taps 14 H .. 14 H + 13: per tap row (dz, dy) the codes of x = 2 ox
-// - 1 .. 2 ox + 1 at bits 0, 2, 4 of one word (x = -1 and rows outside the
-// crop read as 0), then one table entry per pair of taps.
-template <int H>
+
+// Chunks [C0, C1) of layer-0 A row r (output voxel (ox, oy, oz)), i.e.
+// taps 2 C0 .. 2 C1 - 1: per tap row (dz, dy) the codes of x = 2 ox - 1 ..
+// 2 ox + 1 at bits 0, 2, 4 of one word (x = -1 and rows outside the crop
+// read as 0), then one table entry per pair of taps.
+template <int C0, int C1>
 __device__ __forceinline__ void build0(const uint64_t *codes, const uint4 *lut, uint8_t *tile, int r, int ox, int oy,
                                        int oz) {
-  constexpr int t0 = 14 * H;
-  uint32_t cd[14];
+  constexpr int n = 2 * (C1 - C0);
+  uint32_t cd[n];
   uint32_t rowv = 0u;
   int row = -1;
 #pragma unroll
-  for (int i = 0; i < 14; ++i) {
-    const int tap = t0 + i;
+  for (int i = 0; i < n; ++i) {
+    const int tap = 2 * C0 + i;
     if (tap >= 27) {
       cd[i] = 0u;
       continue;
@@ -522,18 +523,45 @@ __device__ __forceinline__ void build0(const uint64_t *codes, const uint4 *lut, 
     cd[i] = (rowv >> (2 * (tap % 3))) & 3u;
   }
 #pragma unroll
-  for (int j = 0; j < 7; ++j) *(uint4 *)(tile + a_off(r, 7 * H + j)) = lut[cd[2 * j] | (cd[2 * j + 1] << 2)];
+  for (int j = 0; j < C1 - C0; ++j) *(uint4 *)(tile + a_off(r, C0 + j)) = lut[cd[2 * j] | (cd[2 * j + 1] << 2)];
 }
 }  // namespace fz
 
-__global__ void __launch_bounds__(fz::kThreads, 1)
+// Bounded wait that gives up at once when another warp already timed out
+// (abort flag in shared memory); a timeout sets the flag.
+__device__ __forceinline__ bool wait_abortable(uint64_t *bar, uint32_t par, volatile int *abort) {
+  const uint64_t t0 = tc::globaltimer();
+  while (!tc::mbar_try_wait(bar, par)) {
+    if (*abort) return false;
+    if (tc::globaltimer() - t0 > tc::kWaitNs) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// Warps 0-15 build the A stages (and read the accumulators back); warp 16
+// waits for each stage to be complete, issues its MMAs and commits them.
+// A stage is complete when all 512 builder threads have arrived on its
+// "full" barrier (each after its own stores and an async-proxy fence); the
+// commit arrives on its "empty" barrier, which the builders wait for before
+// refilling the buffer or reading the accumulator.  No CTA-wide barrier
+// inside the crop loop: the builders run up to two layer-0 tiles / three
+// layer-1 stages ahead of the tensor core.
+__global__ void __launch_bounds__(fz::kThreads + 32, 1)
     conv01_kernel(const uint8_t *__restrict__ codes, const bf16 *__restrict__ wb, const float *__restrict__ params,
                   int64_t n_views, bf16 *__restrict__ act1, int *err) {
   using namespace fz;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  __shared__ uint64_t mbar0[2], mbar1[kBuf1];
+  __shared__ uint64_t full0[2], empty0[2], full1[kBuf1], empty1[kBuf1], bsync;
   __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
   __shared__ float bias0[16], bias1[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint64_t *codes64 = (uint64_t *)(sm + kOffCodes);
@@ -541,15 +569,16 @@ __global__ void __launch_bounds__(fz::kThreads, 1)
   uint8_t *w0s = sm + kOffW0, *w1s = sm + kOffW1, *stg = sm + kOffStage;
   uint4 *lut = (uint4 *)(sm + kOffLut);
   int2 *tapinfo = (int2 *)(sm + kOffTap);
+  volatile int *abort = &abort_flag;
 
   // resident operands: W0 on the class channels (K = 4 tap + slot), W1, biases, tables
-  for (int e = tid; e < 16 * kK0; e += kThreads) {
+  for (int e = tid; e < 16 * kK0; e += blockDim.x) {
     const int co = e / kK0, k = e % kK0, tap = k >> 2, sl = k & 3;
     const bf16 v = (tap < 27 && sl < 3) ? wb[kW0 + co * (27 * kC0) + tap * kC0 + sl] : __float2bfloat16(0.0f);
     const int kc = k >> 3;
     *(bf16 *)(w0s + (kc >> 1) * (16 * 32) + (co >> 3) * 256 + (kc & 1) * 128 + (co & 7) * 16 + (k & 7) * 2) = v;
   }
-  for (int e = tid; e < 32 * 448; e += kThreads) {
+  for (int e = tid; e < 32 * 448; e += blockDim.x) {
     const int co = e / 448, k = e % 448;
     const bf16 v = k < 27 * 16 ? wb[kW1 + co * (27 * 16) + k] : __float2bfloat16(0.0f);
     const int kc = k >> 3;
@@ -573,9 +602,16 @@ __global__ void __launch_bounds__(fz::kThreads, 1)
   }
   if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
   if (tid == 0) {
-    tc::mbar_init(&mbar0[0], 1);
-    tc::mbar_init(&mbar0[1], 1);
-    for (int i = 0; i < kBuf1; ++i) tc::mbar_init(&mbar1[i], 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&full0[i], kThreads);
+      tc::mbar_init(&empty0[i], 1);
+    }
+    for (int i = 0; i < kBuf1; ++i) {
+      tc::mbar_init(&full1[i], kThreads);
+      tc::mbar_init(&empty1[i], 1);
+    }
+    tc::mbar_init(&bsync, kThreads);
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_smem_async();
@@ -583,167 +619,208 @@ __global__ void __launch_bounds__(fz::kThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  constexpr uint32_t idesc0 = tc::idesc_bf16(128, 16);
-  constexpr uint32_t idesc1 = tc::idesc_bf16(128, 32);
-  const uint32_t stg_a = tc::smem_u32(stg), w0_a = tc::smem_u32(w0s), w1_a = tc::smem_u32(w1s);
-  const int quarter = warp & 3, half = warp >> 2;   // TMEM lane quarter; half of the row's chunks / columns
-  const int r = quarter * 32 + lane;                // A row (TMEM lane) of this thread
-  const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-  bool ok = true;
-  uint32_t g0 = 0, g1 = 0;  // layer-0 tiles / layer-1 stages issued so far by this CTA
-  uint64_t *last_bar = nullptr;  // barrier and phase of the last commit (it covers all earlier MMAs)
-  uint32_t last_par = 0;
 
-  // bounded wait with a warp-uniform result (the epilogue's tcgen05.ld needs the whole warp)
-  auto wait_warp = [&](uint64_t *bar, uint32_t par) { return __all_sync(0xffffffffu, tc::mbar_wait(bar, par)) != 0; };
-  // layer-0 epilogue of tile t (slot t & 7): 8 channels per thread, bias, ReLU, BF16 into act0
-  auto epi0 = [&](int t) {
-    tc::fence_after_sync();
-    float v[8];
-    tc::tmem_ld8(tmem + lane_base + (uint32_t)((t & 7) * 16 + half * 8), v);
-    const int cell = t * 128 + r;
-    const int ox = cell & 15, oy = (cell >> 4) & 15, oz = cell >> 8;
-    uint32_t u[4];
+  if (warp == kThreads / 32) {
+    // ---- MMA warp: lane 0 issues, the whole warp follows the same waits ----
+    constexpr uint32_t idesc0 = tc::idesc_bf16(128, 16);
+    constexpr uint32_t idesc1 = tc::idesc_bf16(128, 32);
+    // descriptors built once; a byte offset o moves the start address field
+    // by o / 16 (no carry out of its 14 bits: shared memory is < 256 KB)
+    const uint64_t stg_d = tc::sdesc(tc::smem_u32(stg), 128, 256);
+    const uint64_t w0_d = tc::sdesc(tc::smem_u32(w0s), 128, 256);
+    const uint64_t w1_d = tc::sdesc(tc::smem_u32(w1s), 128, 256);
+    uint32_t g0 = 0, g1 = 0;
+    bool ok = true;
+    uint64_t *last_bar = nullptr;  // the last commit (it covers every earlier MMA)
+    uint32_t last_par = 0;
+    for (int64_t view = blockIdx.x; view < n_views && ok; view += gridDim.x) {
+      for (int t = 0; t < kTiles0 && ok; ++t) {
+        const uint32_t g = g0 + (uint32_t)t, b = g & 1u;
+        ok = __all_sync(0xffffffffu, wait_abortable(&full0[b], (g >> 1) & 1u, abort)) != 0;
+        if (ok && lane == 0) {
+          tc::fence_after_sync();
+          const uint64_t a0 = stg_d + (b * kTile0 >> 4);
+          const uint32_t d = tmem + (uint32_t)((t & 7) * 16);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(v[2 * q] + bias0[half * 8 + 2 * q], 0.0f),
-                                                     fmaxf(v[2 * q + 1] + bias0[half * 8 + 2 * q + 1], 0.0f));
-      u[q] = *(const uint32_t *)&h;
-    }
-    const int xp = (ox & 1) * 8 + (ox >> 1);
-    *(uint4 *)(act0 + (((half * 16 + oz) * 16 + oy) * 16 + xp) * 16) = make_uint4(u[0], u[1], u[2], u[3]);
-  };
-
-  for (int64_t view = blockIdx.x; view < n_views && ok; view += gridDim.x) {
-    // codes of this crop, 2 bits each: 16 codes (16 bytes) -> 32 bits
-    {
-      const uint4 *src = (const uint4 *)(codes + view * (int64_t)(kCrop * kCrop * kCrop));
-      for (int c = tid; c < 2048; c += kThreads) {
-        const uint4 v = __ldg(src + c);
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        uint32_t p = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t b = (w[q] & 3u) | ((w[q] >> 6) & 0xCu) | ((w[q] >> 12) & 0x30u) | ((w[q] >> 18) & 0xC0u);
-          p |= b << (8 * q);
+          for (int kk = 0; kk < kK0 / 16; ++kk)
+            tc::mma_bf16(d, a0 + kk * (128 * 32 / 16), w0_d + kk * (16 * 32 / 16), idesc0, kk > 0 ? 1u : 0u);
+          tc::mma_commit(&empty0[b]);
         }
-        ((uint32_t *)codes64)[c] = p;
+        if (ok) {
+          last_bar = &empty0[b];
+          last_par = (g >> 1) & 1u;
+        }
+        __syncwarp();
       }
-    }
-    __syncthreads();
-    // ---- layer 0: 32 tiles of 128 output voxels, two A tiles in flight ----
-    const int ox0 = r & 15;  // the same for every tile
-    for (int t = 0; t < kTiles0; ++t) {
-      const uint32_t g = g0 + (uint32_t)t, b = g & 1u;
-      if (t >= 2 && ok) {
-        ok = wait_warp(&mbar0[b], ((g - 2u) >> 1) & 1u);
-        if (ok) epi0(t - 2);
-      }
-      if (ok) {
-        const int oy = (8 * t + (r >> 4)) & 15, oz = t >> 1;
-        uint8_t *tile = stg + b * kTile0;
-        if (half == 0)
-          build0<0>(codes64, lut, tile, r, ox0, oy, oz);
-        else
-          build0<1>(codes64, lut, tile, r, ox0, oy, oz);
-      }
-      tc::fence_smem_async();
-      tc::fence_before_sync();
-      ok = __syncthreads_and(ok) != 0;
-      if (!ok) break;
-      if (tid == 0) {
-        tc::fence_after_sync();
-        const uint32_t a0 = stg_a + b * kTile0;
-#pragma unroll
-        for (int kk = 0; kk < kK0 / 16; ++kk)
-          tc::mma_bf16(tmem + (uint32_t)((t & 7) * 16), tc::sdesc(a0 + kk * (128 * 32), 128, 256),
-                       tc::sdesc(w0_a + kk * (16 * 32), 128, 256), idesc0, kk > 0 ? 1u : 0u);
-        tc::mma_commit(&mbar0[b]);
-      }
-      last_bar = &mbar0[b];
-      last_par = (g >> 1) & 1u;
-    }
-    if (!ok) break;
-    ok = wait_warp(last_bar, last_par);  // every layer-0 MMA done
-    if (ok) {
-      epi0(kTiles0 - 2);
-      epi0(kTiles0 - 1);
-    }
-    g0 += kTiles0;
-    tc::fence_before_sync();
-    ok = __syncthreads_and(ok) != 0;  // act0 complete; layer-0 tiles free
-    if (!ok) break;
-    tc::fence_after_sync();
-    // ---- layer 1: 4 M tiles x 7 K stages, three stages in flight ----
-    {
-      const int jj = tid >> 7;  // this thread's chunks of a stage: jj, jj + 2, jj + 4, jj + 6 (warp-uniform)
-      const int ox = r & 7, oy = (r >> 3) & 7, ozl = r >> 6;
-      for (int s = 0; s < kTiles1 * kStages1; ++s) {
+      g0 += kTiles0;
+      for (int s = 0; s < kTiles1 * kStages1 && ok; ++s) {
         const int mt = s / kStages1, ks = s % kStages1;
         const uint32_t g = g1 + (uint32_t)s, b = g % kBuf1;
-        if (s >= kBuf1 && ok) ok = wait_warp(&mbar1[b], ((g - kBuf1) / kBuf1) & 1u);
+        ok = __all_sync(0xffffffffu, wait_abortable(&full1[b], (g / kBuf1) & 1u, abort)) != 0;
+        if (ok && lane == 0) {
+          tc::fence_after_sync();
+          const uint64_t a0 = stg_d + (b * kStage1 >> 4), b0 = w1_d + ks * (4 * 32 * 32 / 16);
+          const uint32_t d = tmem + 128u + (uint32_t)(mt * 32);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_bf16(d, a0 + kk * (128 * 32 / 16), b0 + kk * (32 * 32 / 16), idesc1, (ks | kk) != 0 ? 1u : 0u);
+          tc::mma_commit(&empty1[b]);
+        }
         if (ok) {
+          last_bar = &empty1[b];
+          last_par = (g / kBuf1) & 1u;
+        }
+        __syncwarp();
+      }
+      g1 += kTiles1 * kStages1;
+    }
+    // before TMEM is freed: the last commit done (bounded, whatever the abort flag says)
+    if (last_bar) {
+      const uint64_t t0 = tc::globaltimer();
+      while (!tc::mbar_try_wait(last_bar, last_par) && tc::globaltimer() - t0 < tc::kWaitNs) {
+      }
+    }
+  } else {
+    // ---- builder warps ----
+    const int quarter = warp & 3, part = warp >> 2;  // TMEM lane quarter; quarter of the row's chunks / columns
+    const int r = quarter * 32 + lane;               // A row (TMEM lane) of this thread
+    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+    uint32_t g0 = 0, g1 = 0, nb = 0;
+    bool ok = true;
+    auto wait_warp = [&](uint64_t *bar, uint32_t par) {
+      return __all_sync(0xffffffffu, wait_abortable(bar, par, abort)) != 0;
+    };
+    // all builders reach this point (bounded)
+    auto builders_sync = [&]() {
+      tc::fence_before_sync();
+      mbar_arrive(&bsync);
+      const bool r_ok = __all_sync(0xffffffffu, wait_abortable(&bsync, nb & 1u, abort)) != 0;
+      ++nb;
+      tc::fence_after_sync();
+      return r_ok;
+    };
+    // publish this thread's stage stores (and earlier accumulator reads) to the MMA warp
+    auto publish = [&](uint64_t *bar) {
+      tc::fence_smem_async();
+      tc::fence_before_sync();
+      mbar_arrive(bar);
+    };
+    // layer-0 epilogue of tile t (slot t & 7): 4 channels per thread, bias, ReLU, BF16 into act0
+    auto epi0 = [&](int t) {
+      tc::fence_after_sync();
+      float v[4];
+      tc::tmem_ld4(tmem + lane_base + (uint32_t)((t & 7) * 16 + part * 4), v);
+      const int cell = t * 128 + r;
+      const int ox = cell & 15, oy = (cell >> 4) & 15, oz = cell >> 8;
+      const __nv_bfloat162 h0 = __floats2bfloat162_rn(fmaxf(v[0] + bias0[part * 4], 0.0f),
+                                                      fmaxf(v[1] + bias0[part * 4 + 1], 0.0f));
+      const __nv_bfloat162 h1 = __floats2bfloat162_rn(fmaxf(v[2] + bias0[part * 4 + 2], 0.0f),
+                                                      fmaxf(v[3] + bias0[part * 4 + 3], 0.0f));
+      const int xp = (ox & 1) * 8 + (ox >> 1);
+      *(uint2 *)(act0 + ((((part >> 1) * 16 + oz) * 16 + oy) * 16 + xp) * 16 + (part & 1) * 8) =
+          make_uint2(*(const uint32_t *)&h0, *(const uint32_t *)&h1);
+    };
+
+    for (int64_t view = blockIdx.x; view < n_views && ok; view += gridDim.x) {
+      // codes of this crop, 2 bits each: 16 codes (16 bytes) -> 32 bits
+      {
+        const uint4 *src = (const uint4 *)(codes + view * (int64_t)(kCrop * kCrop * kCrop));
+        for (int c = tid; c < 2048; c += kThreads) {
+          const uint4 v = __ldg(src + c);
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+          uint32_t p = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t b = (w[q] & 3u) | ((w[q] >> 6) & 0xCu) | ((w[q] >> 12) & 0x30u) | ((w[q] >> 18) & 0xC0u);
+            p |= b << (8 * q);
+          }
+          ((uint32_t *)codes64)[c] = p;
+        }
+      }
+      ok = builders_sync();  // codes complete
+      // ---- layer 0: 32 tiles of 128 output voxels, two A tiles in flight ----
+      const int ox0 = r & 15;  // the same for every tile
+      for (int t = 0; t < kTiles0 && ok; ++t) {
+        const uint32_t g = g0 + (uint32_t)t, b = g & 1u;
+        if (t >= 2) {
+          ok = wait_warp(&empty0[b], ((g - 2u) >> 1) & 1u);  // tile t - 2: buffer free, accumulator ready
+          if (!ok) break;
+          epi0(t - 2);
+        }
+        const int oy = (8 * t + (r >> 4)) & 15, oz = t >> 1;
+        uint8_t *tile = stg + b * kTile0;
+        switch (part) {  // chunks 0-3, 4-7, 8-10, 11-13
+          case 0: build0<0, 4>(codes64, lut, tile, r, ox0, oy, oz); break;
+          case 1: build0<4, 8>(codes64, lut, tile, r, ox0, oy, oz); break;
+          case 2: build0<8, 11>(codes64, lut, tile, r, ox0, oy, oz); break;
+          default: build0<11, 14>(codes64, lut, tile, r, ox0, oy, oz); break;
+        }
+        publish(&full0[b]);
+      }
+      if (!ok) break;
+      {
+        const uint32_t g = g0 + kTiles0 - 1;
+        ok = wait_warp(&empty0[g & 1u], (g >> 1) & 1u);  // the last tile's commit covers every layer-0 MMA
+      }
+      if (!ok) break;
+      epi0(kTiles0 - 2);
+      epi0(kTiles0 - 1);
+      g0 += kTiles0;
+      ok = builders_sync();  // act0 complete
+      if (!ok) break;
+      // ---- layer 1: 4 M tiles x 7 K stages, three stages in flight ----
+      {
+        const int jj = tid >> 7;  // this thread's chunks of a stage: jj and jj + 4 (warp-uniform)
+        const int ox = r & 7, oy = (r >> 3) & 7, ozl = r >> 6;
+        for (int s = 0; s < kTiles1 * kStages1 && ok; ++s) {
+          const int mt = s / kStages1, ks = s % kStages1;
+          const uint32_t g = g1 + (uint32_t)s, b = g % kBuf1;
+          if (s >= kBuf1) {
+            ok = wait_warp(&empty1[b], ((g - kBuf1) / kBuf1) & 1u);
+            if (!ok) break;
+          }
           const int oz = 2 * mt + ozl;
           const int base = oz * 8192 + oy * 512 + ox * 16;
           const int low = (ox == 0) | ((oy == 0) << 1) | ((oz == 0) << 2) | 8;
           uint8_t *st = stg + b * kStage1;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int j = jj + 2 * i;
+          for (int i = 0; i < 2; ++i) {
+            const int j = jj + 4 * i;
             const int2 ti = tapinfo[ks * 8 + j];
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if ((low & ti.y) == 0) v = *(const uint4 *)(act0 + base + ti.x);
             *(uint4 *)(st + a_off(r, j)) = v;
           }
+          publish(&full1[b]);
         }
-        tc::fence_smem_async();
-        tc::fence_before_sync();
-        ok = __syncthreads_and(ok) != 0;
-        if (!ok) break;
-        if (tid == 0) {
-          tc::fence_after_sync();
-          const uint32_t a0 = stg_a + b * kStage1;
+      }
+      if (!ok) break;
+      {
+        const uint32_t g = g1 + kTiles1 * kStages1 - 1;
+        ok = wait_warp(&empty1[g % kBuf1], (g / kBuf1) & 1u);  // every layer-1 MMA done, every stage built
+      }
+      if (!ok) break;
+      g1 += kTiles1 * kStages1;
+      tc::fence_after_sync();
+      for (int mt = 0; mt < kTiles1; ++mt) {
+        float v[8];
+        tc::tmem_ld8(tmem + lane_base + 128u + (uint32_t)(mt * 32 + part * 8), v);
+        const int o = mt * 128 + r;
+        uint32_t u[4];
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_bf16(tmem + 128u + (uint32_t)(mt * 32), tc::sdesc(a0 + kk * (128 * 32), 128, 256),
-                         tc::sdesc(w1_a + (ks * 4 + kk) * (32 * 32), 128, 256), idesc1, (ks | kk) != 0 ? 1u : 0u);
-          tc::mma_commit(&mbar1[b]);
+        for (int q = 0; q < 4; ++q) {
+          const __nv_bfloat162 hh = __floats2bfloat162_rn(fmaxf(v[2 * q] + bias1[part * 8 + 2 * q], 0.0f),
+                                                          fmaxf(v[2 * q + 1] + bias1[part * 8 + 2 * q + 1], 0.0f));
+          u[q] = *(const uint32_t *)&hh;
         }
-        last_bar = &mbar1[b];
-        last_par = (g / kBuf1) & 1u;
+        *(uint4 *)(act1 + ((size_t)view * 512 + o) * 32 + part * 8) = make_uint4(u[0], u[1], u[2], u[3]);
       }
     }
-    if (!ok) break;
-    ok = wait_warp(last_bar, last_par);  // every layer-1 MMA done
-    g1 += kTiles1 * kStages1;
-    ok = __syncthreads_and(ok) != 0;
-    if (!ok) break;
-    tc::fence_after_sync();
-    for (int mt = 0; mt < kTiles1; ++mt) {
-      float v[16];
-      tc::tmem_ld16(tmem + lane_base + 128u + (uint32_t)(mt * 32 + half * 16), v);
-      const int o = mt * 128 + r;
-      uint32_t u[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const __nv_bfloat162 hh = __floats2bfloat162_rn(fmaxf(v[2 * q] + bias1[half * 16 + 2 * q], 0.0f),
-                                                        fmaxf(v[2 * q + 1] + bias1[half * 16 + 2 * q + 1], 0.0f));
-        u[q] = *(const uint32_t *)&hh;
-      }
-      uint4 *dst = (uint4 *)(act1 + ((size_t)view * 512 + o) * 32 + half * 16);
-      dst[0] = make_uint4(u[0], u[1], u[2], u[3]);
-      dst[1] = make_uint4(u[4], u[5], u[6], u[7]);
-    }
-    tc::fence_before_sync();
-    __syncthreads();  // accumulators read and codes consumed before the next crop
-    tc::fence_after_sync();
-  }
-  if (!ok) {
-    if (tid == 0) atomicExch(err, 1);
-    if (last_bar) (void)tc::mbar_wait(last_bar, last_par);  // bounded: MMAs done before TMEM is freed
+    if (!ok) *abort = 1;
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (*abort && tid == 0) atomicExch(err, 1);
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
@@ -1152,7 +1229,7 @@ int launch_conv01(nbt_surrogate net, const uint8_t *crops, int n, cudaStream_t s
   constexpr size_t smem = (size_t)fz::kSmem + 128;
   NBT_CUDA_TRY(cudaFuncSetAttribute(conv01_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::min(n, sm_count());
-  conv01_kernel<<<(unsigned)grid, fz::kThreads, smem, s>>>(crops, net->wb, net->params, n, net->act[1], err);
+  conv01_kernel<<<(unsigned)grid, fz::kThreads + 32, smem, s>>>(crops, net->wb, net->params, n, net->act[1], err);
   NBT_CUDA_TRY(cudaGetLastError());
   return NBT_OK;
 }
