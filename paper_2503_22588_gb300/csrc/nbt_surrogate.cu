@@ -295,7 +295,10 @@ struct CropConst {
   float occ_thr, free_thr;
 };
 
-template <int KIND>
+// LINEAR: linear x-fastest layout, element index (z ny + y) nx + x computed
+// instead of read from the offset tables.  Four samples per iteration so
+// that each thread has several map reads in flight.
+template <int KIND, bool LINEAR>
 __global__ void __launch_bounds__(256) crop_kernel(DevMap m, CropConst cc, const float *__restrict__ poses, int64_t n,
                                                    uint8_t *__restrict__ crops, bf16 *__restrict__ feats) {
   // one CTA per perspective: the rotation is formed once, then every sample
@@ -322,6 +325,7 @@ __global__ void __launch_bounds__(256) crop_kernel(DevMap m, CropConst cc, const
     for (int a = 0; a < 3; ++a) o[a] = s_o[a];
     const int dims[3] = {m.nx, m.ny, m.nz};
     uint8_t *cv = crops + v * (int64_t)(kCrop * kCrop * kCrop);
+#pragma unroll 4
     for (int cell = threadIdx.x; cell < kCrop * kCrop * kCrop; cell += blockDim.x) {
       const int i = cell & 31, j = (cell >> 5) & 31, k = cell >> 10;
       const float fr = fmul(fadd((float)k, 0.5f), 0.03125f);   // (k + 1/2) / 32, exact
@@ -340,7 +344,8 @@ __global__ void __launch_bounds__(256) crop_kernel(DevMap m, CropConst cc, const
       }
       uint32_t cls = 3u;  // 3 = outside: no channel set
       if (inside) {
-        const int32_t off = m.tab[idx[0]] + m.tab[m.nx + idx[1]] + m.tab[m.nx + m.ny + idx[2]];
+        const int32_t off = LINEAR ? (idx[2] * m.ny + idx[1]) * m.nx + idx[0]
+                                   : m.tab[idx[0]] + m.tab[m.nx + idx[1]] + m.tab[m.nx + m.ny + idx[2]];
         if (KIND == PAYLOAD_GAIN_F32) {
           const float pv = __ldg((const float *)m.payload + off);
           cls = pv > cc.occ_thr ? 2u : (pv < cc.free_thr ? 1u : 0u);
@@ -1503,16 +1508,28 @@ int nbt_surrogate_crops(nbt_map map, const nbt_pose *poses, int64_t n, const nbt
   m.nz = map->desc.nz;
   cudaStream_t s = (cudaStream_t)stream;
   const int grid = (int)std::min<int64_t>(n, (int64_t)sm_count() * 8);
+  const bool lin = map->brick == 1;
+  const float *pz = (const float *)poses;
+  uint8_t *cr = (uint8_t *)crops;
+  bf16 *ft = (bf16 *)feats;
   switch (map->desc.encoding) {
     case NBT_F32_PROB:
-      crop_kernel<PAYLOAD_GAIN_F32><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (uint8_t *)crops,
-                                                         (bf16 *)feats);
+      if (lin)
+        crop_kernel<PAYLOAD_GAIN_F32, true><<<grid, 256, 0, s>>>(m, cc, pz, n, cr, ft);
+      else
+        crop_kernel<PAYLOAD_GAIN_F32, false><<<grid, 256, 0, s>>>(m, cc, pz, n, cr, ft);
       break;
     case NBT_U2_STATE:
-      crop_kernel<PAYLOAD_U2><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (uint8_t *)crops, (bf16 *)feats);
+      if (lin)
+        crop_kernel<PAYLOAD_U2, true><<<grid, 256, 0, s>>>(m, cc, pz, n, cr, ft);
+      else
+        crop_kernel<PAYLOAD_U2, false><<<grid, 256, 0, s>>>(m, cc, pz, n, cr, ft);
       break;
     default:
-      crop_kernel<PAYLOAD_U8><<<grid, 256, 0, s>>>(m, cc, (const float *)poses, n, (uint8_t *)crops, (bf16 *)feats);
+      if (lin)
+        crop_kernel<PAYLOAD_U8, true><<<grid, 256, 0, s>>>(m, cc, pz, n, cr, ft);
+      else
+        crop_kernel<PAYLOAD_U8, false><<<grid, 256, 0, s>>>(m, cc, pz, n, cr, ft);
       break;
   }
   NBT_CUDA_TRY(cudaGetLastError());

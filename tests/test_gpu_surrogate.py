@@ -64,12 +64,13 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("enc", ["u8", "u2", "f32"])
-def test_crops_bitexact(enc):
+@pytest.mark.parametrize("enc,brick", [(e, b) for e in ("u8", "u2", "f32") for b in (1, 8)])
+def test_crops_bitexact(enc, brick):
+    """Linear layout (offsets computed) and 8^3 bricks (offsets from the tables)."""
     grid, p = small_scene(enc, seed=3)
     cam = nbt.camera(64, 48, math.radians(60), math.radians(45), 0.5)
     prm = nbt.ig_params("count" if enc != "f32" else "entropy")
-    m = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01, (0.0, 0.0, 0.0), enc)
+    m = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01, (0.0, 0.0, 0.0), enc, brick)
     cr, ft = gs.crops(m, torch.from_numpy(p).cuda(), cam, prm)
     assert cr.dtype == torch.uint8 and cr.shape == (len(p), 32, 32, 32)
     cr = cr.cpu().numpy()
