@@ -457,10 +457,14 @@ __global__ void __launch_bounds__(kThreads, CHUNK ? 4 : (LINEAR ? 6 : 5))
       else
         ray_ig<KIND, HIT, LINEAR>(m.payload, stab, addr_max, m.nx, m.ny, m.nz, o, d, facc, iacc, steps);
     }
+    // FP32-gain walks leave the count at 0 and count walks the gain: reduce
+    // only what the payload kind produces
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
-      facc += __shfl_xor_sync(0xffffffffu, facc, s);
-      iacc += __shfl_xor_sync(0xffffffffu, iacc, s);
+      if (KIND == PAYLOAD_GAIN_F32)
+        facc += __shfl_xor_sync(0xffffffffu, facc, s);
+      else
+        iacc += __shfl_xor_sync(0xffffffffu, iacc, s);
       steps += __shfl_xor_sync(0xffffffffu, steps, s);
     }
     if (lane == 0) {
@@ -608,10 +612,14 @@ __global__ void __launch_bounds__(kThreads)
       iacc += ic;
       steps += st;
     }
+    // FP32-gain walks leave the count at 0 and count walks the gain: reduce
+    // only what the payload kind produces
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
-      facc += __shfl_xor_sync(0xffffffffu, facc, s);
-      iacc += __shfl_xor_sync(0xffffffffu, iacc, s);
+      if (KIND == PAYLOAD_GAIN_F32)
+        facc += __shfl_xor_sync(0xffffffffu, facc, s);
+      else
+        iacc += __shfl_xor_sync(0xffffffffu, iacc, s);
       steps += __shfl_xor_sync(0xffffffffu, steps, s);
     }
     if (lane == 0) {
