@@ -75,7 +75,7 @@ constexpr ParamLayout make_layout() {
 constexpr ParamLayout kP = make_layout();
 // scalar copies for device code (arrays of a host constexpr are not visible there)
 constexpr int64_t kW0 = kP.w[0], kW1 = kP.w[1], kW2 = kP.w[2], kW3 = kP.w[3];
-constexpr int64_t kB0 = kP.b[0], kB1 = kP.b[1];
+constexpr int64_t kB0 = kP.b[0], kB1 = kP.b[1], kB2 = kP.b[2], kB3 = kP.b[3];
 
 __device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
 
@@ -829,6 +829,226 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+// ---------------------------------------------------------------------------
+// Layers 2 and 3 (both 4^3 outputs per crop, 64 channels): a 128-row tile is
+// exactly two crops, so the tile's whole input (two crops' activations:
+// 2 x 32 KB for layer 2, 2 x 8 KB for layer 3) is staged in shared memory
+// once and the im2col stages are copied shared -> shared instead of
+// gathering each input vector up to 27 times from L2.  Same K order, same
+// MMA sequence and same epilogues as the generic implicit GEMM, so the
+// outputs are bit-identical.  One persistent CTA per SM: 16 builder warps
+// (A from the staged input, B = the weight stage by cp.async), one MMA warp,
+// four stages in flight on full/empty mbarriers; the next tile's input is
+// staged while the current tile's last MMAs run.
+// ---------------------------------------------------------------------------
+namespace c23 {
+constexpr int kBuilders = 512;
+constexpr int kBuf = 4;
+constexpr int kStageA = 128 * 64 * 2;            // 16 KB
+constexpr int kStageB = 64 * 64 * 2;             // 8 KB
+constexpr int kMaxIn = 2 * 8 * 8 * 8 * 32 * 2;   // two crops of layer 2's input: 64 KB
+constexpr int kOffIn = 0;
+constexpr int kOffStage = kOffIn + kMaxIn;
+constexpr int kOffTap = kOffStage + kBuf * (kStageA + kStageB);
+constexpr int kSmem = kOffTap + 256 * 8;         // 165,888 B
+
+template <int L>
+struct Geo;
+template <>
+struct Geo<2> {
+  static constexpr int din = 8, stride = 2, cin = 32, cg = 4, stages = 14;
+};
+template <>
+struct Geo<3> {
+  static constexpr int din = 4, stride = 1, cin = 64, cg = 8, stages = 27;
+};
+}  // namespace c23
+
+template <int L>
+__global__ void __launch_bounds__(c23::kBuilders + 32, 1)
+    conv23_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const float *__restrict__ bias,
+                  int64_t n_views, bf16 *__restrict__ out, int *err) {
+  using namespace c23;
+  using G = Geo<L>;
+  constexpr int kIn = G::din * G::din * G::din * G::cin * 2;  // bytes of one crop's input
+  constexpr int kK = 27 * G::cin;                               // weight row length
+  constexpr int kChunks = 27 * G::cg;                           // real 16-byte chunks of a row
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  __shared__ uint64_t full[kBuf], empty[kBuf], bsync;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  __shared__ float sbias[64];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t *sin = sm + kOffIn, *stg = sm + kOffStage;
+  int2 *tapinfo = (int2 *)(sm + kOffTap);
+  volatile int *abort = &abort_flag;
+  const int64_t n_tiles = (n_views + 1) / 2;
+
+  if (tid < 64) sbias[tid] = bias[tid];
+  for (int kc = tid; kc < G::stages * 8; kc += blockDim.x) {
+    // chunk kc = tap * cg + channel group: input offset relative to the output
+    // voxel's own, and the padding cases it falls into (bit 6: past K)
+    const int tap = kc / G::cg, cgi = kc % G::cg;
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+    const int off = (((dz - 1) * G::din + (dy - 1)) * G::din + (dx - 1)) * G::cin * 2 + cgi * 16;
+    int mask = (dx == 0) | ((dy == 0) << 1) | ((dz == 0) << 2);
+    if (G::stride == 1) mask |= ((dx == 2) << 3) | ((dy == 2) << 4) | ((dz == 2) << 5);
+    tapinfo[kc] = make_int2(off, kc < kChunks ? mask : 64);
+  }
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 64);
+  if (tid == 0) {
+    for (int i = 0; i < kBuf; ++i) {
+      tc::mbar_init(&full[i], kBuilders);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(&bsync, kBuilders);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == kBuilders / 32) {
+    // ---- MMA warp ----
+    constexpr uint32_t idesc = tc::idesc_bf16(128, 64);
+    const uint64_t stg_d = tc::sdesc(tc::smem_u32(stg), 128, 256);
+    uint32_t g = 0;
+    bool ok = true;
+    uint64_t *last_bar = nullptr;
+    uint32_t last_par = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      for (int ks = 0; ks < G::stages && ok; ++ks, ++g) {
+        const uint32_t b = g % kBuf;
+        ok = __all_sync(0xffffffffu, wait_abortable(&full[b], (g / kBuf) & 1u, abort)) != 0;
+        if (ok && lane == 0) {
+          tc::fence_after_sync();
+          const uint64_t a0 = stg_d + (b * (kStageA + kStageB) >> 4), b0 = a0 + (kStageA >> 4);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_bf16(tmem, a0 + kk * (128 * 32 / 16), b0 + kk * (64 * 32 / 16), idesc, (ks | kk) != 0 ? 1u : 0u);
+          tc::mma_commit(&empty[b]);
+        }
+        if (ok) {
+          last_bar = &empty[b];
+          last_par = (g / kBuf) & 1u;
+        }
+        __syncwarp();
+      }
+    }
+    if (last_bar) {  // before TMEM is freed (bounded)
+      const uint64_t t0 = tc::globaltimer();
+      while (!tc::mbar_try_wait(last_bar, last_par) && tc::globaltimer() - t0 < tc::kWaitNs) {
+      }
+    }
+  } else {
+    // ---- builder warps ----
+    const int quarter = warp & 3, part = warp >> 2;
+    const int r = quarter * 32 + lane;  // tile row = TMEM lane of this thread
+    const int crop = r >> 6, o = r & 63, ox = o & 3, oy = (o >> 2) & 3, oz = o >> 4;
+    const int base = crop * kIn + ((G::stride * oz * G::din + G::stride * oy) * G::din + G::stride * ox) * G::cin * 2;
+    int rowmask = (ox == 0) | ((oy == 0) << 1) | ((oz == 0) << 2) | 64;
+    if (G::stride == 1) rowmask |= ((ox == 3) << 3) | ((oy == 3) << 4) | ((oz == 3) << 5);
+    const int jj = tid >> 7;  // A chunks jj and jj + 4 of a stage (warp-uniform)
+    const int br = tid >> 3, bj = tid & 7;  // the B chunk (weight row br, chunk bj) this thread copies
+    uint32_t g = 0, nb = 0;
+    bool ok = true;
+    auto wait_warp = [&](uint64_t *bar, uint32_t par) {
+      return __all_sync(0xffffffffu, wait_abortable(bar, par, abort)) != 0;
+    };
+    auto builders_sync = [&]() {
+      tc::fence_before_sync();
+      mbar_arrive(&bsync);
+      const bool r_ok = __all_sync(0xffffffffu, wait_abortable(&bsync, nb & 1u, abort)) != 0;
+      ++nb;
+      tc::fence_after_sync();
+      return r_ok;
+    };
+    // the tile's two crops (the second may be past the batch: zeros)
+    auto stage_input = [&](int64_t tile) {
+      const uint32_t dst = tc::smem_u32(sin);
+      for (int c = tid; c < 2 * kIn / 16; c += kBuilders) {
+        const int64_t v = 2 * tile + (c * 16) / kIn;
+        const bool valid = v < n_views;
+        const uint8_t *src = (const uint8_t *)in + (valid ? (2 * tile * (int64_t)kIn + (int64_t)c * 16) : 0);
+        tc::cp_async16(dst + c * 16, src, valid);
+      }
+      tc::cp_async_commit();
+    };
+    int64_t tile = blockIdx.x;
+    if (tile < n_tiles) stage_input(tile);
+    for (; tile < n_tiles && ok; tile += gridDim.x) {
+      tc::cp_async_wait<0>();
+      ok = builders_sync();  // this tile's input staged
+      if (!ok) break;
+      for (int ks = 0; ks < G::stages && ok; ++ks, ++g) {
+        const uint32_t b = g % kBuf;
+        if (g >= kBuf) {
+          ok = wait_warp(&empty[b], ((g - kBuf) / kBuf) & 1u);
+          if (!ok) break;
+        }
+        uint8_t *sa = stg + b * (kStageA + kStageB), *sb = sa + kStageA;
+        {  // B: weight rows 0..63, K chunks 8 ks .. 8 ks + 7
+          const int kc = ks * 8 + bj;
+          const bool valid = kc < kChunks;
+          const bf16 *src = w + (valid ? (size_t)br * kK + kc * 8 : 0);
+          tc::cp_async16(tc::smem_u32(sb + (bj >> 1) * (64 * 32) + (br >> 3) * 256 + (bj & 1) * 128 + (br & 7) * 16),
+                         src, valid);
+          tc::cp_async_commit();
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {  // A: im2col from the staged input
+          const int j = jj + 4 * i;
+          const int2 ti = tapinfo[ks * 8 + j];
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          if ((rowmask & ti.y) == 0) v = *(const uint4 *)(sin + base + ti.x);
+          *(uint4 *)(sa + (j >> 1) * (128 * 32) + (r >> 3) * 256 + (j & 1) * 128 + (r & 7) * 16) = v;
+        }
+        tc::cp_async_wait<0>();
+        tc::fence_smem_async();
+        tc::fence_before_sync();
+        mbar_arrive(&full[b]);
+      }
+      if (!ok) break;
+      // every stage of this tile built: stage the next tile's input meanwhile
+      const int64_t next = tile + gridDim.x;
+      ok = builders_sync();  // all builders are done reading this tile's input
+      if (!ok) break;
+      if (next < n_tiles) stage_input(next);
+      {
+        const uint32_t gl = g - 1;
+        ok = wait_warp(&empty[gl % kBuf], (gl / kBuf) & 1u);  // the tile's last commit covers all its MMAs
+      }
+      if (!ok) break;
+      tc::fence_after_sync();
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(part * 16), v);
+      const int64_t m = 2 * tile * 64 + r;
+      if (m < n_views * 64) {
+        uint32_t u[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(v[2 * q] + sbias[part * 16 + 2 * q], 0.0f),
+                                                         fmaxf(v[2 * q + 1] + sbias[part * 16 + 2 * q + 1], 0.0f));
+          u[q] = *(const uint32_t *)&h;
+        }
+        bf16 *d = L == 2 ? out + m * 64 + part * 16 : out + (m >> 6) * kFcIn + (m & 63) * 64 + part * 16;
+        ((uint4 *)d)[0] = make_uint4(u[0], u[1], u[2], u[3]);
+        ((uint4 *)d)[1] = make_uint4(u[4], u[5], u[6], u[7]);
+      }
+      tc::fence_before_sync();  // accumulator read before the next tile's MMAs (ordered by the full barriers)
+    }
+    tc::cp_async_wait<0>();
+    if (!ok) *abort = 1;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (*abort && tid == 0) atomicExch(err, 1);
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
 // Layer 0 weight gradient on one-hot crops: dW0[co][tap][class] is the sum
 // of dy[o][co] over the output voxels o whose tap input has that class.  CTA
 // c reduces output voxels [c chunk, (c + 1) chunk) in order into
@@ -1239,6 +1459,21 @@ int launch_conv01(nbt_surrogate net, const uint8_t *crops, int n, cudaStream_t s
   return NBT_OK;
 }
 
+// Layers 2 and 3 from shared-memory-staged inputs: one persistent CTA per SM.
+template <int L>
+int launch_conv23(nbt_surrogate net, const bf16 *in, bf16 *out, int n, cudaStream_t s) {
+  int *err = nullptr;
+  int rc = dev_err_word(&err);
+  if (rc != NBT_OK) return rc;
+  constexpr size_t smem = (size_t)c23::kSmem + 128;
+  NBT_CUDA_TRY(cudaFuncSetAttribute(conv23_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = std::min((n + 1) / 2, sm_count());
+  conv23_kernel<L><<<(unsigned)grid, c23::kBuilders + 32, smem, s>>>(in, net->wb + (L == 2 ? kW2 : kW3),
+                                                                     net->params + (L == 2 ? kB2 : kB3), n, out, err);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
 // fused: layers 0 and 1 in one kernel (inference; training keeps the layer-0
 // activation for the backward pass and runs them separately).
 int forward_batch(nbt_surrogate net, const uint8_t *crops, const bf16 *feats, int n, float *pred, cudaStream_t s,
@@ -1256,6 +1491,12 @@ int forward_batch(nbt_surrogate net, const uint8_t *crops, const bf16 *feats, in
   }
   const bf16 *in = net->act[first - 1];
   for (int l = first; l < kLayers; ++l) {
+    if (l >= 2) {  // 4^3-output layers: inputs staged in shared memory, same sums as the generic GEMM
+      const int rc = l == 2 ? launch_conv23<2>(net, in, net->act[2], n, s) : launch_conv23<3>(net, in, net->x, n, s);
+      if (rc != NBT_OK) return rc;
+      in = net->act[l];
+      continue;
+    }
     const LayerDims &L = kL[l];
     const int M = n * L.dout * L.dout * L.dout;
     const ConvFwdLoader la{in, M, L.din, L.stride, ilog2(L.dout), ilog2(L.cin / 8), L.cin};
