@@ -296,8 +296,7 @@ struct CropConst {
 };
 
 // LINEAR: linear x-fastest layout, element index (z ny + y) nx + x computed
-// instead of read from the offset tables.  Four samples per iteration so
-// that each thread has several map reads in flight.
+// instead of read from the offset tables.  Launched with 256 threads.
 template <int KIND, bool LINEAR>
 __global__ void __launch_bounds__(256) crop_kernel(DevMap m, CropConst cc, const float *__restrict__ poses, int64_t n,
                                                    uint8_t *__restrict__ crops, bf16 *__restrict__ feats) {
@@ -325,41 +324,57 @@ __global__ void __launch_bounds__(256) crop_kernel(DevMap m, CropConst cc, const
     for (int a = 0; a < 3; ++a) o[a] = s_o[a];
     const int dims[3] = {m.nx, m.ny, m.nz};
     uint8_t *cv = crops + v * (int64_t)(kCrop * kCrop * kCrop);
-#pragma unroll 4
-    for (int cell = threadIdx.x; cell < kCrop * kCrop * kCrop; cell += blockDim.x) {
-      const int i = cell & 31, j = (cell >> 5) & 31, k = cell >> 10;
-      const float fr = fmul(fadd((float)k, 0.5f), 0.03125f);   // (k + 1/2) / 32, exact
-      const float cx = fadd(cc.x0, fmul((float)i, cc.xs));
-      const float cy = fadd(cc.y0, fmul((float)j, cc.ys));
-      const float p[3] = {fmul(cx, fr), fmul(cy, fr), fmul(cc.zc, fr)};
-      int idx[3];
-      bool inside = true;
+    // Sample (i, j, k) of cell i + 32 j + 1024 k.  With 256 threads a thread
+    // keeps i = tid % 32 and takes j = tid / 32 + 8 q (q = 0..3) for every
+    // k, so the factors that depend on i or k alone are formed once per k;
+    // each sample still runs the same operations in the same order.
+    const int i = threadIdx.x & 31, j0 = threadIdx.x >> 5;
+    const float cx = fadd(cc.x0, fmul((float)i, cc.xs));
+    float cyq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cyq[q] = fadd(cc.y0, fmul((float)(j0 + 8 * q), cc.ys));
+    for (int k = 0; k < kCrop; ++k) {
+      const float fr = fmul(fadd((float)k, 0.5f), 0.03125f);  // (k + 1/2) / 32, exact
+      const float px = fmul(cx, fr), pz = fmul(cc.zc, fr);
+      float rx[3], rz[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const float w = fadd(fadd(fmul(r[3 * a], p[0]), fmul(r[3 * a + 1], p[1])), fmul(r[3 * a + 2], p[2]));
-        const float q = fadd(o[a], fmul(w, cc.inv_s));
-        const float fl = floorf(q);
-        inside = inside && fl >= 0.0f && fl < (float)dims[a];
-        idx[a] = inside ? (int)fl : 0;
+        rx[a] = fmul(r[3 * a], px);
+        rz[a] = fmul(r[3 * a + 2], pz);
       }
-      uint32_t cls = 3u;  // 3 = outside: no channel set
-      if (inside) {
-        const int32_t off = LINEAR ? (idx[2] * m.ny + idx[1]) * m.nx + idx[0]
-                                   : m.tab[idx[0]] + m.tab[m.nx + idx[1]] + m.tab[m.nx + m.ny + idx[2]];
-        if (KIND == PAYLOAD_GAIN_F32) {
-          const float pv = __ldg((const float *)m.payload + off);
-          cls = pv > cc.occ_thr ? 2u : (pv < cc.free_thr ? 1u : 0u);
-        } else if (KIND == PAYLOAD_U8) {
-          const uint32_t st = __ldg((const uint8_t *)m.payload + off);
-          cls = st >= 2u ? 2u : st;
-        } else {
-          const uint32_t byte = __ldg((const uint8_t *)m.payload + (off >> 2));
-          const uint32_t st = (byte >> ((off & 3) << 1)) & 3u;
-          cls = st >= 2u ? 2u : st;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float py = fmul(cyq[q], fr);
+        const int cell = k * 1024 + (j0 + 8 * q) * 32 + i;
+        int idx[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float w = fadd(fadd(rx[a], fmul(r[3 * a + 1], py)), rz[a]);
+          const float qa = fadd(o[a], fmul(w, cc.inv_s));
+          const float fl = floorf(qa);
+          inside = inside && fl >= 0.0f && fl < (float)dims[a];
+          idx[a] = inside ? (int)fl : 0;
         }
+        uint32_t cls = 3u;  // 3 = outside: no channel set
+        if (inside) {
+          const int32_t off = LINEAR ? (idx[2] * m.ny + idx[1]) * m.nx + idx[0]
+                                     : m.tab[idx[0]] + m.tab[m.nx + idx[1]] + m.tab[m.nx + m.ny + idx[2]];
+          if (KIND == PAYLOAD_GAIN_F32) {
+            const float pv = __ldg((const float *)m.payload + off);
+            cls = pv > cc.occ_thr ? 2u : (pv < cc.free_thr ? 1u : 0u);
+          } else if (KIND == PAYLOAD_U8) {
+            const uint32_t st = __ldg((const uint8_t *)m.payload + off);
+            cls = st >= 2u ? 2u : st;
+          } else {
+            const uint32_t byte = __ldg((const uint8_t *)m.payload + (off >> 2));
+            const uint32_t st = (byte >> ((off & 3) << 1)) & 3u;
+            cls = st >= 2u ? 2u : st;
+          }
+        }
+        // code: 0 outside the map, else 1 + class (unknown, free, occupied)
+        cv[cell] = (uint8_t)(cls < 3u ? cls + 1u : 0u);
       }
-      // code: 0 outside the map, else 1 + class (unknown, free, occupied)
-      cv[cell] = (uint8_t)(cls < 3u ? cls + 1u : 0u);
     }
     if (threadIdx.x == 0) {
       const float ext[3] = {cc.ext_x, cc.ext_y, cc.ext_z};
