@@ -465,62 +465,61 @@ __global__ void __launch_bounds__(256) conv0_lookup_kernel(const uint8_t *__rest
 
 // ---------------------------------------------------------------------------
 // Layers 0 and 1 fused for inference: one CTA of 17 warps per crop at a
-// time (persistent, one CTA per SM), both layers on tcgen05 with every
-// operand in shared memory; only layer 1's output goes to global memory.
+// time (persistent, one CTA per SM), both layers on tcgen05 with the A
+// operands in tensor memory; only layer 1's output goes to global memory.
 //
 // Layer 0 as a GEMM over one-hot inputs: rows = output voxels (16^3 per
 // crop, 32 tiles of 128), K = 28 taps x 4 slots (tap 27 and slot 3 are
 // zero), slot s of a tap = 1.0 where the tap's input class code is s + 1;
-// B = W0 on the three class channels.  The crop's codes are repacked to 2
-// bits (one 64-bit word per x-row); the three codes a tap row needs (x =
-// 2 ox - 1 .. 2 ox + 1) come out of one shift, and a 16-byte chunk of A
-// (two taps) is one entry of a 16-entry table indexed by the two codes.
-// Two A tiles in flight.  Bias and ReLU in the epilogue, which writes the
+// B = W0 on the three class channels (shared memory).  The crop's codes are
+// repacked to 2 bits (one 64-bit word per x-row); the three codes a tap row
+// needs (x = 2 ox - 1 .. 2 ox + 1) come out of one shift, and a 16-byte
+// chunk of A (two taps) is one entry of a 16-entry table indexed by the two
+// codes, stored by the row's own thread into its TMEM lane (tcgen05.st).
+// Four A tiles in flight.  Bias and ReLU in the epilogue, which writes the
 // layer-0 activation into shared memory as [channel group 0..1][z][y][x']
 // 16-byte vectors with x' = (x & 1) * 8 + x / 2: the stride-2 reads of
 // layer 1 then hit consecutive vectors.
 // Layer 1: rows = 8^3 output voxels (4 tiles of 128), K = 27 taps x 16
-// channels (padded to 7 stages of 64), three stages in flight, copied
-// shared -> shared: the source of (row, chunk) is a per-row offset plus a
-// per-chunk offset, zero where the tap falls in the padding (a 3-bit mask
-// test); W1 stays resident.  Accumulators: layer 0 in 8 TMEM slots of 16
-// columns, layer 1 in 4 x 32.  Every mbarrier wait is bounded.
+// channels (padded to 7 stages of 64), six stages in flight: each A chunk is
+// read from the shared layer-0 activation (per-row offset plus per-chunk
+// offset, zero where the tap falls in the padding: a 3-bit mask test) and
+// stored into TMEM; W1 stays resident in shared memory.  TMEM: layer-0
+// accumulators in 8 slots of 16 columns (0-127), layer 1 in 4 x 32
+// (128-255), A stages from column 256.  Every mbarrier wait is bounded.
 // ---------------------------------------------------------------------------
 namespace fz {
 constexpr int kThreads = 512;                  // builder threads (plus one MMA warp)
 constexpr int kK0 = 112;                       // layer-0 K: 28 taps x 4 slots
-constexpr int kTile0 = 128 * kK0 * 2;          // 28,672 B
 constexpr int kTiles0 = 32;                    // 16^3 / 128
 constexpr int kTiles1 = 4;                     // 8^3 / 128
 constexpr int kStages1 = 7;                    // layer-1 K stages of 64 per tile
-constexpr int kStage1 = 128 * 64 * 2;          // 16,384 B
-constexpr int kBuf1 = 3;
+constexpr int kBuf0 = 4;                       // layer-0 A tiles in flight (56 TMEM columns each)
+constexpr int kBuf1 = 6;                       // layer-1 A stages in flight (32 TMEM columns each)
+constexpr uint32_t kColA = 256;                // TMEM columns 0-127: layer-0 accumulators, 128-255: layer 1
+constexpr uint32_t kColsA0 = kK0 / 2, kColsA1 = 32;
 constexpr int kOffCodes = 0;                   // 32 x 32 x-rows x 8 B
 constexpr int kOffAct0 = kOffCodes + 8192;     // 2 x 16^3 x 16 B
 constexpr int kOffW0 = kOffAct0 + 131072;      // 7 K16 blocks x 16 rows x 32 B
 constexpr int kOffW1 = kOffW0 + 3584;          // 28 K16 blocks x 32 rows x 32 B
-constexpr int kOffStage = kOffW1 + 28672;      // 2 layer-0 tiles / 3 layer-1 stages
-constexpr int kOffLut = kOffStage + 2 * kTile0;
+constexpr int kOffLut = kOffW1 + 28672;
 constexpr int kOffTap = kOffLut + 256;         // 64 x (offset, mask) for layer-1 chunks
-constexpr int kSmem = kOffTap + 512;           // 229,632 B
-constexpr uint32_t kTmemCols = 256;
-static_assert(kBuf1 * kStage1 <= 2 * kTile0, "layer-1 stages reuse the layer-0 tile space");
-
-// Offset of 16-byte chunk (row r, chunk kc) in a 128-row stage.
-__device__ __forceinline__ uint32_t a_off(int r, int kc) {
-  return (uint32_t)((kc >> 1) * (128 * 32) + (r >> 3) * 256 + (kc & 1) * 128 + (r & 7) * 16);
-}
+constexpr int kSmem = kOffTap + 512;           // 172,288 B
+constexpr uint32_t kTmemCols = 512;
+static_assert(kColA + kBuf0 * kColsA0 <= kTmemCols && kColA + kBuf1 * kColsA1 <= kTmemCols, "TMEM budget");
 
 // One-hot slots of class code c (0: none) as four BF16 values.
 __host__ __device__ constexpr uint64_t onehot4(uint32_t c) { return (0x3F80ull << (16u * c)) >> 16; }
 
 
-// Chunks [C0, C1) of layer-0 A row r (output voxel (ox, oy, oz)), i.e.
-// taps 2 C0 .. 2 C1 - 1: per tap row (dz, dy) the codes of x = 2 ox - 1 ..
-// 2 ox + 1 at bits 0, 2, 4 of one word (x = -1 and rows outside the crop
-// read as 0), then one table entry per pair of taps.
+// Chunks [C0, C1) of this thread's layer-0 A row (output voxel (ox, oy,
+// oz)), i.e. taps 2 C0 .. 2 C1 - 1: per tap row (dz, dy) the codes of x =
+// 2 ox - 1 .. 2 ox + 1 at bits 0, 2, 4 of one word (x = -1 and rows outside
+// the crop read as 0), then one table entry per pair of taps, stored into
+// TMEM columns 4 kc .. 4 kc + 3 of the row's lane (trow: the tile's first
+// column, the warp's lane quarter).
 template <int C0, int C1>
-__device__ __forceinline__ void build0(const uint64_t *codes, const uint4 *lut, uint8_t *tile, int r, int ox, int oy,
+__device__ __forceinline__ void build0(const uint64_t *codes, const uint4 *lut, uint32_t trow, int ox, int oy,
                                        int oz) {
   constexpr int n = 2 * (C1 - C0);
   uint32_t cd[n];
@@ -543,7 +542,7 @@ __device__ __forceinline__ void build0(const uint64_t *codes, const uint4 *lut, 
     cd[i] = (rowv >> (2 * (tap % 3))) & 3u;
   }
 #pragma unroll
-  for (int j = 0; j < C1 - C0; ++j) *(uint4 *)(tile + a_off(r, C0 + j)) = lut[cd[2 * j] | (cd[2 * j + 1] << 2)];
+  for (int j = 0; j < C1 - C0; ++j) tc::tmem_st4(trow + 4u * (C0 + j), lut[cd[2 * j] | (cd[2 * j + 1] << 2)]);
 }
 }  // namespace fz
 
@@ -568,10 +567,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // Warps 0-15 build the A stages (and read the accumulators back); warp 16
 // waits for each stage to be complete, issues its MMAs and commits them.
 // A stage is complete when all 512 builder threads have arrived on its
-// "full" barrier (each after its own stores and an async-proxy fence); the
+// "full" barrier (each after its own TMEM stores have completed); the
 // commit arrives on its "empty" barrier, which the builders wait for before
 // refilling the buffer or reading the accumulator.  No CTA-wide barrier
-// inside the crop loop: the builders run up to two layer-0 tiles / three
+// inside the crop loop: the builders run up to four layer-0 tiles / six
 // layer-1 stages ahead of the tensor core.
 __global__ void __launch_bounds__(fz::kThreads + 32, 1)
     conv01_kernel(const uint8_t *__restrict__ codes, const bf16 *__restrict__ wb, const float *__restrict__ params,
@@ -579,14 +578,14 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
   using namespace fz;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  __shared__ uint64_t full0[2], empty0[2], full1[kBuf1], empty1[kBuf1], bsync;
+  __shared__ uint64_t full0[kBuf0], empty0[kBuf0], full1[kBuf1], empty1[kBuf1], bsync;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ float bias0[16], bias1[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint64_t *codes64 = (uint64_t *)(sm + kOffCodes);
   uint8_t *act0 = sm + kOffAct0;
-  uint8_t *w0s = sm + kOffW0, *w1s = sm + kOffW1, *stg = sm + kOffStage;
+  uint8_t *w0s = sm + kOffW0, *w1s = sm + kOffW1;
   uint4 *lut = (uint4 *)(sm + kOffLut);
   int2 *tapinfo = (int2 *)(sm + kOffTap);
   volatile int *abort = &abort_flag;
@@ -622,7 +621,7 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
   }
   if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kBuf0; ++i) {
       tc::mbar_init(&full0[i], kThreads);
       tc::mbar_init(&empty0[i], 1);
     }
@@ -646,7 +645,6 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
     constexpr uint32_t idesc1 = tc::idesc_bf16(128, 32);
     // descriptors built once; a byte offset o moves the start address field
     // by o / 16 (no carry out of its 14 bits: shared memory is < 256 KB)
-    const uint64_t stg_d = tc::sdesc(tc::smem_u32(stg), 128, 256);
     const uint64_t w0_d = tc::sdesc(tc::smem_u32(w0s), 128, 256);
     const uint64_t w1_d = tc::sdesc(tc::smem_u32(w1s), 128, 256);
     uint32_t g0 = 0, g1 = 0;
@@ -655,20 +653,20 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
     uint32_t last_par = 0;
     for (int64_t view = blockIdx.x; view < n_views && ok; view += gridDim.x) {
       for (int t = 0; t < kTiles0 && ok; ++t) {
-        const uint32_t g = g0 + (uint32_t)t, b = g & 1u;
-        ok = __all_sync(0xffffffffu, wait_abortable(&full0[b], (g >> 1) & 1u, abort)) != 0;
+        const uint32_t g = g0 + (uint32_t)t, b = g % kBuf0;
+        ok = __all_sync(0xffffffffu, wait_abortable(&full0[b], (g / kBuf0) & 1u, abort)) != 0;
         if (ok && lane == 0) {
           tc::fence_after_sync();
-          const uint64_t a0 = stg_d + (b * kTile0 >> 4);
+          const uint32_t a0 = tmem + kColA + b * kColsA0;
           const uint32_t d = tmem + (uint32_t)((t & 7) * 16);
 #pragma unroll
           for (int kk = 0; kk < kK0 / 16; ++kk)
-            tc::mma_bf16(d, a0 + kk * (128 * 32 / 16), w0_d + kk * (16 * 32 / 16), idesc0, kk > 0 ? 1u : 0u);
+            tc::mma_bf16_ta(d, a0 + 8u * kk, w0_d + kk * (16 * 32 / 16), idesc0, kk > 0 ? 1u : 0u);
           tc::mma_commit(&empty0[b]);
         }
         if (ok) {
           last_bar = &empty0[b];
-          last_par = (g >> 1) & 1u;
+          last_par = (g / kBuf0) & 1u;
         }
         __syncwarp();
       }
@@ -679,11 +677,12 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
         ok = __all_sync(0xffffffffu, wait_abortable(&full1[b], (g / kBuf1) & 1u, abort)) != 0;
         if (ok && lane == 0) {
           tc::fence_after_sync();
-          const uint64_t a0 = stg_d + (b * kStage1 >> 4), b0 = w1_d + ks * (4 * 32 * 32 / 16);
+          const uint32_t a0 = tmem + kColA + b * kColsA1;
+          const uint64_t b0 = w1_d + ks * (4 * 32 * 32 / 16);
           const uint32_t d = tmem + 128u + (uint32_t)(mt * 32);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            tc::mma_bf16(d, a0 + kk * (128 * 32 / 16), b0 + kk * (32 * 32 / 16), idesc1, (ks | kk) != 0 ? 1u : 0u);
+            tc::mma_bf16_ta(d, a0 + 8u * kk, b0 + kk * (32 * 32 / 16), idesc1, (ks | kk) != 0 ? 1u : 0u);
           tc::mma_commit(&empty1[b]);
         }
         if (ok) {
@@ -719,9 +718,9 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
       tc::fence_after_sync();
       return r_ok;
     };
-    // publish this thread's stage stores (and earlier accumulator reads) to the MMA warp
+    // publish this thread's TMEM stage stores (and earlier accumulator reads) to the MMA warp
     auto publish = [&](uint64_t *bar) {
-      tc::fence_smem_async();
+      tc::tmem_wait_st();
       tc::fence_before_sync();
       mbar_arrive(bar);
     };
@@ -758,29 +757,33 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
         }
       }
       ok = builders_sync();  // codes complete
-      // ---- layer 0: 32 tiles of 128 output voxels, two A tiles in flight ----
+      // ---- layer 0: 32 tiles of 128 output voxels, four A tiles in flight ----
+      // Tile t's A buffer was last used by tile t - 4, whose MMAs precede
+      // those of tile t - 2, awaited for its epilogue; at a crop's first
+      // tiles the previous crop's MMAs are all done.
       const int ox0 = r & 15;  // the same for every tile
       for (int t = 0; t < kTiles0 && ok; ++t) {
-        const uint32_t g = g0 + (uint32_t)t, b = g & 1u;
+        const uint32_t g = g0 + (uint32_t)t, b = g % kBuf0;
         if (t >= 2) {
-          ok = wait_warp(&empty0[b], ((g - 2u) >> 1) & 1u);  // tile t - 2: buffer free, accumulator ready
+          const uint32_t ge = g - 2u;
+          ok = wait_warp(&empty0[ge % kBuf0], (ge / kBuf0) & 1u);  // tile t - 2 done: accumulator ready
           if (!ok) break;
           epi0(t - 2);
         }
         const int oy = (8 * t + (r >> 4)) & 15, oz = t >> 1;
-        uint8_t *tile = stg + b * kTile0;
+        const uint32_t trow = tmem + lane_base + kColA + b * kColsA0;
         switch (part) {  // chunks 0-3, 4-7, 8-10, 11-13
-          case 0: build0<0, 4>(codes64, lut, tile, r, ox0, oy, oz); break;
-          case 1: build0<4, 8>(codes64, lut, tile, r, ox0, oy, oz); break;
-          case 2: build0<8, 11>(codes64, lut, tile, r, ox0, oy, oz); break;
-          default: build0<11, 14>(codes64, lut, tile, r, ox0, oy, oz); break;
+          case 0: build0<0, 4>(codes64, lut, trow, ox0, oy, oz); break;
+          case 1: build0<4, 8>(codes64, lut, trow, ox0, oy, oz); break;
+          case 2: build0<8, 11>(codes64, lut, trow, ox0, oy, oz); break;
+          default: build0<11, 14>(codes64, lut, trow, ox0, oy, oz); break;
         }
         publish(&full0[b]);
       }
       if (!ok) break;
       {
         const uint32_t g = g0 + kTiles0 - 1;
-        ok = wait_warp(&empty0[g & 1u], (g >> 1) & 1u);  // the last tile's commit covers every layer-0 MMA
+        ok = wait_warp(&empty0[g % kBuf0], (g / kBuf0) & 1u);  // the last tile's commit covers every layer-0 MMA
       }
       if (!ok) break;
       epi0(kTiles0 - 2);
@@ -788,7 +791,7 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
       g0 += kTiles0;
       ok = builders_sync();  // act0 complete
       if (!ok) break;
-      // ---- layer 1: 4 M tiles x 7 K stages, three stages in flight ----
+      // ---- layer 1: 4 M tiles x 7 K stages, six stages in flight ----
       {
         const int jj = tid >> 7;  // this thread's chunks of a stage: jj and jj + 4 (warp-uniform)
         const int ox = r & 7, oy = (r >> 3) & 7, ozl = r >> 6;
@@ -802,14 +805,14 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
           const int oz = 2 * mt + ozl;
           const int base = oz * 8192 + oy * 512 + ox * 16;
           const int low = (ox == 0) | ((oy == 0) << 1) | ((oz == 0) << 2) | 8;
-          uint8_t *st = stg + b * kStage1;
+          const uint32_t trow = tmem + lane_base + kColA + b * kColsA1;
 #pragma unroll
           for (int i = 0; i < 2; ++i) {
             const int j = jj + 4 * i;
             const int2 ti = tapinfo[ks * 8 + j];
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if ((low & ti.y) == 0) v = *(const uint4 *)(act0 + base + ti.x);
-            *(uint4 *)(st + a_off(r, j)) = v;
+            tc::tmem_st4(trow + 4u * j, v);
           }
           publish(&full1[b]);
         }
