@@ -854,21 +854,24 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
 // once and the im2col stages are copied shared -> shared instead of
 // gathering each input vector up to 27 times from L2.  Same K order, same
 // MMA sequence and same epilogues as the generic implicit GEMM, so the
-// outputs are bit-identical.  One persistent CTA per SM: 16 builder warps
-// (A from the staged input, B = the weight stage by cp.async), one MMA warp,
-// four stages in flight on full/empty mbarriers; the next tile's input is
-// staged while the current tile's last MMAs run.
+// outputs are bit-identical.  Two persistent CTAs per SM, each 8 builder
+// warps (A from the staged input into TMEM, B = the weight stage into
+// shared memory by cp.async) and one MMA warp, four stages in flight on
+// full/empty mbarriers; the next tile's input is staged while the current
+// tile's last MMAs run.
 // ---------------------------------------------------------------------------
 namespace c23 {
-constexpr int kBuilders = 512;
+constexpr int kBuilders = 256;                   // builder threads (plus one MMA warp); two CTAs per SM
+constexpr int kParts = kBuilders / 128;          // builders per tile row
 constexpr int kBuf = 4;
-constexpr int kStageA = 128 * 64 * 2;            // 16 KB
-constexpr int kStageB = 64 * 64 * 2;             // 8 KB
+constexpr int kStageB = 64 * 64 * 2;             // 8 KB of weights per stage (A stages live in TMEM)
 constexpr int kMaxIn = 2 * 8 * 8 * 8 * 32 * 2;   // two crops of layer 2's input: 64 KB
 constexpr int kOffIn = 0;
 constexpr int kOffStage = kOffIn + kMaxIn;
-constexpr int kOffTap = kOffStage + kBuf * (kStageA + kStageB);
-constexpr int kSmem = kOffTap + 256 * 8;         // 165,888 B
+constexpr int kOffTap = kOffStage + kBuf * kStageB;
+constexpr int kSmem = kOffTap + 256 * 8;         // 100,352 B
+constexpr uint32_t kColA = 64, kColsA = 32;      // TMEM: accumulator in columns 0-63, A stages after it
+constexpr uint32_t kTmemCols = 256;
 
 template <int L>
 struct Geo;
@@ -883,7 +886,7 @@ struct Geo<3> {
 }  // namespace c23
 
 template <int L>
-__global__ void __launch_bounds__(c23::kBuilders + 32, 1)
+__global__ void __launch_bounds__(c23::kBuilders + 32, 2)
     conv23_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const float *__restrict__ bias,
                   int64_t n_views, bf16 *__restrict__ out, int *err) {
   using namespace c23;
@@ -914,7 +917,7 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 1)
     if (G::stride == 1) mask |= ((dx == 2) << 3) | ((dy == 2) << 4) | ((dz == 2) << 5);
     tapinfo[kc] = make_int2(off, kc < kChunks ? mask : 64);
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 64);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
   if (tid == 0) {
     for (int i = 0; i < kBuf; ++i) {
       tc::mbar_init(&full[i], kBuilders);
@@ -943,10 +946,11 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 1)
         ok = __all_sync(0xffffffffu, wait_abortable(&full[b], (g / kBuf) & 1u, abort)) != 0;
         if (ok && lane == 0) {
           tc::fence_after_sync();
-          const uint64_t a0 = stg_d + (b * (kStageA + kStageB) >> 4), b0 = a0 + (kStageA >> 4);
+          const uint64_t b0 = stg_d + (b * kStageB >> 4);
+          const uint32_t a0 = tmem + kColA + b * kColsA;
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            tc::mma_bf16(tmem, a0 + kk * (128 * 32 / 16), b0 + kk * (64 * 32 / 16), idesc, (ks | kk) != 0 ? 1u : 0u);
+            tc::mma_bf16_ta(tmem, a0 + 8u * kk, b0 + kk * (64 * 32 / 16), idesc, (ks | kk) != 0 ? 1u : 0u);
           tc::mma_commit(&empty[b]);
         }
         if (ok) {
@@ -969,8 +973,7 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 1)
     const int base = crop * kIn + ((G::stride * oz * G::din + G::stride * oy) * G::din + G::stride * ox) * G::cin * 2;
     int rowmask = (ox == 0) | ((oy == 0) << 1) | ((oz == 0) << 2) | 64;
     if (G::stride == 1) rowmask |= ((ox == 3) << 3) | ((oy == 3) << 4) | ((oz == 3) << 5);
-    const int jj = tid >> 7;  // A chunks jj and jj + 4 of a stage (warp-uniform)
-    const int br = tid >> 3, bj = tid & 7;  // the B chunk (weight row br, chunk bj) this thread copies
+    const int jj = tid >> 7;  // A chunks jj, jj + kParts, ... of a stage (warp-uniform)
     uint32_t g = 0, nb = 0;
     bool ok = true;
     auto wait_warp = [&](uint64_t *bar, uint32_t par) {
@@ -1007,24 +1010,28 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 1)
           ok = wait_warp(&empty[b], ((g - kBuf) / kBuf) & 1u);
           if (!ok) break;
         }
-        uint8_t *sa = stg + b * (kStageA + kStageB), *sb = sa + kStageA;
-        {  // B: weight rows 0..63, K chunks 8 ks .. 8 ks + 7
+        uint8_t *sb = stg + b * kStageB;
+        const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + kColA + b * kColsA;
+#pragma unroll
+        for (int i = 0; i < 512 / kBuilders; ++i) {  // B: weight rows 0..63, K chunks 8 ks .. 8 ks + 7
+          const int c = tid + kBuilders * i, br = c >> 3, bj = c & 7;
           const int kc = ks * 8 + bj;
           const bool valid = kc < kChunks;
           const bf16 *src = w + (valid ? (size_t)br * kK + kc * 8 : 0);
           tc::cp_async16(tc::smem_u32(sb + (bj >> 1) * (64 * 32) + (br >> 3) * 256 + (bj & 1) * 128 + (br & 7) * 16),
                          src, valid);
-          tc::cp_async_commit();
         }
+        tc::cp_async_commit();
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {  // A: im2col from the staged input
-          const int j = jj + 4 * i;
+        for (int i = 0; i < 8 / kParts; ++i) {  // A: im2col from the staged input
+          const int j = jj + kParts * i;
           const int2 ti = tapinfo[ks * 8 + j];
           uint4 v = make_uint4(0u, 0u, 0u, 0u);
           if ((rowmask & ti.y) == 0) v = *(const uint4 *)(sin + base + ti.x);
-          *(uint4 *)(sa + (j >> 1) * (128 * 32) + (r >> 3) * 256 + (j & 1) * 128 + (r & 7) * 16) = v;
+          tc::tmem_st4(trow + 4u * j, v);
         }
         tc::cp_async_wait<0>();
+        tc::tmem_wait_st();
         tc::fence_smem_async();
         tc::fence_before_sync();
         mbar_arrive(&full[b]);
@@ -1041,20 +1048,24 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 1)
       }
       if (!ok) break;
       tc::fence_after_sync();
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(part * 16), v);
       const int64_t m = 2 * tile * 64 + r;
-      if (m < n_views * 64) {
-        uint32_t u[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(v[2 * q] + sbias[part * 16 + 2 * q], 0.0f),
-                                                         fmaxf(v[2 * q + 1] + sbias[part * 16 + 2 * q + 1], 0.0f));
-          u[q] = *(const uint32_t *)&h;
+      for (int h = 0; h < 64 / kParts / 16; ++h) {  // columns n0 .. n0 + 15 of this row
+        const int n0 = part * (64 / kParts) + 16 * h;
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)n0, v);
+        if (m < n_views * 64) {
+          uint32_t u[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const __nv_bfloat162 hh = __floats2bfloat162_rn(fmaxf(v[2 * q] + sbias[n0 + 2 * q], 0.0f),
+                                                            fmaxf(v[2 * q + 1] + sbias[n0 + 2 * q + 1], 0.0f));
+            u[q] = *(const uint32_t *)&hh;
+          }
+          bf16 *d = L == 2 ? out + m * 64 + n0 : out + (m >> 6) * kFcIn + (m & 63) * 64 + n0;
+          ((uint4 *)d)[0] = make_uint4(u[0], u[1], u[2], u[3]);
+          ((uint4 *)d)[1] = make_uint4(u[4], u[5], u[6], u[7]);
         }
-        bf16 *d = L == 2 ? out + m * 64 + part * 16 : out + (m >> 6) * kFcIn + (m & 63) * 64 + part * 16;
-        ((uint4 *)d)[0] = make_uint4(u[0], u[1], u[2], u[3]);
-        ((uint4 *)d)[1] = make_uint4(u[4], u[5], u[6], u[7]);
       }
       tc::fence_before_sync();  // accumulator read before the next tile's MMAs (ordered by the full barriers)
     }
@@ -1064,7 +1075,7 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 1)
   tc::fence_before_sync();
   __syncthreads();
   if (*abort && tid == 0) atomicExch(err, 1);
-  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 // Layer 0 weight gradient on one-hot crops: dW0[co][tap][class] is the sum
@@ -1485,7 +1496,7 @@ int launch_conv23(nbt_surrogate net, const bf16 *in, bf16 *out, int n, cudaStrea
   if (rc != NBT_OK) return rc;
   constexpr size_t smem = (size_t)c23::kSmem + 128;
   NBT_CUDA_TRY(cudaFuncSetAttribute(conv23_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int grid = std::min((n + 1) / 2, sm_count());
+  const int grid = std::min((n + 1) / 2, 2 * sm_count());
   conv23_kernel<L><<<(unsigned)grid, c23::kBuilders + 32, smem, s>>>(in, net->wb + (L == 2 ? kW2 : kW3),
                                                                      net->params + (L == 2 ? kB2 : kB3), n, out, err);
   NBT_CUDA_TRY(cudaGetLastError());
