@@ -127,6 +127,22 @@ def test_forward_many_views_matches_oracle_on_a_sample():
     net.close()
 
 
+def test_forward_odd_batch_matches_oracle():
+    """7 views in one batch: the last two-crop tile of layers 2-3 has no second crop."""
+    cr, ft = _batch(7, seed=11)
+    params = S.init_params(6)
+    params["b2"] += 0.02
+    params["b3"] += 0.02
+    net = gs.Surrogate(max_batch=8, params=params)
+    pred = net.forward(cr, ft).cpu().numpy().astype(np.float64)
+    y, _ = S.forward(as_used_by_gpu(params), S.codes_to_onehot(cr.cpu().numpy()), ft.float().cpu().numpy(),
+                     bf16_activations=True)
+    assert no_device_timeout()
+    assert pred.shape == (7,)
+    assert np.allclose(pred, y, rtol=2e-2, atol=2e-2 * np.abs(y).max()), (pred, y)
+    net.close()
+
+
 def test_backward_matches_oracle_gradients():
     cr, ft = _batch(8, seed=5)
     params = S.init_params(4)
