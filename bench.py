@@ -21,6 +21,7 @@ import math
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -85,7 +86,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"nbt_clocks_rank{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
