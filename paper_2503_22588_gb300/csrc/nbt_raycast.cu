@@ -313,42 +313,35 @@ __device__ __forceinline__ void ray_ig(const void *payload, const int32_t *tab, 
       walk_gain_f32<HIT>(w, lin, raw, (const float *)payload, addr_max, facc);
     else
       walk_count<KIND>(w, lin, raw, addr, (const uint8_t *)payload, addr_max, iacc);
+    // one walk step per visited voxel, each moving one plane by one: the
+    // visited count is the plane travel (exact integer-valued floats)
     steps += (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
-    return;
-  }
-  // Bricked layouts (the linear layout returned above): three voxels per
-  // iteration for FP32 gains (fewer register moves and back-edges); the
-  // 1-byte and 2-bit payloads measured no gain from it.
+  } else {
+    // Bricked layouts: three voxels per iteration for FP32 gains (fewer
+    // register moves and back-edges); the 1-byte and 2-bit payloads measured
+    // no gain from it.
 #pragma unroll(KIND == PAYLOAD_GAIN_F32 ? 3 : 1)
-  for (;;) {
-    bool more;
-    if (LINEAR) {
-      more = walk_advance_lin(w, lin);
-    } else {
-      more = walk_advance(w, tab, offx, offy, offz);
+    for (;;) {
+      const bool more = walk_advance(w, tab, offx, offy, offz);
       steps += 1u;
+      const uint32_t naddr = min((uint32_t)(offx + offy + offz), addr_max);
+      const uint32_t nraw = more ? raw_load<KIND>(payload, naddr) : 0u;
+      bool occ;
+      if (KIND == PAYLOAD_GAIN_F32) {
+        occ = (int32_t)raw < 0;
+        const float g = fabsf(__uint_as_float(raw));
+        if (HIT || !occ) facc += g;
+      } else {
+        uint32_t st = raw;
+        if (KIND == PAYLOAD_U2) st = (st >> ((addr & 3u) << 1)) & 3u;
+        occ = st >= 2u;
+        iacc += st == 0u ? 1u : 0u;  // an occupied voxel is never unknown
+      }
+      if (occ || !more) break;
+      raw = nraw;
+      addr = naddr;
     }
-    const uint32_t naddr = min(LINEAR ? (uint32_t)lin : (uint32_t)(offx + offy + offz), addr_max);
-    const uint32_t nraw = more ? raw_load<KIND>(payload, naddr) : 0u;
-    bool occ;
-    if (KIND == PAYLOAD_GAIN_F32) {
-      occ = (int32_t)raw < 0;
-      const float g = fabsf(__uint_as_float(raw));
-      if (HIT || !occ) facc += g;
-    } else {
-      uint32_t st = raw;
-      if (KIND == PAYLOAD_U2) st = (st >> ((addr & 3u) << 1)) & 3u;
-      occ = st >= 2u;
-      iacc += st == 0u ? 1u : 0u;  // an occupied voxel is never unknown
-    }
-    if (occ || !more) break;
-    raw = nraw;
-    addr = naddr;
   }
-  // Linear walk: one call of walk_advance_lin per visited voxel, each moving
-  // one plane by one, so the visited count is the plane travel (exact
-  // integer-valued floats).
-  if (LINEAR) steps += (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
 }
 
 // Latency-bound variant of ray_ig (linear layout): the walk runs K voxels

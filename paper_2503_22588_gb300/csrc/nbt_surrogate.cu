@@ -93,14 +93,6 @@ struct MatLoader {
     return (r >= rows || k >= K) ? nullptr : (const void *)(p + (size_t)r * ld + k);
   }
   __device__ __forceinline__ const void *base() const { return p; }
-  __device__ __forceinline__ uint4 chunk(int r, int kc) const {
-    const void *q = src(r, kc);
-    return q ? __ldg((const uint4 *)q) : zero4();
-  }
-  template <int ROWS>
-  __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
-    tc::fill_chunks<ROWS>(*this, s, row0, kc0, tid);
-  }
 };
 
 // Implicit im2col of a 3^3 convolution (padding 1): row m = output voxel
@@ -122,14 +114,6 @@ struct ConvFwdLoader {
     return x + ((((size_t)b * D + iz) * D + iy) * D + ix) * cin + cg * 8;
   }
   __device__ __forceinline__ const void *base() const { return x; }
-  __device__ __forceinline__ uint4 chunk(int m, int kc) const {
-    const void *q = src(m, kc);
-    return q ? __ldg((const uint4 *)q) : zero4();
-  }
-  template <int ROWS>
-  __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
-    tc::fill_chunks<ROWS>(*this, s, row0, kc0, tid);
-  }
 };
 
 // Implicit im2col of the transposed convolution giving the input gradient:
@@ -156,14 +140,6 @@ struct ConvBwdDataLoader {
     return dy + ((((size_t)b * Do + oz) * Do + oy) * Do + ox) * cout + cg * 8;
   }
   __device__ __forceinline__ const void *base() const { return dy; }
-  __device__ __forceinline__ uint4 chunk(int m, int kc) const {
-    const void *q = src(m, kc);
-    return q ? __ldg((const uint4 *)q) : zero4();
-  }
-  template <int ROWS>
-  __device__ __forceinline__ void fill(uint8_t *s, int row0, int kc0, int tid) const {
-    tc::fill_chunks<ROWS>(*this, s, row0, kc0, tid);
-  }
 };
 
 // Weight gradient, operand A: rows = (tap, ci) (27 cin of them), K = output
