@@ -1005,7 +1005,8 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         m.close()
     seg, keep = 4096, 205
     same = cases = 0
-    ex_ms, pr_ms = [], []
+    ex_ms, pr_ms, e2e_ms = [], [], []
+    e2e_h2d = e2e_d2h = 0
     n_views = 0
     clocks = ClockSampler(local)
     clocks.start()
@@ -1016,7 +1017,7 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         ws = nbt.workspace(len(pt), cam, dev)
         P.exact_best(m, pt, seg, cam, prm, ws)
         P.pruned_best(net, m, pt, seg, keep, cam, prm)
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         e[0].record()
         bx, vx, _ = P.exact_best(m, pt, seg, cam, prm, ws)
         e[1].record()
@@ -1025,6 +1026,17 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         torch.cuda.synchronize(dev)
         ex_ms.append(e[0].elapsed_time(e[1]))
         pr_ms.append(e[1].elapsed_time(e[2]))
+        # end to end: candidate poses from pinned host memory, best indices back to the host
+        ph = torch.from_numpy(w.poses).pin_memory()
+        bh = torch.empty(bp.shape, dtype=bp.dtype).pin_memory()
+        e[3].record()
+        pt.copy_(ph, non_blocking=True)
+        be, _, _ = P.pruned_best(net, m, pt, seg, keep, cam, prm)
+        bh.copy_(be, non_blocking=True)
+        e[4].record()
+        e[4].synchronize()
+        e2e_ms.append(e[3].elapsed_time(e[4]))
+        e2e_h2d, e2e_d2h = ph.numel() * ph.element_size(), bh.numel() * bh.element_size()
         same += int((bx == bp).sum().item())
         cases += len(bx)
         n_views += len(pt)
@@ -1045,8 +1057,11 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         "speedup": ex_total / pr_total,
         "same_best_view": {"agree": same, "cases": cases, "rate": same / max(1, cases)},
         "train": {"seconds": train_s, "final_loss": losses[-1], "samples": 24 * 8 * 1024},
-        "e2e": None,
-        "gpu_launches": None,
+        "e2e": {"value": n_views / (float(sum(e2e_ms)) * 1e-3), "unit": "views/s", "h2d_bytes_per_step": e2e_h2d,
+                "d2h_bytes_per_step": e2e_d2h},
+        # per scene: 8 chunks x (crops, layers 0-1, layer 2, layer 3, features, fc1, fc2), then top-k,
+        # the exact walk of the kept views and its reduce, argmax
+        "gpu_launches": 60 * args.steps,
         "clocks": clk,
     }
     if rank == 0:
