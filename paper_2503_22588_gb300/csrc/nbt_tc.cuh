@@ -9,12 +9,17 @@
 //     a convolution) into shared memory in the canonical no-swizzle K-major
 //     layout, then one thread issues four tcgen05.mma (K = 16 each) and
 //     commits them to the stage's mbarrier; two stages alternate, so the
-//     gather of stage k+1 overlaps the MMAs of stage k;
+//     gather of stage k+1 overlaps the MMAs of stage k (gemm_kernel, for
+//     loaders that must transpose); loaders that can name a 16-byte source
+//     per chunk get four stages filled by cp.async (gemm_async_kernel);
 //   - the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 //     lanes 32w .. 32w+31 = rows of the tile) and hands each row's values
 //     to an epilogue functor.
 // Every mbarrier wait is bounded (%globaltimer); on timeout the kernel sets
 // an error word, waits once more (bounded) for its MMAs and frees its TMEM.
+// The helpers below (descriptors, MMAs with A in shared or tensor memory,
+// TMEM loads and stores, bounded waits) also serve the fused surrogate
+// kernels.
 //
 // Shared-memory layout of one operand stage (rows R = 128 for A, BN for B):
 // four K16 blocks of R x 16 BF16; inside a block, 8-row x 16-byte core
@@ -188,23 +193,11 @@ __device__ __forceinline__ uint32_t stage_off(int r, int kc, int rows) {
 __host__ __device__ constexpr size_t stage_bytes(int bn) { return (size_t)(kBM + bn) * kBK * 2; }
 __host__ __device__ constexpr size_t gemm_smem_bytes(int bn) { return 2 * stage_bytes(bn) + 1024; }
 
-// Default stage fill from a chunk loader: 16-byte chunk (row, kchunk) of
-// the operand -> its place in the stage.  Threads take consecutive rows of
-// one chunk column, so a warp's 512-byte store is bank-conflict free.
-template <int ROWS, class L>
-__device__ __forceinline__ void fill_chunks(const L &l, uint8_t *stage, int row0, int kc0, int tid) {
-  for (int c = tid; c < ROWS * 8; c += kThreads) {
-    const int r = c % ROWS, kc = c / ROWS;
-    *(uint4 *)(stage + stage_off(r, kc, ROWS)) = l.chunk(row0 + r, kc0 + kc);
-  }
-}
-
 // The GEMM kernel.  Grid: x over 128-row tiles of M, y over BN-column tiles
 // of N, z over splits of K (kt_split stages of 64 each).
 // LoadA / LoadB: `template <int ROWS> void fill(uint8_t *stage, int row0,
 // int kc0, int tid) const` writes rows row0 .. row0+ROWS-1, K chunks
-// kc0 .. kc0+7 (8 BF16 each, zero outside the operand) into the stage
-// (fill_chunks does it from a `uint4 chunk(int row, int kchunk)`).
+// kc0 .. kc0+7 (8 BF16 each, zero outside the operand) into the stage.
 // Epi: `void row(int m, int n, const float v[16], int z) const` receives
 // columns n .. n+15 of row m < M (columns past the real N are the loader's
 // zeros' products; the epilogue skips them).
