@@ -7,6 +7,7 @@ FP32 reference walk and along the exact FP64 walk.
 """
 
 import math
+import os
 
 import numpy as np
 import pytest
@@ -94,6 +95,50 @@ def test_trace_segments_bitexact(dims, brick):
         ref = oracle.trace(dims, o[k], d[k], "f32")
         assert cnt[k] == len(ref), k
         assert np.array_equal(idx[k, :cnt[k]], ref), k
+
+
+def test_largest_map_walks_bit_exact():
+    """The largest accepted map: 2048 x 2048 x 511 one-byte states, 2,143,289,344 voxels, just under
+    the 2^31-element limit, so linear voxel indices reach the top of the int32 range."""
+    dims = (2048, 2048, 511)
+    with pytest.raises(nbt.NbtError):
+        nbt.Map(2049, 4, 4, 0.01)                      # a side above 2048
+    with pytest.raises(nbt.NbtError):
+        nbt.Map(2048, 2048, 512, 0.01, brick=1)        # exactly 2^31 elements
+    with pytest.raises(nbt.NbtError):
+        nbt.Map(*dims, 0.01, brick=8)                  # 8^3 bricks pad it to 2^31 elements
+    grid = torch.zeros(dims[::-1], dtype=torch.uint8, device="cuda")   # all unknown
+    gm = nbt.Map.from_grid(grid, 0.01, (0.0, 0.0, 0.0), "u8", 1)
+    del grid
+    rng = np.random.default_rng(2048)
+    o, d = _segments(rng, dims, 300, max_len=3000.0)
+    eo = np.array([[0.5, 0.5, 0.5], [2047.5, 2047.5, 510.5], [2047.9, 0.1, 510.9]], np.float32)
+    ed = np.array([[2047.0, 2047.0, 510.0], [-2047.0, -2047.0, -510.0], [-2047.0, 2047.0, -510.0]], np.float32)
+    o = np.concatenate([o, eo])
+    d = np.concatenate([d, ed])
+    idx, cnt = nbt.trace_segments(gm, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+    idx = idx.cpu().numpy()
+    cnt = cnt.cpu().numpy()
+    assert idx.max() == 2048 * 2048 * 511 - 1                # the last voxel is reached
+    for k in range(len(o)):
+        ref = oracle.trace(dims, o[k], d[k], "f32")
+        assert cnt[k] == len(ref), k
+        assert np.array_equal(idx[k, :cnt[k]], ref), k
+    # whole perspectives: 48 views of 120 x 90 rays are more rays than two per resident thread, so
+    # they take the main tile kernel; on an all-unknown map the count IG of a view is its voxel steps
+    # (below 2^24 per view, so exact in FP32)
+    xy = [(1.0 + 3.0 * a, 1.0 + 0.75 * b) for a in range(2) for b in range(24)]
+    pose = np.array([[x, y, 0.3, 1.0, 0.0, 0.0, 0.0] if k % 2 == 0 else      # looking up the z axis
+                     [x + 12.0, y + 0.5, 4.8, 0.0, 1.0, 0.0, 0.0]              # from the top, looking down
+                     for k, (x, y) in enumerate(xy)], np.float32)
+    cam = configs.Camera(120, 90, max_range=30.0)
+    ig, st = views_gpu(gm, pose, gpu_camera(cam), nbt.ig_params("count"))
+    om = oracle.Map(np.zeros(dims[::-1], np.uint8), 0.01, (0.0, 0.0, 0.0))
+    ig_o, st_o = oracle.views_ig(om, pose, oracle_camera(cam), oracle.params("count"), "f32",
+                                 threads=os.cpu_count() or 1)
+    assert np.array_equal(st, st_o)
+    assert np.array_equal(ig, ig_o) and np.array_equal(ig, st.astype(np.float64))
+    assert st.min() > 100 * 120 * 90 and st.max() < 2 ** 24
 
 
 @pytest.mark.parametrize("encoding", ["u8", "u2"])
