@@ -1005,6 +1005,13 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         m.close()
     seg, keep = 4096, 205
     same = cases = 0
+    # pruning baselines at the same exact budget: random candidates, the untrained network, and
+    # Eq. 3's interpolation (a random half of the budget raycast, G(x) at the rest, its top half raycast)
+    base = {"random": 0, "untrained_network": 0, "idw_eq3": 0}
+    net0 = gs.Surrogate(max_batch=4096, params=gs.he_init(0))
+    k1 = keep // 2
+    k2 = keep - k1
+    idbuf = nbt.IdBuffer(n_b=1, max_views=k1)
     ex_ms, pr_ms, e2e_ms = [], [], []
     e2e_h2d = e2e_d2h = 0
     n_views = 0
@@ -1040,8 +1047,31 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         same += int((bx == bp).sum().item())
         cases += len(bx)
         n_views += len(pt)
+        nseg = len(pt) // seg
+        rs = torch.from_numpy(np.random.default_rng(4000 + es).random(len(pt), dtype=np.float32)).to(dev)
+        idx_r, kept_r = P.segment_topk(rs, seg, keep, pt)
+        ig_r, _ = nbt.views_ig(m, kept_r, cam, prm, want_steps=False)
+        b_r, _ = P.segment_argmax(ig_r, keep, idx_r.reshape(-1).contiguous())
+        base["random"] += int((bx == b_r).sum().item())
+        b_u, _, _ = P.pruned_best(net0, m, pt, seg, keep, cam, prm)
+        base["untrained_network"] += int((bx == b_u).sum().item())
+        idx_1, kept_1 = P.segment_topk(rs, seg, k1, pt)
+        ig_1, _ = nbt.views_ig(m, kept_1, cam, prm, want_steps=False)
+        g_all = torch.empty(len(pt), dtype=torch.float32, device=dev)
+        for s in range(nseg):
+            idbuf.push(kept_1[s * k1:(s + 1) * k1], ig_1[s * k1:(s + 1) * k1])
+            nbt.idw_gain(idbuf, pt[s * seg:(s + 1) * seg], 2.0, g_all[s * seg:(s + 1) * seg])
+        g_all.index_fill_(0, idx_1.reshape(-1).long(), float("-inf"))  # already raycast
+        idx_2, kept_2 = P.segment_topk(g_all, seg, k2, pt)
+        ig_2, _ = nbt.views_ig(m, kept_2, cam, prm, want_steps=False)
+        vals = torch.cat([ig_1.view(nseg, k1), ig_2.view(nseg, k2)], 1).reshape(-1).contiguous()
+        idxs = torch.cat([idx_1, idx_2], 1).reshape(-1).contiguous()
+        b_i, _ = P.segment_argmax(vals, keep, idxs)
+        base["idw_eq3"] += int((bx == b_i).sum().item())
         m.close()
     clk = clocks.stop()
+    idbuf.close()
+    net0.close()
     ex_total, pr_total = float(sum(ex_ms)), float(sum(pr_ms))
     line = {
         "metric": METRIC, "value": n_views / (pr_total * 1e-3), "unit": "views/s", "n_gpus": world,
@@ -1056,6 +1086,11 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         "pruned_views_per_s": n_views / (pr_total * 1e-3),
         "speedup": ex_total / pr_total,
         "same_best_view": {"agree": same, "cases": cases, "rate": same / max(1, cases)},
+        "pruning_baselines": {
+            "exact_views_per_poi": keep,
+            **{k: {"agree": v, "cases": cases, "rate": v / max(1, cases)} for k, v in base.items()},
+            "idw_eq3_scheme": f"{k1} random candidates per PoI raycast, G(x) of Eq. 3 (p = 2, one ID) at the "
+                              f"others, its top {k2} raycast; best of the {keep}"},
         "train": {"seconds": train_s, "final_loss": losses[-1], "samples": 24 * 8 * 1024},
         "e2e": {"value": n_views / (float(sum(e2e_ms)) * 1e-3), "unit": "views/s", "h2d_bytes_per_step": e2e_h2d,
                 "d2h_bytes_per_step": e2e_d2h},
