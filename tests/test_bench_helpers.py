@@ -1,5 +1,6 @@
 """Host-side logic of bench.py that the reported numbers depend on (no GPU)."""
 
+import argparse
 import json
 
 import pytest
@@ -44,3 +45,27 @@ def test_workload_descriptions_name_the_workload(name):
     w = W()
     w.name = name
     assert bench.describe(w).startswith(name)
+
+
+def test_every_workload_has_a_reference_arm():
+    from workload import configs
+    for name in bench.WORKLOAD_CHOICES:
+        if name == "idw_cost" or name in bench.REFERENCE_ARMS:
+            continue
+        assert bench.reference_views_workload(name) in configs.WORKLOADS, name
+
+
+@pytest.mark.parametrize("arm", ["insert", "fig3", "surrogate"])
+def test_reference_arm_lines(arm):
+    """The oracle arms of the non-view workloads print the native line's metric, unit and direction."""
+    args = argparse.Namespace(steps=1, warmup=0, gpus=1, workload=arm)
+    fn = bench.REFERENCE_ARMS[arm]
+    line = fn(args) if arm == "fig3" else fn(args, budget_s=0.01)
+    metric, unit, hib = {"insert": (bench.INSERT_METRIC, "points/s", True),
+                         "fig3": (bench.FIG3_METRIC, "ms", False),
+                         "surrogate": (bench.SURROGATE_METRIC, "views/s", True)}[arm]
+    assert line["impl"] == "reference" and line["metric"] == metric and line["unit"] == unit
+    assert line["higher_is_better"] is hib and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
+    json.dumps(line)
