@@ -147,7 +147,10 @@ int nbt_map_destroy(nbt_map map);
  * NBT_F32_PROB maps; bytes must equal that size.  src_on_device: 1 if src is
  * a device pointer, 0 for host memory (copied in slabs through a staging
  * buffer the map owns).  Asynchronous on `stream`; invalidates derived gain
- * tables.  Errors: NBT_EINVAL, NBT_ECUDA. */
+ * tables.  Host src: pageable memory has been read when the call returns;
+ * page-locked memory is read when the stream reaches the copy, so it must
+ * stay valid until then.  The staging buffer is shared by the map's uploads:
+ * issue uploads of one map on one stream.  Errors: NBT_EINVAL, NBT_ECUDA. */
 int nbt_map_upload(nbt_map map, const void *src, int64_t bytes, int32_t src_on_device, void *stream);
 
 /* Description and device bytes held by the map (either output may be NULL). */

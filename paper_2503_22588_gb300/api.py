@@ -90,7 +90,12 @@ class Map:
         return self._h.value
 
     def upload(self, grid, stream=None) -> None:
-        """nbt_map_upload from a CUDA tensor, a CPU tensor or a numpy array (dense, x fastest)."""
+        """nbt_map_upload from a CUDA tensor, a CPU tensor or a numpy array (dense, x fastest).
+
+        The copy is asynchronous on ``stream``: a pinned (page-locked) host grid is read when the
+        stream reaches the copy, so keep it alive until then; pageable memory is read before the
+        call returns.
+        """
         want = np.float32 if self.encoding == "f32" else np.uint8
         if isinstance(grid, torch.Tensor) and grid.is_cuda:
             tdt = torch.float32 if want == np.float32 else torch.uint8
