@@ -9,6 +9,7 @@ and which passage of the paper it follows.
 
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 
@@ -53,29 +54,45 @@ def lib():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             build()
-        L = C.CDLL(LIB_PATH)
-        P = C.POINTER
-        f32p, f64p, i64p, i32p = P(C.c_float), P(C.c_double), P(C.c_int64), P(C.c_int32)
-        L.orc_camera_consts.argtypes = [P(OrcCamera), P(OrcCamConsts)]
-        L.orc_view_rays.argtypes = [P(OrcMap), P(OrcCamera), f32p, f32p, f32p]
-        L.orc_trace.argtypes = [i32p, f32p, f32p, C.c_int, i64p, C.c_int64]
-        L.orc_trace.restype = C.c_int64
-        L.orc_trace_occluded.argtypes = [P(OrcMap), f32p, f32p, P(OrcParams), C.c_int, i64p, C.c_int64]
-        L.orc_trace_occluded.restype = C.c_int64
-        L.orc_segments_ig.argtypes = [P(OrcMap), f32p, f32p, C.c_int64, P(OrcParams), C.c_int, f64p, i64p]
-        L.orc_views_ig.argtypes = [P(OrcMap), f32p, C.c_int64, P(OrcCamera), P(OrcParams), C.c_int, C.c_int,
-                                   f64p, i64p]
-        L.orc_views_ig.restype = C.c_int
-        L.orc_traj_ig.argtypes = [P(OrcMap), f32p, i32p, C.c_int32, P(OrcCamera), P(OrcParams), C.c_int, C.c_int,
-                                  f64p, i64p]
-        L.orc_traj_ig.restype = C.c_int
-        L.orc_min_tie_gap.argtypes = [i32p, f32p, f32p]
-        L.orc_min_tie_gap.restype = C.c_double
-        L.orc_entropy.argtypes = [C.c_double]
-        L.orc_entropy.restype = C.c_double
-        L.orc_voxel_gain.argtypes = [P(OrcMap), C.c_int64, P(OrcParams), f64p, P(C.c_int)]
-        _lib = L
+        _lib = _bind(C.CDLL(LIB_PATH))
     return _lib
+
+
+@contextlib.contextmanager
+def using_library(path: str):
+    """Run the wrappers against another build of ``nbt_oracle.c`` (the tests' planted-mistake builds)."""
+    global _lib
+    saved = _lib
+    _lib = _bind(C.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def _bind(L):
+    """Argument and result types of the oracle's entry points."""
+    P = C.POINTER
+    f32p, f64p, i64p, i32p = P(C.c_float), P(C.c_double), P(C.c_int64), P(C.c_int32)
+    L.orc_camera_consts.argtypes = [P(OrcCamera), P(OrcCamConsts)]
+    L.orc_view_rays.argtypes = [P(OrcMap), P(OrcCamera), f32p, f32p, f32p]
+    L.orc_trace.argtypes = [i32p, f32p, f32p, C.c_int, i64p, C.c_int64]
+    L.orc_trace.restype = C.c_int64
+    L.orc_trace_occluded.argtypes = [P(OrcMap), f32p, f32p, P(OrcParams), C.c_int, i64p, C.c_int64]
+    L.orc_trace_occluded.restype = C.c_int64
+    L.orc_segments_ig.argtypes = [P(OrcMap), f32p, f32p, C.c_int64, P(OrcParams), C.c_int, f64p, i64p]
+    L.orc_views_ig.argtypes = [P(OrcMap), f32p, C.c_int64, P(OrcCamera), P(OrcParams), C.c_int, C.c_int,
+                               f64p, i64p]
+    L.orc_views_ig.restype = C.c_int
+    L.orc_traj_ig.argtypes = [P(OrcMap), f32p, i32p, C.c_int32, P(OrcCamera), P(OrcParams), C.c_int, C.c_int,
+                              f64p, i64p]
+    L.orc_traj_ig.restype = C.c_int
+    L.orc_min_tie_gap.argtypes = [i32p, f32p, f32p]
+    L.orc_min_tie_gap.restype = C.c_double
+    L.orc_entropy.argtypes = [C.c_double]
+    L.orc_entropy.restype = C.c_double
+    L.orc_voxel_gain.argtypes = [P(OrcMap), C.c_int64, P(OrcParams), f64p, P(C.c_int)]
+    return L
 
 
 def _ptr(a: np.ndarray, ctype):

@@ -68,6 +68,30 @@ def test_hand_cases_all_walks(orc):
             assert ig[0] == case["count_ig"] and st[0] == case["steps"], (case["name"], walk)
 
 
+def test_hand_tie_cases(orc):
+    """Segments exactly through voxel edges and corners: the definition (brute force) keeps the
+    voxels crossed over a positive length; the stepping walks take the tie-break x, then y, then z."""
+    for case in json.load(open(GOLDEN))["tie_cases"]:
+        dims = case["dims"]
+        o = np.array(case["o"], np.float32)
+        d = np.array(case["d"], np.float32)
+        assert list(orc.trace(dims, o, d, "brute")) == [lin(dims, v) for v in case["definition_sequence"]], \
+            case["name"]
+        for walk in ("f64", "f32"):
+            assert list(orc.trace(dims, o, d, walk)) == [lin(dims, v) for v in case["stepping_sequence"]], \
+                (case["name"], walk)
+
+
+def test_segments_start_at_the_camera_in_voxel_units(orc):
+    """A ray starts at the camera position p_P, in voxel units (p_P - origin) / s_Vox, and the central
+    ray of an identity pose runs d_Cam along +z.  Dyadic values make both exact in FP32."""
+    m = orc.Map(np.zeros((8, 8, 8), np.uint8), 0.25, (-1.0, 2.0, 0.5))
+    pose = np.array([0.0, 3.0, 1.5, 1.0, 0.0, 0.0, 0.0], np.float32)
+    o, d = orc.view_rays(m, orc.camera(3, 3, 1.0, 1.0, 0.5), pose)
+    assert np.array_equal(o, np.tile(np.float32([4.0, 4.0, 4.0]), (9, 1)))
+    assert np.array_equal(d[4], np.float32([0.0, 0.0, 2.0]))
+
+
 def test_hand_case_eq2(orc):
     spec = json.load(open(GOLDEN))["eq2_case"]
     dims = spec["dims"]
