@@ -56,6 +56,15 @@ def test_single_point_by_hand():
     assert np.all(g == 0.5)                                   # nothing else touched
 
 
+def test_single_point_by_hand_with_the_map_moved():
+    """The same scan with the map's origin, the sensor and the point all moved by (-4, 2, 0.5) m:
+    positions are taken relative to the origin, so the update is the same (dyadic values, exact in FP32)."""
+    shift = np.array([-4.0, 2.0, 0.5])
+    g = I.insert(UNKNOWN, [np.array([7.5, 1.5, 1.5]) + shift], tuple(np.array(SENSOR) + shift), 1.0,
+                 origin=tuple(shift))
+    assert np.array_equal(g, I.insert(UNKNOWN, [[7.5, 1.5, 1.5]], SENSOR, 1.0))
+
+
 def test_points_in_one_voxel_are_one_hit():
     g = I.insert(UNKNOWN, [[7.2, 1.5, 1.5], [7.8, 1.1, 1.9], [7.5, 1.5, 1.5]], SENSOR, 1.0)
     assert _row(g)[7] == f32(0.7)
