@@ -77,6 +77,10 @@ MUTANTS = [
      "return 1 if v > np.float32(occ_threshold) else (2 if v < np.float32(free_threshold) else 0)"),
     ("surrogate", "crop_codes_off_by_one", "oh.argmax(axis=-1) + 1", "oh.argmax(axis=-1)"),
     ("surrogate", "bf16_truncates", "u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16", "u = (u >> 16) << 16"),
+    ("surrogate", "crop_origin_not_subtracted", "o = [f32((f32(pose[a]) - f32(origin[a])) * inv_s) for a in range(3)]",
+     "o = [f32(f32(pose[a]) * inv_s) for a in range(3)]"),
+    ("surrogate", "pose_features_origin_not_subtracted", "feats[a] = f32(f32(f32(pose[a]) - f32(origin[a])) / ext)",
+     "feats[a] = f32(f32(pose[a]) / ext)"),
 ]
 
 

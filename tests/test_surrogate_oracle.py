@@ -125,14 +125,19 @@ def _sample_points(pose, cc, voxel_size):
     return (np.asarray(pose[:3], np.float64) + pc @ R.T) / voxel_size
 
 
-def test_frustum_crop_occupied_block():
+@pytest.mark.parametrize("shift", [(0.0, 0.0, 0.0), (0.25, -0.5, 0.125)])
+def test_frustum_crop_occupied_block(shift):
+    """The crop of a known block; with the map's origin and the camera moved by the same vector
+    (second case), positions are taken relative to the origin and nothing changes."""
     n = 8
     g = np.ones((40, 40, 40), np.uint8)           # all free
     g[21:24, 19:22, 24:27] = 2                    # occupied block x 24..26, y 19..21, z 21..23
     poi = np.array([25.5, 20.5, 22.5]) * 0.01
     pose = poses.look_at_poses(poi[None] + np.array([[0.06, -0.05, 0.04]]), poi)[0]
     cc = S.crop_consts(math.radians(60), math.radians(45), 0.2, crop=n)
-    crop, feats = S.frustum_crop(g, 0.01, (0, 0, 0), pose, cc)
+    moved = pose.copy()
+    moved[:3] = (pose[:3].astype(np.float64) + np.array(shift)).astype(moved.dtype)
+    crop, feats = S.frustum_crop(g, 0.01, shift, moved, cc)
     pts = _sample_points(pose, cc, 0.01)
     inside = np.all((pts >= 0) & (pts < 40), axis=-1)
     cell = np.floor(pts).astype(int)
