@@ -89,6 +89,15 @@ MUTANTS = [
     ("trajectory_drops_last_pose", "int orc_traj_ig(",
      "for (int32_t k = offsets[t]; k < offsets[t + 1]; ++k) {",
      "for (int32_t k = offsets[t]; k < offsets[t + 1] - 1; ++k) {"),
+    ("centre_grid_without_half_step", "void orc_camera_consts(",
+     "cc->x0 = (float)(-dh + dh / (double)w);", "cc->x0 = (float)(-dh);"),
+    ("spherical_length_without_z", "void orc_view_ray_f32(",
+     "float len = sqrtf((cx * cx + cy * cy) + cz * cz);", "float len = sqrtf(cx * cx + cy * cy);"),
+    ("steps_exclude_the_occluding_voxel", "static int visit_gain(",
+     "acc->steps += 1;", "acc->steps += occ ? 0 : 1;"),
+    ("thread_ranges_skip_a_view", "int orc_views_ig(",
+     "n_views * t / n_threads, n_views * (t + 1) / n_threads,",
+     "n_views * t / n_threads + (t > 0), n_views * (t + 1) / n_threads,"),
 ]
 
 
