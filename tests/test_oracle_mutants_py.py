@@ -12,7 +12,9 @@ unmodified copy must pass them all.
 
 import importlib.util
 import inspect
+import warnings
 
+import numpy as np
 import pytest
 
 import oracle
@@ -20,14 +22,18 @@ import test_endpoints_oracle
 import test_idw_oracle
 import test_insert_oracle
 import test_surrogate_oracle
+import test_workload
 from oracle import endpoints, idw, insert, surrogate
+from workload import poses
 
-# oracle module -> (its pin file, the name the pin file binds it to)
+# module -> (its pin file, the name the pin file binds it to); the perspective sampler of Eq. 1
+# and the look-at orientation are inputs, not oracle arithmetic, but Eq. 1 is the paper's
 TARGETS = {
     "idw": (idw, test_idw_oracle, "I"),
     "insert": (insert, test_insert_oracle, "I"),
     "endpoints": (endpoints, test_endpoints_oracle, "E"),
     "surrogate": (surrogate, test_surrogate_oracle, "S"),
+    "poses": (poses, test_workload, "poses"),
 }
 
 # (target, name, text, planted text): the first occurrence of text is replaced
@@ -81,16 +87,29 @@ MUTANTS = [
      "o = [f32(f32(pose[a]) * inv_s) for a in range(3)]"),
     ("surrogate", "pose_features_origin_not_subtracted", "feats[a] = f32(f32(f32(pose[a]) - f32(origin[a])) / ext)",
      "feats[a] = f32(f32(pose[a]) / ext)"),
+    ("poses", "eq1_square_root_radius", "np.cbrt(xr)", "np.sqrt(xr)"),
+    ("poses", "eq1_direction_not_normalised", "return r_s * np.cbrt(xr)[:, None] * x / norm",
+     "return r_s * np.cbrt(xr)[:, None] * x"),
+    ("poses", "golden_angle_wrong", "GOLDEN_ANGLE = math.pi * (3.0 - math.sqrt(5.0))",
+     "GOLDEN_ANGLE = math.pi * (3.0 + math.sqrt(5.0))"),
+    ("poses", "fibonacci_heights_not_centred", "z = 1.0 - (2.0 * k + 1.0) / n", "z = 1.0 - 2.0 * k / n"),
+    ("poses", "image_y_axis_up", "y = np.cross(z, x)", "y = np.cross(x, z)"),
+    ("poses", "optical_axis_away_from_poi", "z = poi[None, :] - pos", "z = pos - poi[None, :]"),
+    ("poses", "quaternion_conjugated", "q[k] = [0.25 * s, (m[2, 1] - m[1, 2]) / s, (m[0, 2] - m[2, 0]) / s, (m[1, 0] - m[0, 1]) / s]",
+     "q[k] = [0.25 * s, (m[1, 2] - m[2, 1]) / s, (m[2, 0] - m[0, 2]) / s, (m[0, 1] - m[1, 0]) / s]"),
+    ("poses", "vertical_axis_without_fallback_up", "up[vertical] = np.array([1.0, 0.0, 0.0])",
+     "up[vertical] = np.array([0.0, 0.0, 1.0])"),
 ]
 
 
 def load_copy(module, source: str, tmp_path):
-    """Load source as a module of the oracle package (relative imports resolve as in the original)."""
-    path = tmp_path / f"{module.__name__.rsplit('.', 1)[-1]}_copy.py"
+    """Load source as a module of the original's package (relative imports resolve as in the original)."""
+    package, name = module.__name__.rsplit(".", 1)
+    path = tmp_path / f"{name}_copy.py"
     path.write_text(source)
-    spec = importlib.util.spec_from_file_location(f"oracle.{path.stem}", str(path))
+    spec = importlib.util.spec_from_file_location(f"{package}.{path.stem}", str(path))
     mod = importlib.util.module_from_spec(spec)
-    mod.__package__ = "oracle"
+    mod.__package__ = package
     spec.loader.exec_module(mod)
     return mod
 
@@ -120,11 +139,13 @@ def pin_calls(pin_module):
 def first_failing_pin(target: str, copy, monkeypatch):
     _, pin_module, attr = TARGETS[target]
     monkeypatch.setattr(pin_module, attr, copy)
-    for name, fn, kw in pin_calls(pin_module):
-        try:
-            fn(**kw)
-        except Exception:
-            return name
+    with warnings.catch_warnings(), np.errstate(all="ignore"):
+        warnings.simplefilter("ignore")    # a planted mistake may divide by zero
+        for name, fn, kw in pin_calls(pin_module):
+            try:
+                fn(**kw)
+            except Exception:
+                return name
     return None
 
 

@@ -8,13 +8,20 @@ from workload import configs, poses, scenes, trajectories
 
 
 def test_fibonacci_sphere_closed_form():
+    """Centred Fibonacci lattice: heights 1 - (2k + 1)/n (symmetric about the equator), successive
+    azimuths one golden angle apart, 2 pi / phi^2 = 137.50776405... degrees."""
     n = 257
     p = poses.fibonacci_directions(n)
     assert np.allclose(np.linalg.norm(p, axis=1), 1.0, atol=1e-14)
     assert np.allclose(np.diff(p[:, 2]), -2.0 / n, atol=1e-14)
+    assert abs(p[0, 2] - (1.0 - 1.0 / n)) < 1e-14 and abs(p[-1, 2] + (1.0 - 1.0 / n)) < 1e-14
+    assert abs(p[:, 2].mean()) < 1e-14
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    golden = 2.0 * math.pi / phi ** 2
+    assert abs(math.degrees(golden) - 137.50776405003785) < 1e-9
     az = np.arctan2(p[:, 1], p[:, 0])
     dphi = np.mod(np.diff(az), 2 * math.pi)
-    assert np.allclose(dphi, poses.GOLDEN_ANGLE % (2 * math.pi), atol=1e-12)
+    assert np.allclose(dphi, golden, atol=1e-12)
 
 
 def test_eq1_uniform_in_ball():
