@@ -1070,8 +1070,8 @@ def run_surrogate(args, nbt, torch, dev, stream, world, rank, local, dist) -> No
                      "algorithmic": f"{fl} FLOP per view x {n} views", "peak_kind": "measured (bf16_tflops, burst)"},
         "e2e": {"value": job_throughput(n * args.steps, world, e2e_total), "unit": "views/s",
                 "h2d_bytes_per_step": int(pz_host.numel() * 4), "d2h_bytes_per_step": int(sc_host.numel() * 4)},
-        # per batch: crops, layer-0 lookup, three convolution GEMMs, features, fc1 GEMM, fc2
-        "gpu_launches": 8 * n_b * args.steps,
+        # per batch: crops, fused layers 0-1, layer 2, layer 3, features, fc1 GEMM, fc2
+        "gpu_launches": 7 * n_b * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
