@@ -946,7 +946,8 @@ def run_insert(args, nbt, torch, dev, stream, world, rank, local, dist) -> None:
                                     "cleared per scan", "peak_kind": f"{peak_kind} (hbm_gbs)"},
         "e2e": {"value": job_throughput(points, world, e2e_total), "unit": "points/s",
                 "h2d_bytes_per_step": int(np.mean([p.numel() * 4 for p in host_pts])), "d2h_bytes_per_step": 24},
-        "gpu_launches": 6 * args.steps,
+        # per scan: points, enumerate, free rays, apply, stats
+        "gpu_launches": 5 * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
