@@ -549,7 +549,8 @@ def main() -> None:
                 "h2d_bytes_per_step": int(grid_host.numel() * grid_host.element_size()
                                           + poses_host.numel() * 4),
                 "d2h_bytes_per_step": int(ig_host.numel() * 4)},
-        "gpu_launches": 4 * args.steps,
+        # per step: upload (scatter / pack), gain derivation (probability maps only), tile kernel, reduce
+        "gpu_launches": (4 if w.encoding == "f32" else 3) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
