@@ -16,7 +16,7 @@ import oracle
 import test_oracle_pins as pins
 from oracle.build import SRC, compile_source
 
-PINS = ([("test_hand_cases_all_walks", {}), ("test_hand_tie_cases", {}),
+PINS = ([("test_hand_cases_all_walks", {}), ("test_hand_tie_cases", {}), ("test_tie_gap_by_hand", {}),
          ("test_segments_start_at_the_camera_in_voxel_units", {}), ("test_hand_case_eq2", {})]
         + [("test_walks_match_brute_force", {"dims": d}) for d in [(7, 5, 9), (16, 16, 16), (1, 12, 3)]]
         + [("test_f32_walk_differs_from_f64_only_at_ties", {}), ("test_walk_is_a_connected_monotone_path", {}),
@@ -95,6 +95,9 @@ MUTANTS = [
      "float len = sqrtf((cx * cx + cy * cy) + cz * cz);", "float len = sqrtf(cx * cx + cy * cy);"),
     ("steps_exclude_the_occluding_voxel", "static int visit_gain(",
      "acc->steps += 1;", "acc->steps += occ ? 0 : 1;"),
+    ("tie_gap_always_zero", "double orc_min_tie_gap(", "  free(c);\n  return best;", "  free(c);\n  return 0.0;"),
+    ("tie_gap_never_reports_ties", "double orc_min_tie_gap(", "  free(c);\n  return best;",
+     "  free(c);\n  return INFINITY;"),
     ("thread_ranges_skip_a_view", "int orc_views_ig(",
      "n_views * t / n_threads, n_views * (t + 1) / n_threads,",
      "n_views * t / n_threads + (t > 0), n_views * (t + 1) / n_threads,"),

@@ -82,6 +82,20 @@ def test_hand_tie_cases(orc):
                 (case["name"], walk)
 
 
+def test_tie_gap_by_hand(orc):
+    """The smallest parameter gap between crossings of different axes (or a crossing and a clip
+    end): zero for segments through an edge or corner; 8/15 - 1/2 = 1/30 for the worked diagonal
+    (x crossings at 1/6, 1/2, 5/6, the y crossing at 8/15, ends at 0 and 1)."""
+    spec = json.load(open(GOLDEN))
+    for case in spec["tie_cases"]:
+        o = np.array(case["o"], np.float32)
+        d = np.array(case["d"], np.float32)
+        assert orc.min_tie_gap(case["dims"], o, d) == 0.0, case["name"]
+    case = next(c for c in spec["cases"] if c["name"] == "diagonal_in_plane_hits_wall")
+    gap = orc.min_tie_gap(case["dims"], np.array(case["o"], np.float32), np.array(case["d"], np.float32))
+    assert abs(gap - 1.0 / 30.0) < 1e-7, gap
+
+
 def test_segments_start_at_the_camera_in_voxel_units(orc):
     """A ray starts at the camera position p_P, in voxel units (p_P - origin) / s_Vox, and the central
     ray of an identity pose runs d_Cam along +z.  Dyadic values make both exact in FP32."""
