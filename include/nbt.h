@@ -283,8 +283,8 @@ int nbt_view_segments(nbt_map map, const nbt_pose *poses, int64_t n_views, const
  * nbt_plan_create_traj captures one nbt_traj_ig call with exactly these
  * arguments (work-queue reset, the persistent tile kernel, the per-
  * trajectory reduction) into a CUDA graph; nbt_plan_launch replays it on
- * `stream`.  The graph keeps the pointers: every buffer passed here must
- * stay allocated until nbt_plan_destroy, and the caller may change the
+ * `stream`.  The graph keeps the pointers: the map and every buffer passed
+ * here must stay alive until nbt_plan_destroy, and the caller may change the
  * contents of poses, offsets and the map between launches (not n_poses,
  * n_traj, the camera or the params).  A probability map's derived gains
  * are refreshed outside the graph when the map was re-uploaded.  Creating

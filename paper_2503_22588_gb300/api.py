@@ -273,6 +273,8 @@ class TrajPlan:
         self._h = h
 
     def launch(self, stream=None) -> torch.Tensor:
+        if self.map._h is None:
+            raise ValueError("the plan's map is closed")
         check(lib().nbt_plan_launch(self._h, _stream(stream)), "nbt_plan_launch")
         return self.out
 
