@@ -24,7 +24,7 @@ import test_insert_oracle
 import test_surrogate_oracle
 import test_workload
 from oracle import endpoints, idw, insert, surrogate
-from workload import poses
+from workload import poses, scenes
 
 # module -> (its pin file, the name the pin file binds it to); the perspective sampler of Eq. 1
 # and the look-at orientation are inputs, not oracle arithmetic, but Eq. 1 is the paper's
@@ -34,6 +34,7 @@ TARGETS = {
     "endpoints": (endpoints, test_endpoints_oracle, "E"),
     "surrogate": (surrogate, test_surrogate_oracle, "S"),
     "poses": (poses, test_workload, "poses"),
+    "scenes": (scenes, test_workload, "scenes"),
 }
 
 # (target, name, text, planted text): the first occurrence of text is replaced
@@ -99,6 +100,15 @@ MUTANTS = [
      "q[k] = [0.25 * s, (m[1, 2] - m[2, 1]) / s, (m[2, 0] - m[0, 2]) / s, (m[0, 1] - m[1, 0]) / s]"),
     ("poses", "vertical_axis_without_fallback_up", "up[vertical] = np.array([1.0, 0.0, 0.0])",
      "up[vertical] = np.array([0.0, 0.0, 1.0])"),
+    ("scenes", "free_and_occupied_beta_swapped", "p[free] = rng.beta(2.0, 8.0, size=int(free.sum()))",
+     "p[free] = rng.beta(8.0, 2.0, size=int(free.sum()))"),
+    ("scenes", "free_beta_too_narrow", "p[free] = rng.beta(2.0, 8.0, size=int(free.sum()))",
+     "p[free] = rng.beta(4.0, 16.0, size=int(free.sum()))"),
+    ("scenes", "unknown_probability_not_half", "p[unknown] = 0.5", "p[unknown] = 0.45"),
+    ("scenes", "occupied_overrides_unknown", "    st[unknown] = UNKNOWN\n",
+     "    st[unknown & ~occupied] = UNKNOWN\n"),
+    ("scenes", "unknown_half_on_the_wrong_side", "unk[:, :, n // 2:] = True", "unk[:, :, :n // 2] = True"),
+    ("scenes", "box_fill_by_voxel_corners", "a = max(0, math.ceil(lo - 0.5))", "a = max(0, math.floor(lo))"),
 ]
 
 

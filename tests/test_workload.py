@@ -77,6 +77,24 @@ def test_scene_generators_are_seeded_and_shaped():
     assert abs((r == 0).mean() - 0.4) < 0.08
 
 
+def test_probability_recipe():
+    """Unknown voxels hold P = 0.5 exactly (overriding occupied), free P ~ Beta(2, 8) (mean 0.2,
+    variance 16/1100) and occupied P ~ Beta(8, 2) (mean 0.8, same variance)."""
+    occ = np.zeros((40, 40, 40), bool)
+    occ[:, :, :12] = True
+    unk = np.zeros_like(occ)
+    unk[:, :, 30:] = True
+    unk[:, :, 8:12] = True                       # overlaps the occupied slab
+    p = scenes.probabilities_from_masks(occ, unk, seed=0).astype(np.float64)
+    free = ~occ & ~unk
+    occ_only = occ & ~unk
+    assert np.all(p[unk] == 0.5)
+    assert abs(p[free].mean() - 0.2) < 0.005 and abs(p[free].var() - 16 / 1100) < 1e-3
+    assert abs(p[occ_only].mean() - 0.8) < 0.005 and abs(p[occ_only].var() - 16 / 1100) < 1e-3
+    st = scenes.states_from_masks(occ, unk)
+    assert np.all(st[unk] == 0) and np.all(st[occ_only] == 2) and np.all(st[free] == 1)
+
+
 def test_box_fill_uses_voxel_centres():
     m = np.zeros((8, 8, 8), bool)
     scenes.fill_box(m, (1.4, 2.6, 0.0), (3.5, 4.4, 1.0))
