@@ -24,7 +24,7 @@ import test_insert_oracle
 import test_surrogate_oracle
 import test_workload
 from oracle import endpoints, idw, insert, surrogate
-from workload import poses, scenes
+from workload import poses, scenes, trajectories
 
 # module -> (its pin file, the name the pin file binds it to); the perspective sampler of Eq. 1
 # and the look-at orientation are inputs, not oracle arithmetic, but Eq. 1 is the paper's
@@ -35,6 +35,7 @@ TARGETS = {
     "surrogate": (surrogate, test_surrogate_oracle, "S"),
     "poses": (poses, test_workload, "poses"),
     "scenes": (scenes, test_workload, "scenes"),
+    "trajectories": (trajectories, test_workload, "trajectories"),
 }
 
 # (target, name, text, planted text): the first occurrence of text is replaced
@@ -109,6 +110,15 @@ MUTANTS = [
      "    st[unknown & ~occupied] = UNKNOWN\n"),
     ("scenes", "unknown_half_on_the_wrong_side", "unk[:, :, n // 2:] = True", "unk[:, :, :n // 2] = True"),
     ("scenes", "box_fill_by_voxel_corners", "a = max(0, math.ceil(lo - 0.5))", "a = max(0, math.floor(lo))"),
+    ("trajectories", "spline_coefficient_error", "(2.0 * p0 - 5.0 * p1 + 4.0 * p2 - p3) * t * t\n",
+     "(2.0 * p0 - 4.0 * p1 + 4.0 * p2 - p3) * t * t\n"),
+    ("trajectories", "spline_tangent_halved", "return 0.5 * ((2.0 * p1) + (-p0 + p2) * t",
+     "return 0.5 * ((2.0 * p1) + 0.5 * (-p0 + p2) * t"),
+    ("trajectories", "jitter_in_degrees_as_radians", "ang = math.radians(jitter_deg) * rng.random()",
+     "ang = jitter_deg * rng.random()"),
+    ("trajectories", "horizon_tilt_not_skew_symmetric",
+     "K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = axis[:, 2], -axis[:, 1], axis[:, 0]",
+     "K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = -axis[:, 2], axis[:, 1], -axis[:, 0]"),
 ]
 
 

@@ -114,6 +114,40 @@ def test_trajectories_csr():
     assert np.all(d > 0.3 - 1e-6) and np.all(d < 0.8 + 1e-6)
 
 
+def test_catmull_rom_interpolates_its_inner_control_points():
+    """A Catmull-Rom segment runs from p1 (t = 0) to p2 (t = 1) with tangents (p2 - p0)/2 and (p3 - p1)/2."""
+    rng = np.random.default_rng(1)
+    p0, p1, p2, p3 = rng.standard_normal((4, 3))
+    t = np.array([0.0, 1.0, 1e-6, 1.0 - 1e-6])
+    c = trajectories._catmull_rom(p0, p1, p2, p3, t)
+    assert np.allclose(c[0], p1, atol=1e-14) and np.allclose(c[1], p2, atol=1e-14)
+    assert np.allclose((c[2] - c[0]) / 1e-6, (p2 - p0) / 2, atol=1e-5)
+    assert np.allclose((c[1] - c[3]) / 1e-6, (p3 - p1) / 2, atol=1e-5)
+    b = trajectories._catmull_rom_batch(p0[None, None], p1[None, None], p2[None, None], p3[None, None],
+                                        t[None, :, None])
+    assert np.allclose(b[0], c, atol=1e-14)
+
+
+def _axis_angles_deg(p, pois):
+    """Angle between each pose's optical axis (R e_z) and the direction to its nearest PoI."""
+    w, x, y, z = (p[:, 3 + k].astype(np.float64) for k in range(4))
+    axis = np.stack([2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)], axis=1)
+    pos = p[:, :3].astype(np.float64)
+    poi = pois[np.argmin(np.linalg.norm(pos[:, None] - pois[None], axis=2), axis=1)]
+    to = (poi - pos) / np.linalg.norm(poi - pos, axis=1, keepdims=True)
+    return np.degrees(np.arccos(np.clip(np.sum(axis * to, axis=1), -1.0, 1.0)))
+
+
+def test_trajectory_orientations_look_at_the_poi_within_the_jitter():
+    pois = np.array([[1.0, 1.0, 1.0]])
+    p, _ = trajectories.random_trajectories(pois, 30, seed=2, jitter_deg=3.0)
+    a = _axis_angles_deg(p, pois)
+    assert a.max() <= 3.0 + 1e-3 and a.max() > 1.0
+    q, _ = trajectories.horizon_trajectories(pois[0], 50, 11, seed=3, jitter_deg=10.0)
+    b = _axis_angles_deg(q, pois)
+    assert b.max() <= 10.0 + 1e-3 and b.max() > 5.0
+
+
 def test_workload_presets_small():
     w = configs.exact64()
     assert w.grid.shape == (64, 64, 64) and w.poses.shape == (64, 7) and w.rays_per_pose == 3072
