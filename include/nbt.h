@@ -18,12 +18,16 @@
  *   - "device" pointers are CUDA global-memory pointers on the device the
  *     map was created on, which must be the current device of the calling
  *     thread.  The caller owns every pointer it passes; the library keeps
- *     none beyond the call, except what a map handle owns.
+ *     none beyond the call, except what a handle owns (maps, ID buffers,
+ *     surrogates) and the buffers a trajectory plan captures.
  *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *     stream) and is asynchronous: results are valid once the stream has
- *     reached the call.  No call synchronises the device, except
- *     nbt_map_upload from pageable host memory (CUDA copies pageable memory
- *     synchronously).
+ *     reached the call.  Calls do not synchronise, except where a
+ *     function's comment says so: uploads from pageable host memory (CUDA
+ *     copies pageable memory synchronously), destroying a map, ID buffer or
+ *     surrogate (so no enqueued call still reads it), creating a
+ *     trajectory plan, reading the tensor-core error word and copying
+ *     surrogate parameters to or from the host.
  *   - A map handle may be used from several host threads; calls that read
  *     it may overlap on different streams, but an upload must not overlap
  *     with calls that read the same map.
