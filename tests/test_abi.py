@@ -105,3 +105,18 @@ def test_grid_scale_camera_matches_the_oracle(libnbt):
                 (1.0, 1.0, float("nan"), 0.01, 5.0), (3.0, 1.0, 100.0, 0.0001, 0.01)):
         with _pt.raises(NbtError):
             libnbt.camera_from_grid_scale(*bad)
+
+
+def test_surrogate_parameter_layout_matches_the_oracle_network(libnbt):
+    """The library's parameter count, and the binding's layout of them (the order
+    nbt_surrogate_set_params documents), equal the oracle network's shapes."""
+    import numpy as np
+
+    from oracle import surrogate as S
+    from paper_2503_22588_gb300 import surrogate as gs
+    p = S.init_params(0)
+    assert gs.param_count() == sum(v.size for v in p.values())
+    assert [k for k, _ in gs.SHAPES] == list(p.keys())
+    assert all(tuple(p[k].shape) == tuple(shp) for k, shp in gs.SHAPES)
+    back = gs.unpack(gs.pack(p))
+    assert all(np.array_equal(back[k], p[k]) for k in p)
