@@ -120,3 +120,33 @@ def test_surrogate_parameter_layout_matches_the_oracle_network(libnbt):
     assert all(tuple(p[k].shape) == tuple(shp) for k, shp in gs.SHAPES)
     back = gs.unpack(gs.pack(p))
     assert all(np.array_equal(back[k], p[k]) for k in p)
+
+
+def test_map_create_rejects_bad_descriptions_before_any_cuda_call(libnbt):
+    """Map descriptions are validated on the host first, so these fail with NBT_EINVAL (-1) on a
+    machine without a GPU as well: sides outside [1, 2048], 2^31 or more voxels, a brick other than
+    1, 4 or 8, a non-positive or non-finite voxel size, a non-finite origin, an unknown encoding."""
+    from paper_2503_22588_gb300 import _lib
+    L = _lib.lib()
+
+    def create(nx=8, ny=8, nz=8, voxel=0.01, origin=(0.0, 0.0, 0.0), enc=0, brick=1):
+        d = _lib.MapDesc(nx, ny, nz, voxel, (C.c_float * 3)(*origin), enc, brick)
+        h = C.c_void_p()
+        rc = L.nbt_map_create(C.byref(d), C.byref(h))
+        assert h.value is None
+        return rc
+
+    bad = [dict(nx=0), dict(ny=-3), dict(nz=2049), dict(nx=2048, ny=2048, nz=512), dict(brick=5),
+           dict(brick=2), dict(voxel=0.0), dict(voxel=-0.01), dict(voxel=float("nan")), dict(voxel=float("inf")),
+           dict(origin=(0.0, float("nan"), 0.0)), dict(origin=(float("inf"), 0.0, 0.0)), dict(enc=3), dict(enc=-1)]
+    for kw in bad:
+        assert create(**kw) == -1, kw
+
+
+def test_surrogate_create_rejects_batch_sizes_outside_1_to_4096(libnbt):
+    from paper_2503_22588_gb300 import _lib
+    L = _lib.lib()
+    h = C.c_void_p()
+    for mb in (0, -1, 4097):
+        assert L.nbt_surrogate_create(mb, C.byref(h)) == -1 and h.value is None
+    assert L.nbt_surrogate_create(16, None) == -1
