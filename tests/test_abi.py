@@ -150,3 +150,34 @@ def test_surrogate_create_rejects_batch_sizes_outside_1_to_4096(libnbt):
     for mb in (0, -1, 4097):
         assert L.nbt_surrogate_create(mb, C.byref(h)) == -1 and h.value is None
     assert L.nbt_surrogate_create(16, None) == -1
+
+
+def test_null_handles_are_rejected_on_the_host(libnbt):
+    """Every entry point that takes a map, plan, surrogate or ID-buffer handle answers NBT_EINVAL to a
+    NULL handle without touching the GPU; destroying NULL is a no-op (NBT_OK)."""
+    from paper_2503_22588_gb300 import _lib
+    L = _lib.lib()
+    cam = libnbt.camera(8, 8, 1.0, 0.8, 1.0)
+    prm = libnbt.ig_params("count")
+    calls = {
+        "nbt_map_upload": (None, None, 0, 0, None),
+        "nbt_map_info": (None, None, None),
+        "nbt_map_download": (None, None, 0, None),
+        "nbt_views_ig": (None, None, 1, C.byref(cam), C.byref(prm), None, None, None, 0, None),
+        "nbt_views_ig_noalloc": (None, None, 1, C.byref(cam), C.byref(prm), None, None, None),
+        "nbt_traj_ig": (None, None, 1, None, 1, C.byref(cam), C.byref(prm), None, None, None, 0, None),
+        "nbt_trace_segments": (None, None, None, 1, None, None, 0, None, None),
+        "nbt_view_segments": (None, None, 1, C.byref(cam), None, None, None),
+        "nbt_plan_launch": (None, None),
+        "nbt_map_set_tuning": (None, None),
+        "nbt_map_get_tuning": (None, None),
+        "nbt_surrogate_set_params": (None, None, 0),
+        "nbt_surrogate_get_params": (None, None, 0),
+        "nbt_surrogate_forward": (None, None, None, 1, None, None),
+        "nbt_id_buffer_push": (None, None, None, 1, None),
+        "nbt_id_buffer_count": (None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == -1, name
+    for name in ("nbt_map_destroy", "nbt_plan_destroy", "nbt_surrogate_destroy", "nbt_id_buffer_destroy"):
+        assert getattr(L, name)(None) == 0, name
