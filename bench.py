@@ -395,16 +395,29 @@ def run_reference(args) -> None:
 WORKLOAD_CHOICES = ["prob256", "exact64", "room512", "traj256", "room512-pruned", "idw_cost", "fig3", "insert",
                     "surrogate"]
 
+# (steps, warm-up steps) when not given: each workload's timed work ends within a minute or so
+DEFAULT_STEPS = {"prob256": (1000, 20), "exact64": (1000, 20), "traj256": (200, 5), "room512": (20, 3),
+                 "room512-pruned": (5, 3), "idw_cost": (200, 5), "fig3": (20, 3), "insert": (200, 5),
+                 "surrogate": (100, 5)}
 
-def main() -> None:
+
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: per workload)")
+    ap.add_argument("--warmup", type=int, default=None, help="untimed warm-up steps (default: per workload)")
     ap.add_argument("--workload", default="prob256", choices=WORKLOAD_CHOICES)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
+    steps, warmup = DEFAULT_STEPS[args.workload]
+    args.steps = steps if args.steps is None else args.steps
+    args.warmup = max(3, warmup if args.warmup is None else args.warmup)  # at least three untimed steps
+    return args
+
+
+def main() -> None:
+    args = parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
@@ -1140,8 +1153,9 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         m = nbt.Map.from_grid(torch.from_numpy(w.grid).to(dev), w.voxel_size, w.origin, "u2")
         pt = torch.from_numpy(w.poses).to(dev)
         ws = nbt.workspace(len(pt), cam, dev)
-        P.exact_best(m, pt, seg, cam, prm, ws)
-        P.pruned_best(net, m, pt, seg, keep, cam, prm)
+        for _ in range(max(args.warmup, 3)):    # untimed passes of both selections on this scene
+            P.exact_best(m, pt, seg, cam, prm, ws)
+            P.pruned_best(net, m, pt, seg, keep, cam, prm)
         e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         e[0].record()
         bx, vx, _ = P.exact_best(m, pt, seg, cam, prm, ws)
@@ -1193,7 +1207,8 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
     ex_total, pr_total = float(sum(ex_ms)), float(sum(pr_ms))
     line = {
         "metric": METRIC, "value": n_views / (pr_total * 1e-3), "unit": "views/s", "n_gpus": world,
-        "steps": args.steps, "warmup": 1, "ms_per_step": pr_total / args.steps, "higher_is_better": True,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": pr_total / args.steps,
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 surrogate + u2 exact", "data": "synthetic",
         "config": {"workload": "room512-pruned: per scene 8 PoIs x 4096 candidate views of 320x240 rays on a "
                                "512^3 2-bit room; best view per PoI by exact raycasting of all candidates vs of "

@@ -69,3 +69,15 @@ def test_reference_arm_lines(arm):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
     json.dumps(line)
+
+
+def test_step_defaults_per_workload_and_explicit_flags_win():
+    a = bench.parse_args([])
+    assert (a.workload, a.steps, a.warmup, a.gpus, a.impl) == ("prob256", 1000, 20, 1, "native")
+    assert set(bench.DEFAULT_STEPS) == set(bench.WORKLOAD_CHOICES)
+    assert all(w >= 3 for _, w in bench.DEFAULT_STEPS.values())
+    b = bench.parse_args(["--workload", "room512"])
+    assert (b.steps, b.warmup) == (20, 3)
+    c = bench.parse_args(["--workload", "room512", "--steps", "7", "--warmup", "4"])
+    assert (c.steps, c.warmup) == (7, 4)
+    assert bench.parse_args(["--warmup", "1"]).warmup == 3        # never fewer than three warm-up steps
