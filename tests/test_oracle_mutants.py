@@ -26,7 +26,8 @@ PINS = ([("test_hand_cases_all_walks", {}), ("test_hand_tie_cases", {}), ("test_
         + [("test_occlusion_wall_closed_form", {}), ("test_ray_stops_at_first_occupied", {})]
         + [("test_revealing_voxels_never_increases_ig", {"metric": m}) for m in ("count", "eq2", "entropy")]
         + [("test_view_ig_is_permutation_invariant_sum_of_rays", {}), ("test_traj_ig_is_sum_over_csr_ranges", {}),
-           ("test_threads_do_not_change_results", {}), ("test_entropy_values", {}), ("test_gain_table", {})]
+           ("test_threads_do_not_change_results", {}), ("test_entropy_values", {}), ("test_gain_table", {}),
+           ("test_long_sums_are_accumulated_in_fp64", {})]
         + [("test_endpoint_grid_geometry", {"grid_mode": g, "range_mode": r})
            for g in ("corners", "centers") for r in ("planar", "spherical")]
         + [("test_perspectives_nearer_the_poi_gain_less", {})])
@@ -98,6 +99,8 @@ MUTANTS = [
     ("tie_gap_always_zero", "double orc_min_tie_gap(", "  free(c);\n  return best;", "  free(c);\n  return 0.0;"),
     ("tie_gap_never_reports_ties", "double orc_min_tie_gap(", "  free(c);\n  return best;",
      "  free(c);\n  return INFINITY;"),
+    ("ray_sum_in_fp32", "/* Gain g(v) of one voxel", "  double ig;", "  float ig;"),
+    ("view_sum_in_fp32", "static void view_ig(", "double sum = 0.0;", "float sum = 0.0f;"),
     ("thread_ranges_skip_a_view", "int orc_views_ig(",
      "n_views * t / n_threads, n_views * (t + 1) / n_threads,",
      "n_views * t / n_threads + (t > 0), n_views * (t + 1) / n_threads,"),

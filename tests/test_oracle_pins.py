@@ -348,6 +348,18 @@ def test_threads_do_not_change_results(orc):
 # Gains (Eq. 2 and the entropy / count variants)
 # --------------------------------------------------------------------------
 
+def test_long_sums_are_accumulated_in_fp64(orc):
+    """Every voxel at P = 0.3 (unknown: not above 0.7, not below 0.3) gains H(0.3) and none occludes,
+    so a perspective's entropy IG is its voxel steps x H(0.3) -- to FP64 precision, over ~10^5 terms."""
+    p = float(np.float32(0.3))                          # the map stores P in FP32
+    h = -p * math.log2(p) - (1.0 - p) * math.log2(1.0 - p)
+    m = orc.Map(np.full((48, 48, 48), 0.3, np.float32), 0.01)
+    pose = wposes.look_at_poses(np.array([[0.24, 0.24, 0.01]]), np.array([0.24, 0.24, 0.24]))
+    ig, st = orc.views_ig(m, pose, orc.camera(40, 30, 1.0, 0.8, 0.5), orc.params("entropy"), "f32")
+    assert st[0] > 50_000
+    assert abs(ig[0] - st[0] * h) <= 1e-11 * st[0] * h, (ig[0], st[0] * h)
+
+
 def test_entropy_values(orc):
     assert orc.entropy(0.5) == 1.0
     assert orc.entropy(0.0) == 0.0 and orc.entropy(1.0) == 0.0
