@@ -1,11 +1,15 @@
 """Benchmark of the IG raycasting hot path on one or more GPUs.
 
-One step = one pass of the path over one batch of synthetic input: upload
-the step's dense occupancy grid (already resident in HBM) into the bricked
-map, derive the per-voxel gains, cast every ray of every perspective and
-reduce to per-perspective IG (paper Section III).  Default workload
-``prob256``: 256^3 FP32 tabletop of 200 primitives, 1024 perspectives on a
-0.3-0.8 m Fibonacci shell, 160 x 120 rays each, entropy IG until p > 0.7.
+Default workload ``room512-pruned`` (the headline: exact vs surrogate-pruned
+next-best-view selection, same best view): per step one seeded 512^3 2-bit
+room of 2000 primitives (40 % unknown) with 8 PoIs x 4096 candidate views of
+320 x 240 rays.  The pruned arm uploads the map and runs nbt_plan_pruned
+(surrogate scores of every candidate, the top 5 % per PoI raycast exactly,
+the best of them); the exact arm raycasts every candidate (paper Section
+III IG: unknown voxels along each ray up to the first occupied one).  The
+surrogate is trained inside the run, before timing.  Other workloads
+(``--workload``): prob256, exact64, traj256, room512, surrogate, idw_cost,
+fig3, insert -- each step one pass of its path over one batch of input.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
        [--impl reference]
@@ -382,8 +386,8 @@ def run_reference(args) -> None:
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": describe(w) + (" (exact scoring of the candidates room512-pruned selects among)"
-                                                  if args.workload == "room512-pruned" else ""),
+            "config": {"workload": (pruned_describe() + " (reference: the oracle's exact scoring of the candidates)"
+                                    if args.workload == "room512-pruned" else describe(w)),
                        "views_per_step": n, "parallelism": "host threads"},
             "voxel_steps_per_s": steps / total,
             "cpu_baseline": {"value": value, "unit": "views/s", "cores": threads, "kind": "oracle",
@@ -397,7 +401,7 @@ WORKLOAD_CHOICES = ["prob256", "exact64", "room512", "traj256", "room512-pruned"
 
 # (steps, warm-up steps) when not given: each workload's timed work ends within a minute or so
 DEFAULT_STEPS = {"prob256": (1000, 20), "exact64": (1000, 20), "traj256": (200, 5), "room512": (20, 3),
-                 "room512-pruned": (5, 3), "idw_cost": (200, 5), "fig3": (20, 3), "insert": (200, 5),
+                 "room512-pruned": (25, 3), "idw_cost": (200, 5), "fig3": (20, 3), "insert": (200, 5),
                  "surrogate": (100, 5)}
 
 
@@ -406,7 +410,7 @@ def parse_args(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default: per workload)")
     ap.add_argument("--warmup", type=int, default=None, help="untimed warm-up steps (default: per workload)")
-    ap.add_argument("--workload", default="prob256", choices=WORKLOAD_CHOICES)
+    ap.add_argument("--workload", default="room512-pruned", choices=WORKLOAD_CHOICES)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
@@ -1100,22 +1104,56 @@ def run_surrogate(args, nbt, torch, dev, stream, world, rank, local, dist) -> No
     m.close()
 
 
-def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
-    """room512 next-best-view selection, exact vs surrogate-pruned.
+PRUNED_MIN_SCENES = 25   # agreement is scored on at least this many scenes (8 PoIs each: >= 200 cases)
+PRUNED_SEG, PRUNED_KEEP = 4096, 205
 
-    The surrogate is trained first (inside this run, on exact labels of
-    seeded 256^3 rooms, 24 x 8 PoIs x 1024 views); then for each of the
-    room512 scenes (8 PoIs x 4096 candidate views of 320 x 240 rays) the
-    best view per PoI is chosen by exact raycasting of all candidates and by
-    raycasting only the surrogate's top 5 %.  Reports both views/s, the
-    speedup and how often the two choices agree.
-    """
-    import math
+
+def pruned_describe() -> str:
+    return ("room512-pruned: 512^3 2-bit room (2000 primitives, 40% unknown), 8 PoIs x 4096 candidate views of "
+            "320x240 rays per scene, unknown-voxel count; best view per PoI by exact raycasting of all "
+            "candidates vs of the surrogate's top 5 % (205 per PoI)")
+
+
+def wilson_interval(k: int, n: int, z: float = 1.959964) -> tuple[float, float]:
+    """95 % Wilson score interval of a binomial rate k / n."""
+    if n == 0:
+        return 0.0, 1.0
+    p = k / n
+    den = 1.0 + z * z / n
+    mid = (p + z * z / (2 * n)) / den
+    half = z * math.sqrt(p * (1.0 - p) / n + z * z / (4.0 * n * n)) / den
+    # at k = 0 (k = n) the lower (upper) bound is exactly 0 (1); keep rounding from moving it
+    return (0.0 if k == 0 else max(0.0, mid - half)), (1.0 if k == n else min(1.0, mid + half))
+
+
+def surrogate_method_flops_per_view() -> int:
+    """FLOPs of one inference forward as the kernels run it: layer 0 is a tensor-core GEMM over the
+    one-hot crop with K = 112 (28 taps x 4 class slots; 27 real taps) instead of a dense 8-channel
+    convolution (K = 216); layers 1-3 are implicit-GEMM convolutions (K = 27 C_in); fc1 and fc2."""
+    from paper_2503_22588_gb300.surrogate import CROP, FC_IN, HIDDEN, LAYERS
+    flops, size = 0, CROP
+    for i, (cin, cout, stride) in enumerate(LAYERS):
+        size = (size - 1) // stride + 1
+        k = 112 if i == 0 else 27 * cin
+        flops += 2 * size ** 3 * cout * k
+    return flops + 2 * FC_IN * HIDDEN + 2 * HIDDEN
+
+
+def room_scenes(seeds, workers: int):
+    """The room512 workloads of ``seeds``, generated on host cores (spawned worker processes)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from workload import configs
+    if workers <= 1:
+        return [configs.room512(seed=s) for s in seeds]
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(configs.room512, seeds))
+
+
+def train_room_surrogate(nbt, torch, dev, cam, prm, log=None):
+    """The surrogate trained inside the run on exact labels (mean ray IG) of 24 seeded 256^3 rooms."""
     from paper_2503_22588_gb300 import planning as P, surrogate as gs
-    from workload import configs, poses as wp, scenes
-
-    cam = nbt.camera(320, 240, math.radians(60), math.radians(45), 1.0)
-    prm = nbt.ig_params("count")
+    from workload import poses as wp, scenes
     maps, poses, targets = [], [], []
     for sidx in range(24):
         g = scenes.room_states(256, 500, 0.4, seed=1000 + sidx)
@@ -1127,114 +1165,286 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         maps.append(m)
         poses.append(pt)
         targets.append(P.label_views(m, pt, cam, prm))
-    net = gs.Surrogate(max_batch=4096, params=gs.he_init(0))
+    net = gs.Surrogate(max_batch=4096, params=gs.he_init(0), target_scale=P.TARGET_SCALE)
     t0 = time.perf_counter()
-    losses = P.train(net, maps, poses, targets, cam, prm, epochs=12, lr=1e-3, batch=256)
+    losses = P.train(net, maps, poses, targets, cam, prm, epochs=12, lr=1e-3, batch=256, log=log)
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
     for m in maps:
         m.close()
-    seg, keep = 4096, 205
-    same = cases = 0
-    # pruning baselines at the same exact budget: random candidates, the untrained network, and
-    # Eq. 3's interpolation (a random half of the budget raycast, G(x) at the rest, its top half raycast)
+    return net, {"seconds": train_s, "final_loss": losses[-1], "samples": 24 * 8 * 1024, "epochs": 12,
+                 "target": "mean ray IG x 0.01 (scale applied in the loss kernel)"}
+
+
+def pruned_cpu_baseline(w, budget_s: float = 12.0, single_s: float = 6.0) -> dict:
+    """The oracle's exact scoring (FP32 reference walk, FP64 sums) of a bounded sample of the same room512
+    candidates, on every host core and on one thread (the paper's CPU version was sequential)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    m = oracle.Map(w.grid, w.voxel_size, w.origin)
+    cam = oracle.camera_of(w.camera)
+    prm = oracle.params(w.metric)
+    t0 = time.perf_counter()
+    oracle.views_ig(m, w.poses[:threads], cam, prm, "f32", threads)
+    per = (time.perf_counter() - t0) / threads
+    n = int(max(threads, min(w.n_poses, budget_s / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.views_ig(m, w.poses[:n], cam, prm, "f32", threads)
+    dt = time.perf_counter() - t0
+    n1 = int(max(1, min(w.n_poses, single_s / max(per * threads, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.views_ig(m, w.poses[:n1], cam, prm, "f32", 1)
+    dt1 = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "views/s", "cores": threads, "kind": "oracle",
+            "sample": f"exact scoring of the first {n} of the {w.n_poses} candidate views of room512 scene 0",
+            "single_thread": {"value": n1 / dt1, "unit": "views/s", "cores": 1,
+                              "sample": f"the first {n1} candidate views of the same scene"}}
+
+
+def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
+    """room512 next-best-view selection, exact vs surrogate-pruned (the headline metric).
+
+    The surrogate is trained first, inside this run, on exact labels of seeded 256^3 rooms.  Then each
+    timed step takes one room512 scene (8 PoIs x 4096 candidate views of 320 x 240 rays): the pruned
+    arm uploads the map and runs nbt_plan_pruned (crops and network scores of every candidate, the top
+    5 % per PoI raycast exactly, the best of them); the exact arm uploads the map and raycasts every
+    candidate.  Both are timed with CUDA events on the launching stream, the L2 flushed before each.
+    The same-best-view rate is scored on at least 25 scenes (>= 200 PoI cases); scenes beyond the
+    timed steps are evaluated untimed.
+    """
+    import math
+    from paper_2503_22588_gb300 import planning as P, surrogate as gs
+
+    cam = nbt.camera(320, 240, math.radians(60), math.radians(45), 1.0)
+    prm = nbt.ig_params("count")
+    seg, keep = PRUNED_SEG, PRUNED_KEEP
+    stream = torch.cuda.current_stream(dev)
+    n_eval = max(PRUNED_MIN_SCENES, args.steps)
+    seeds = [1000 * rank + k for k in range(n_eval)]
+    t0 = time.perf_counter()
+    scenes_w = room_scenes(seeds, min(8, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - t0
+    net, train_info = train_room_surrogate(nbt, torch, dev, cam, prm)
+    n_views = scenes_w[0].n_poses
+    nseg = n_views // seg
+    grids = [torch.from_numpy(np.ascontiguousarray(w.grid)).to(dev) for w in scenes_w]
+    poses = [torch.from_numpy(w.poses).to(dev) for w in scenes_w]
+    m = nbt.Map(512, 512, 512, 0.01, (0.0, 0.0, 0.0), "u2")
+    ws_exact = nbt.workspace(n_views, cam, dev)
+    ws_pruned = P.pruned_workspace(net, n_views, seg, keep, cam, dev)
+    ig_all = torch.empty(n_views, dtype=torch.float32, device=dev)
+    steps_all = torch.empty(n_views, dtype=torch.int64, device=dev)
+    best_p = torch.empty(nseg, dtype=torch.int32, device=dev)
+    val_p = torch.empty(nseg, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def pruned_step(k):
+        m.upload(grids[k], stream)
+        P.pruned_best(net, m, poses[k], seg, keep, cam, prm, ws_pruned, stream, (best_p, val_p), want_kept=False)
+
+    def exact_step(k, ev=None):
+        m.upload(grids[k], stream)
+        if ev is not None:
+            ev[0].record(stream)
+        nbt.views_ig(m, poses[k], cam, prm, ig_all, steps_all, ws_exact, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        return P.segment_argmax(ig_all, seg, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):                 # untimed passes of both arms
+        pruned_step(0)
+        exact_step(0)
+    barrier()
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ev_p = [(E(), E()) for _ in range(args.steps)]
+    ev_x = [(E(), E()) for _ in range(args.steps)]
+    ev_k = [(E(), E()) for _ in range(args.steps)]
+    same = optimal = cases = 0
+    vox_steps = 0
+    exact_best, exact_ig = [], []
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                    # evict the map from L2 (untimed)
+        ev_p[k][0].record(stream)
+        pruned_step(k)
+        ev_p[k][1].record(stream)
+        flush.fill_((k + 1) & 0xFF)
+        ev_x[k][0].record(stream)
+        bx, vx = exact_step(k, ev_k[k])
+        ev_x[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        same += int((bx == best_p).sum().item())
+        optimal += int((vx == val_p).sum().item())
+        cases += nseg
+        vox_steps += int(steps_all.sum().item())
+        exact_best.append(bx.clone())
+        exact_ig.append(ig_all.clone())
+    barrier()
+    clk = clocks.stop()
+    pr_ms = [a.elapsed_time(b) for a, b in ev_p]
+    ex_ms = [a.elapsed_time(b) for a, b in ev_x]
+    kern_ms = [a.elapsed_time(b) for a, b in ev_k]
+    pr_total = max_over_ranks(float(sum(pr_ms)), dist, dev)
+    ex_total = max_over_ranks(float(sum(ex_ms)), dist, dev)
+
+    # agreement on the scenes beyond the timed steps (untimed), same calls
+    for k in range(args.steps, n_eval):
+        pruned_step(k)
+        bx, vx = exact_step(k)
+        torch.cuda.synchronize(dev)
+        same += int((bx == best_p).sum().item())
+        optimal += int((vx == val_p).sum().item())
+        cases += nseg
+        exact_best.append(bx.clone())
+        exact_ig.append(ig_all.clone())
+
+    # pruning baselines at the same exact budget (205 raycast views per PoI), same scenes: random
+    # candidates, the untrained network, and Eq. 3's interpolation (a random half of the budget
+    # raycast and pushed as one ID, G(x) at the other candidates, the top of G(x) raycast)
     base = {"random": 0, "untrained_network": 0, "idw_eq3": 0}
     net0 = gs.Surrogate(max_batch=4096, params=gs.he_init(0))
+    ws0 = P.pruned_workspace(net0, n_views, seg, keep, cam, dev)
     k1 = keep // 2
     k2 = keep - k1
     idbuf = nbt.IdBuffer(n_b=1, max_views=k1)
-    ex_ms, pr_ms, e2e_ms = [], [], []
-    e2e_h2d = e2e_d2h = 0
-    n_views = 0
-    clocks = ClockSampler(local)
-    clocks.start()
-    for es in range(args.steps):
-        w = configs.room512(seed=es)
-        m = nbt.Map.from_grid(torch.from_numpy(w.grid).to(dev), w.voxel_size, w.origin, "u2")
-        pt = torch.from_numpy(w.poses).to(dev)
-        ws = nbt.workspace(len(pt), cam, dev)
-        for _ in range(max(args.warmup, 3)):    # untimed passes of both selections on this scene
-            P.exact_best(m, pt, seg, cam, prm, ws)
-            P.pruned_best(net, m, pt, seg, keep, cam, prm)
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-        e[0].record()
-        bx, vx, _ = P.exact_best(m, pt, seg, cam, prm, ws)
-        e[1].record()
-        bp, vp, _ = P.pruned_best(net, m, pt, seg, keep, cam, prm)
-        e[2].record()
-        torch.cuda.synchronize(dev)
-        ex_ms.append(e[0].elapsed_time(e[1]))
-        pr_ms.append(e[1].elapsed_time(e[2]))
-        # end to end: candidate poses from pinned host memory, best indices back to the host
-        ph = torch.from_numpy(w.poses).pin_memory()
-        bh = torch.empty(bp.shape, dtype=bp.dtype).pin_memory()
-        e[3].record()
-        pt.copy_(ph, non_blocking=True)
-        be, _, _ = P.pruned_best(net, m, pt, seg, keep, cam, prm)
-        bh.copy_(be, non_blocking=True)
-        e[4].record()
-        e[4].synchronize()
-        e2e_ms.append(e[3].elapsed_time(e[4]))
-        e2e_h2d, e2e_d2h = ph.numel() * ph.element_size(), bh.numel() * bh.element_size()
-        same += int((bx == bp).sum().item())
-        cases += len(bx)
-        n_views += len(pt)
-        nseg = len(pt) // seg
-        rs = torch.from_numpy(np.random.default_rng(4000 + es).random(len(pt), dtype=np.float32)).to(dev)
-        idx_r, kept_r = P.segment_topk(rs, seg, keep, pt)
-        ig_r, _ = nbt.views_ig(m, kept_r, cam, prm, want_steps=False)
-        b_r, _ = P.segment_argmax(ig_r, keep, idx_r.reshape(-1).contiguous())
+    g_all = torch.empty(n_views, dtype=torch.float32, device=dev)
+    for k in range(n_eval):
+        m.upload(grids[k], stream)
+        bx, ig_k, pt = exact_best[k], exact_ig[k], poses[k]
+        rs = torch.from_numpy(np.random.default_rng(4000 + seeds[k]).random(n_views, dtype=np.float32)).to(dev)
+        idx_r, _ = P.segment_topk(rs, seg, keep)
+        b_r, _ = P.segment_argmax(ig_k[idx_r.reshape(-1).long()].contiguous(), keep, idx_r.reshape(-1).contiguous())
         base["random"] += int((bx == b_r).sum().item())
-        b_u, _, _ = P.pruned_best(net0, m, pt, seg, keep, cam, prm)
+        b_u, _, _ = P.pruned_best(net0, m, pt, seg, keep, cam, prm, ws0, want_kept=False)
         base["untrained_network"] += int((bx == b_u).sum().item())
         idx_1, kept_1 = P.segment_topk(rs, seg, k1, pt)
-        ig_1, _ = nbt.views_ig(m, kept_1, cam, prm, want_steps=False)
-        g_all = torch.empty(len(pt), dtype=torch.float32, device=dev)
-        for s in range(nseg):
-            idbuf.push(kept_1[s * k1:(s + 1) * k1], ig_1[s * k1:(s + 1) * k1])
-            nbt.idw_gain(idbuf, pt[s * seg:(s + 1) * seg], 2.0, g_all[s * seg:(s + 1) * seg])
+        ig_1 = ig_k[idx_1.reshape(-1).long()].contiguous()
+        for s_ in range(nseg):
+            idbuf.push(kept_1[s_ * k1:(s_ + 1) * k1], ig_1[s_ * k1:(s_ + 1) * k1])
+            nbt.idw_gain(idbuf, pt[s_ * seg:(s_ + 1) * seg], 2.0, g_all[s_ * seg:(s_ + 1) * seg])
         g_all.index_fill_(0, idx_1.reshape(-1).long(), float("-inf"))  # already raycast
-        idx_2, kept_2 = P.segment_topk(g_all, seg, k2, pt)
-        ig_2, _ = nbt.views_ig(m, kept_2, cam, prm, want_steps=False)
-        vals = torch.cat([ig_1.view(nseg, k1), ig_2.view(nseg, k2)], 1).reshape(-1).contiguous()
+        idx_2, _ = P.segment_topk(g_all, seg, k2)
         idxs = torch.cat([idx_1, idx_2], 1).reshape(-1).contiguous()
-        b_i, _ = P.segment_argmax(vals, keep, idxs)
+        b_i, _ = P.segment_argmax(ig_k[idxs.long()].contiguous(), keep, idxs)
         base["idw_eq3"] += int((bx == b_i).sum().item())
-        m.close()
-    clk = clocks.stop()
+    torch.cuda.synchronize(dev)
     idbuf.close()
     net0.close()
-    ex_total, pr_total = float(sum(ex_ms)), float(sum(pr_ms))
+
+    # surrogate forward alone (crops excluded), for its tensor-core roofline: the timed scenes' candidates
+    cr = torch.empty((net.max_batch, gs.CROP, gs.CROP, gs.CROP), dtype=torch.uint8, device=dev)
+    ft = torch.empty((net.max_batch, gs.FEATS), dtype=torch.bfloat16, device=dev)
+    sc = torch.empty(n_views, dtype=torch.float32, device=dev)
+    fwd_ms = []
+    for k in range(min(args.steps, 4)):
+        m.upload(grids[k], stream)
+        t_k = 0.0
+        for c0 in range(0, n_views, net.max_batch):
+            c_b, f_b = gs.crops(m, poses[k][c0:c0 + net.max_batch], cam, prm, stream, out=(cr, ft))
+            a, b = E(), E()
+            a.record(stream)
+            net.forward(c_b, f_b, sc[c0:c0 + net.max_batch], stream)
+            b.record(stream)
+            b.synchronize()
+            t_k += a.elapsed_time(b)
+        fwd_ms.append(t_k)
+
+    # end to end through the public API: the dense grid and the candidate poses from pinned host memory,
+    # the best views and their IGs back to the host, every step
+    grid_h = torch.empty(grids[0].shape, dtype=torch.uint8).pin_memory()
+    poses_h = torch.empty(poses[0].shape, dtype=torch.float32).pin_memory()
+    best_h = torch.empty(nseg, dtype=torch.int32).pin_memory()
+    val_h = torch.empty(nseg, dtype=torch.float32).pin_memory()
+    pz_dev = torch.empty_like(poses[0])
+    e2e_ms = []
+    for k in range(args.steps):
+        grid_h.numpy()[...] = scenes_w[k].grid            # staging into pinned memory (untimed)
+        poses_h.numpy()[...] = scenes_w[k].poses
+        flush.fill_(k & 0xFF)
+        a, b = E(), E()
+        a.record(stream)
+        m.upload(grid_h.numpy(), stream)
+        pz_dev.copy_(poses_h, non_blocking=True)
+        P.pruned_best(net, m, pz_dev, seg, keep, cam, prm, ws_pruned, stream, (best_p, val_p), want_kept=False)
+        best_h.copy_(best_p, non_blocking=True)
+        val_h.copy_(val_p, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_total = max_over_ranks(float(sum(e2e_ms)), dist, dev)
+
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm, hbm_kind = load_peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    bf16_kind = "measured (bf16_tflops, burst)" if "bf16_tflops" in peaks else "fallback (1.9 PFLOP/s burst)"
+    kern_mean = float(np.mean(kern_ms))
+    steps_per_launch = vox_steps / args.steps
+    achieved = steps_per_launch * BYTES_PER_STEP["u2"] / (kern_mean * 1e-3) / 1e9
+    fl = surrogate_method_flops_per_view()
+    fwd_mean = float(np.mean(fwd_ms))
+    s_achieved = fl * n_views / (fwd_mean * 1e-3) / 1e12
+    lo, hi = wilson_interval(same, cases)
+    n_chunks = (n_views + net.max_batch - 1) // net.max_batch
     line = {
-        "metric": METRIC, "value": n_views / (pr_total * 1e-3), "unit": "views/s", "n_gpus": world,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": pr_total / args.steps,
-        "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 surrogate + u2 exact", "data": "synthetic",
-        "config": {"workload": "room512-pruned: per scene 8 PoIs x 4096 candidate views of 320x240 rays on a "
-                               "512^3 2-bit room; best view per PoI by exact raycasting of all candidates vs of "
-                               "the surrogate's top 5 % (205 per PoI)",
-                   "train": "24 seeded 256^3 rooms x 8 PoIs x 1024 views, exact count labels, 12 epochs",
-                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (32 MiB map + 17 GB crops)"},
-        "exact_views_per_s": n_views / (ex_total * 1e-3),
-        "pruned_views_per_s": n_views / (pr_total * 1e-3),
+        "metric": METRIC, "value": job_throughput(n_views * args.steps, world, pr_total), "unit": "views/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": pr_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 surrogate + u2 exact",
+        "data": "synthetic",
+        "config": {"workload": pruned_describe(), "views_per_step": n_views, "rays_per_view": 320 * 240,
+                   "map": "512^3 u2", "scenes": f"seeds {seeds[0]}..{seeds[-1]} (timed: first {args.steps})",
+                   "train": "24 seeded 256^3 rooms x 8 PoIs x 1024 views, exact labels, 12 epochs (before timing)",
+                   "parallelism": f"replicas x{world}", "l2": "flushed before every timed arm (256 MiB write)",
+                   "step": "pruned: map upload + nbt_plan_pruned (crops, forward, top-k, exact re-score, argmax); "
+                           "exact: map upload + nbt_views_ig of all candidates + argmax"},
+        "exact_views_per_s": job_throughput(n_views * args.steps, world, ex_total),
+        "pruned_views_per_s": job_throughput(n_views * args.steps, world, pr_total),
         "speedup": ex_total / pr_total,
-        "same_best_view": {"agree": same, "cases": cases, "rate": same / max(1, cases)},
+        "voxel_steps_per_s": world * vox_steps / (float(sum(kern_ms)) * 1e-3),
+        "voxel_steps_per_exact_step": steps_per_launch,
+        "exact_views_ig_ms": kern_mean,
+        "same_best_view": {"agree": same, "cases": cases, "rate": same / max(1, cases), "wilson95": [lo, hi],
+                           "target": 0.95, "scenes": n_eval,
+                           "optimal_ig": {"agree": optimal, "rate": optimal / max(1, cases),
+                                          "what": "pruned choice's exact IG equals the exact maximum"}},
         "pruning_baselines": {
             "exact_views_per_poi": keep,
             **{k: {"agree": v, "cases": cases, "rate": v / max(1, cases)} for k, v in base.items()},
             "idw_eq3_scheme": f"{k1} random candidates per PoI raycast, G(x) of Eq. 3 (p = 2, one ID) at the "
                               f"others, its top {k2} raycast; best of the {keep}"},
-        "train": {"seconds": train_s, "final_loss": losses[-1], "samples": 24 * 8 * 1024},
-        "e2e": {"value": n_views / (float(sum(e2e_ms)) * 1e-3), "unit": "views/s", "h2d_bytes_per_step": e2e_h2d,
-                "d2h_bytes_per_step": e2e_d2h},
-        # per scene: 8 chunks x (crops, layers 0-1, layer 2, layer 3, features, fc1, fc2), then top-k,
-        # the exact walk of the kept views and its reduce, argmax
-        "gpu_launches": 60 * args.steps,
+        "train": train_info,
+        "scene_generation_s": gen_s,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": ncu_traffic("room512"), "kernel": "ig_tiles_kernel<u2> (exact arm, + views_reduce)",
+                     "algorithmic": f"0.25 B per voxel step x {steps_per_launch:.0f} steps per launch",
+                     "peak_kind": f"{hbm_kind} (hbm_gbs)"},
+        "roofline_surrogate": {"bound": "tensor", "achieved": s_achieved, "peak": bf16, "unit": "TFLOP/s",
+                               "frac": s_achieved / bf16, "traffic": None,
+                               "kernel": "surrogate forward (fused layers 0-1, layers 2-3, fc1, fc2)",
+                               "algorithmic": f"{fl} FLOP per view (layer 0 as its K = 112 one-hot GEMM) x {n_views}",
+                               "forward_ms_per_step": fwd_mean, "peak_kind": bf16_kind},
+        "e2e": {"value": job_throughput(n_views * args.steps, world, e2e_total), "unit": "views/s",
+                "h2d_bytes_per_step": int(grid_h.numel() + poses_h.numel() * 4),
+                "d2h_bytes_per_step": int(best_h.numel() * 4 + val_h.numel() * 4)},
+        # pruned step: upload (1) + per batch of 4096 (crops, fused layers 0-1, layer 2, layer 3, features,
+        # fc1, fc2) + top-k + tile kernel + reduce + argmax
+        "gpu_launches": (1 + 7 * n_chunks + 4) * args.steps,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = pruned_cpu_baseline(scenes_w[0])
     if rank == 0:
         print(json.dumps(line), flush=True)
     net.close()
+    m.close()
 
 
 if __name__ == "__main__":

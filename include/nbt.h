@@ -142,7 +142,9 @@ int nbt_get_version(int32_t *version);
 int nbt_map_create(const nbt_map_desc *desc, nbt_map *out);
 
 /* Release a map and its device memory (synchronises the device first so no
- * enqueued call still reads it).  NULL is accepted and ignored. */
+ * enqueued call still reads it).  NULL is accepted and ignored; a handle that
+ * names no live map (already destroyed) returns NBT_EINVAL.  Every other
+ * call that takes a map handle also returns NBT_EINVAL for such a handle. */
 int nbt_map_destroy(nbt_map map);
 
 /* Upload a dense x-fastest grid (the paper's voxel map, Section III) into
@@ -218,7 +220,8 @@ int nbt_camera_from_grid_scale(float fov_h, float fov_v, float max_range, float 
 /* Device workspace, in bytes, that nbt_views_ig / nbt_traj_ig need for
  * n_poses perspectives of camera `cam` (per-tile partial sums).  The caller
  * allocates it (any device allocator) and passes it to those calls; it may
- * be reused by calls that do not overlap on the device. */
+ * be reused by calls that do not overlap on the device.  Errors: NBT_EINVAL
+ * (n_poses outside [0, INT32_MAX], an invalid camera). */
 int nbt_workspace_size(int64_t n_poses, const nbt_camera *cam, int64_t *bytes);
 
 /* Per-perspective IG (Section III "IG Calculation"): for each of n_views
@@ -229,9 +232,9 @@ int nbt_workspace_size(int64_t n_poses, const nbt_camera *cam, int64_t *bytes);
  *              (the occluding voxel included).
  *   workspace: device buffer of >= nbt_workspace_size(n_views, cam) bytes,
  *              16-byte aligned.
- * n_views == 0 is valid and enqueues nothing.  Errors: NBT_EINVAL,
- * NBT_EUNSUPPORTED (Eq. 2 / entropy on a state map), NBT_EWORKSPACE,
- * NBT_ECUDA. */
+ * n_views in [0, INT32_MAX]; n_views == 0 is valid and enqueues nothing.
+ * Errors: NBT_EINVAL, NBT_EUNSUPPORTED (Eq. 2 / entropy on a state map),
+ * NBT_EWORKSPACE, NBT_ECUDA. */
 int nbt_views_ig(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_camera *cam,
                  const nbt_ig_params *params, float *ig_out, uint64_t *steps_out, void *workspace,
                  int64_t workspace_bytes, void *stream);
@@ -293,7 +296,9 @@ int nbt_view_segments(nbt_map map, const nbt_pose *poses, int64_t n_views, const
  * n_traj, the camera or the params).  A probability map's derived gains
  * are refreshed outside the graph when the map was re-uploaded.  Creating
  * a plan synchronises an internal stream; launching does not synchronise.
- * Errors: as nbt_traj_ig, plus NBT_ECUDA if capture fails. */
+ * Errors: as nbt_traj_ig, plus NBT_ECUDA if capture fails; nbt_plan_launch
+ * returns NBT_EINVAL (and launches nothing) once the plan's map has been
+ * destroyed, even if a new map now lives at the same address. */
 typedef struct nbt_plan_s *nbt_plan;
 int nbt_plan_create_traj(nbt_map map, const nbt_pose *poses, int64_t n_poses, const int32_t *offsets, int32_t n_traj,
                          const nbt_camera *cam, const nbt_ig_params *params, float *traj_ig_out, float *pose_ig_out,
@@ -329,6 +334,25 @@ int nbt_tc_gemm(const void *a, const void *b, float *c, int32_t m, int32_t n, in
  * bounded device-side wait gave up since the last read (then the results
  * of that launch are invalid).  Synchronises; reading clears the word. */
 int nbt_tc_error(int32_t *flag);
+
+/* Bound, in nanoseconds of the GPU's global timer, on every device-side
+ * mbarrier wait of the tensor-core kernels on the current device (default
+ * 2 s).  A wait that reaches it gives up: the kernel sets the error word
+ * (nbt_tc_error), waits (bounded again) for its own tensor-core operations
+ * in flight, frees its tensor memory and returns, so the context stays
+ * usable.  ns in [1e3, 6e10].  Synchronous (a copy to device constant
+ * memory); do not change it while tensor-core kernels run.  Errors:
+ * NBT_EINVAL, NBT_ECUDA. */
+int nbt_tc_set_wait_limit(uint64_t ns);
+
+/* Test entry point of that failure path (no counterpart in the paper): on
+ * every SM, a CTA takes all 512 tensor-memory columns and waits on an
+ * mbarrier that nothing completes; when the bounded wait gives up it sets
+ * the error word, frees the columns and returns.  The launch therefore ends
+ * after about the wait limit (shorten it first with nbt_tc_set_wait_limit)
+ * and leaves the error word set.  Asynchronous on stream.  Errors:
+ * NBT_ECUDA. */
+int nbt_tc_wait_probe(void *stream);
 
 /* The learned IG surrogate (no counterpart in the paper; it prunes
  * candidate perspectives before the exact Section III raycast re-scores
@@ -382,6 +406,22 @@ int nbt_surrogate_backward(nbt_surrogate net, const void *crops, const void *fea
 int nbt_surrogate_train_step(nbt_surrogate net, const void *crops, const void *feats, const float *targets, int32_t n,
                              float lr, float *loss_out, void *stream);
 
+/* Scale c > 0 (finite) applied to the targets of nbt_surrogate_backward and
+ * nbt_surrogate_train_step: the loss is mean (pred - c t)^2, with c t
+ * rounded to FP32.  Default 1.  Lets the caller pass Section III's mean ray
+ * IG g_P as the target while the network predicts g_P c (e.g. c = 0.01, so
+ * that outputs are of order 1).  Host-side setting.  Errors: NBT_EINVAL. */
+int nbt_surrogate_set_target_scale(nbt_surrogate net, float scale);
+
+/* Checkpoint / resume of training: the Adam moments m and v (FP32 host
+ * arrays in the parameter layout, n = the parameter count) and the number of
+ * Adam steps taken.  Together with nbt_surrogate_get_params / set_params
+ * (set_params first: it resets the Adam state) and the target scale they
+ * are the whole training state, so training resumed from them continues
+ * bit for bit.  Synchronous.  Errors: NBT_EINVAL, NBT_ECUDA. */
+int nbt_surrogate_get_adam(nbt_surrogate net, float *m_host, float *v_host, int64_t n, int64_t *step);
+int nbt_surrogate_set_adam(nbt_surrogate net, const float *m_host, const float *v_host, int64_t n, int64_t step);
+
 /* Surrogate-pruned planning helpers.  Candidates come in segments of seg
  * perspectives (e.g. the views around one PoI); n % seg == 0.
  * nbt_segment_topk: for each segment, the global indices of its keep
@@ -396,8 +436,8 @@ int nbt_segment_topk(const float *scores, int64_t n, int32_t seg, int32_t keep, 
 int nbt_segment_argmax(const float *values, const int32_t *idx, int64_t n, int32_t seg, int32_t *best_idx,
                        float *best_val, void *stream);
 
-/* IG between perspectives (Section III "Orientation Factor and IG", Eq. 3,
- * and "Cost Function Extension").  An information distribution (ID) is one
+/* IG between perspectives (Section IV, paragraphs "Orientation Factor
+ * O(x_k) and IG G(x_k)" with Eq. 3, and "Cost Function Extension").  An information distribution (ID) is one
  * set of N_P perspectives: start points p_P,j (metres, world frame) and
  * IGs g_P,j (e.g. the mean ray IG nbt_views_ig returns).  The buffer keeps
  * the N_B most recent IDs; a camera position x between perspectives gets
@@ -469,6 +509,34 @@ int nbt_ig_cost(nbt_id_buffer buf, const nbt_pose *poses, int64_t n_poses, const
                 const float *poi, float fov_h, float fov_v, const nbt_cost_params *params, float *gain_out,
                 float *orient_out, float *term_out, float *cost_out, void *stream);
 
+/* Surrogate-pruned next-best-view selection in one call.  n candidate
+ * perspectives (device poses) in segments of seg (e.g. the candidates
+ * around one PoI; n % seg == 0, 1 <= keep <= seg <= 8192, n <= INT32_MAX):
+ *   1. crops and network scores of every candidate (nbt_surrogate_crops and
+ *      nbt_surrogate_forward, in batches of the net's max_batch);
+ *   2. per segment, the keep highest scores (nbt_segment_topk);
+ *   3. the exact IG of those keep candidates (nbt_views_ig: Section III,
+ *      Eq. 2 / the unknown count along the rays to N_O, reduced per params);
+ *   4. per segment, the kept candidate of highest exact IG
+ *      (nbt_segment_argmax; ties to the lowest candidate index).
+ * Exact raycasting judges the kept candidates, so pruning may miss the
+ * best view but never reports a wrong IG; keep = seg gives exactly the
+ * choice of raycasting every candidate.  The surrogate is not part of the
+ * paper.
+ *   best_out:    device int32[n / seg], global candidate index per segment;
+ *   best_ig_out: device float[n / seg] or NULL, its exact IG;
+ *   kept_out:    device int32[n / seg][keep] or NULL, the kept indices
+ *                (descending score);
+ *   workspace:   device buffer of >= nbt_pruned_workspace_size bytes,
+ *                256-byte aligned, owned by the caller.
+ * Allocates nothing; asynchronous on stream.  n == 0 enqueues nothing.
+ * Errors: NBT_EINVAL, NBT_EUNSUPPORTED, NBT_EWORKSPACE, NBT_ECUDA. */
+int nbt_pruned_workspace_size(nbt_surrogate net, int64_t n, int32_t seg, int32_t keep, const nbt_camera *cam,
+                              int64_t *bytes);
+int nbt_plan_pruned(nbt_map map, nbt_surrogate net, const nbt_pose *poses, int64_t n, int32_t seg, int32_t keep,
+                    const nbt_camera *cam, const nbt_ig_params *params, int32_t *best_out, float *best_ig_out,
+                    int32_t *kept_out, void *workspace, int64_t workspace_bytes, void *stream);
+
 /* Size of the fixed device scratch array behind nbt_views_ig_noalloc. */
 #define NBT_NOALLOC_SCRATCH_BYTES (4 << 20)
 
@@ -490,13 +558,16 @@ int nbt_ig_cost(nbt_id_buffer buf, const nbt_pose *poses, int64_t n_poses, const
  * (the map, the poses and the outputs are still the caller's).  The request
  * must fit the array: n_views * ceil(W / 32) * ceil(H / 8) tiles, 16 bytes
  * each, plus a 256-byte header, at most NBT_NOALLOC_SCRATCH_BYTES (262,128
- * tiles, e.g. 3,495 views of 160 x 120 rays); larger requests return
- * NBT_ESCRATCH before anything is enqueued -- split them into several
- * calls.
+ * tiles, e.g. 3,495 views of 160 x 120 rays); larger requests (n_views is
+ * bounded before any size is multiplied out) return NBT_ESCRATCH before
+ * anything is enqueued -- split them into several calls.
  *
  * The first call on a device looks up the array's device address there
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array
+ * before any stream capture.  The address is kept per device and CUDA
+ * context: after the device's context was destroyed and created again
+ * (cudaDeviceReset), the next call looks it up anew, so that first call on
+ * the new context too should come before any stream capture.  Every call on a device shares the one array
  * and clears the part that must start at zero itself; calls whose work
  * overlaps on the GPU (different streams, no ordering between them) race
  * on the array and give wrong results, so order them on one stream or with

@@ -1,6 +1,6 @@
 """CPU oracle of the IG interpolation and the IG cost -- TEST INFRASTRUCTURE, NOT PRODUCT CODE.
 
-Section III ("Orientation Factor and IG" and "Cost Function Extension")
+Section IV ("Orientation Factor O(x_k) and IG G(x_k)" and "Cost Function Extension")
 turns a buffer of information distributions (IDs; each one is N_P
 perspective start points p_P,j with their IGs g_P,j) into a cost for a
 candidate trajectory x_0..x_K:

@@ -92,6 +92,14 @@ SIGNATURES = {
     "nbt_surrogate_forward": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "nbt_surrogate_backward": (C.c_int, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "nbt_surrogate_train_step": (C.c_int, [_vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp]),
+    "nbt_surrogate_set_target_scale": (C.c_int, [_vp, _f]),
+    "nbt_surrogate_get_adam": (C.c_int, [_vp, _vp, _vp, _i64, P(C.c_int64)]),
+    "nbt_surrogate_set_adam": (C.c_int, [_vp, _vp, _vp, _i64, _i64]),
+    "nbt_tc_set_wait_limit": (C.c_int, [C.c_uint64]),
+    "nbt_tc_wait_probe": (C.c_int, [_vp]),
+    "nbt_pruned_workspace_size": (C.c_int, [_vp, _i64, _i32, _i32, P(Camera), P(C.c_int64)]),
+    "nbt_plan_pruned": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, P(Camera), P(IgParams), _vp, _vp, _vp, _vp, _i64,
+                                  _vp]),
     "nbt_map_get_tuning": (C.c_int, [_vp, P(Tuning)]),
     "nbt_id_buffer_create": (C.c_int, [_i32, _i32, P(_vp)]),
     "nbt_id_buffer_destroy": (C.c_int, [_vp]),

@@ -1,7 +1,7 @@
 // IG between perspectives: the information-distribution (ID) buffer, the
 // inverse-distance-weighted gain G(x) of Eq. 3, the orientation factor O(x)
-// and the IG cost c_I (Section III, "Orientation Factor and IG" and "Cost
-// Function Extension").
+// and the IG cost c_I (Section IV, "Orientation Factor O(x_k) and IG
+// G(x_k)" and "Cost Function Extension").
 //
 // Layout: one device slab of n_b slots; a slot holds up to `cap`
 // perspectives (a multiple of kBlock) as pairs, two float4 per pair:

@@ -58,6 +58,7 @@ struct nbt_map_s {
   int32_t *d_tab = nullptr;          // offset tables: nx + ny + nz entries
   void *d_stage = nullptr;           // staging buffer for host uploads
   int64_t stage_bytes = 0;
+  uint64_t id = 0;                   // unique per created map (live-map registry)
   uint64_t version = 0;              // bumped by every upload
   // derived gain cache key
   bool gain_valid = false;
@@ -449,7 +450,11 @@ __device__ __forceinline__ bool walk_lane_part(Walk &w, int &lin, int lane, int 
 }
 
 // Host helpers (defined in nbt_map.cu).
-int check_map(nbt_map map);
+bool valid_camera(const nbt_camera *c);     // ranges of nbt_camera (defined in nbt_raycast.cu)
+bool valid_params(const nbt_ig_params *p);  // ranges of nbt_ig_params (defined in nbt_raycast.cu)
+int check_map(nbt_map map);                 // NBT_EINVAL unless a live map on the current device
+bool map_alive(nbt_map map, uint64_t id);   // live, and (id != 0) created with that id
+void free_map(nbt_map map);                 // release a map's memory (no registry update)
 int prepare_gain(nbt_map map, const nbt_ig_params *params, cudaStream_t stream);
 int payload_kind(nbt_map map, const nbt_ig_params *params, PayloadKind *kind, const void **payload);
 int sm_count();

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "nbt_internal.cuh"
@@ -197,8 +198,36 @@ int sm_count() {
   return cached[dev];
 }
 
+// Live maps: handle -> creation id.  Every handle-taking call checks that
+// the handle names a live map before reading it, so a destroyed handle
+// returns NBT_EINVAL instead of reading freed memory; a plan also checks the
+// id, which a new map created at the same address does not share.
+namespace {
+std::mutex g_maps_mu;
+std::unordered_map<const nbt_map_s *, uint64_t> g_maps;
+uint64_t g_next_map_id = 1;
+
+uint64_t register_map(nbt_map m) {
+  std::lock_guard<std::mutex> lock(g_maps_mu);
+  const uint64_t id = g_next_map_id++;
+  g_maps[m] = id;
+  return id;
+}
+
+bool unregister_map(nbt_map m) {
+  std::lock_guard<std::mutex> lock(g_maps_mu);
+  return g_maps.erase(m) == 1;
+}
+}  // namespace
+
+bool map_alive(nbt_map map, uint64_t id) {
+  std::lock_guard<std::mutex> lock(g_maps_mu);
+  const auto it = g_maps.find(map);
+  return it != g_maps.end() && (id == 0 || it->second == id);
+}
+
 int check_map(nbt_map map) {
-  if (!map) return NBT_EINVAL;
+  if (!map || !map_alive(map, 0)) return NBT_EINVAL;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return NBT_ECUDA;
   return dev == map->device ? NBT_OK : NBT_EINVAL;
@@ -336,15 +365,26 @@ int nbt_map_create(const nbt_map_desc *desc, nbt_map *out) {
     rc = NBT_ECUDA;
   if (rc != NBT_OK) {
     (void)cudaGetLastError();
-    nbt_map_destroy(m);
+    free_map(m);
     return rc;
   }
+  m->id = register_map(m);
   *out = m;
   return NBT_OK;
 }
 
 int nbt_map_destroy(nbt_map map) {
   if (!map) return NBT_OK;
+  if (!unregister_map(map)) return NBT_EINVAL;  // not a live map (already destroyed)
+  free_map(map);
+  return NBT_OK;
+}
+
+}  // extern "C"
+
+namespace nbt {
+
+void free_map(nbt_map map) {
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != map->device) cudaSetDevice(map->device);
@@ -361,8 +401,11 @@ int nbt_map_destroy(nbt_map map) {
   (void)cudaGetLastError();
   if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
   delete map;
-  return NBT_OK;
 }
+
+}  // namespace nbt
+
+extern "C" {
 
 int nbt_map_upload(nbt_map map, const void *src, int64_t bytes, int32_t src_on_device, void *stream_) {
   int rc = check_map(map);
@@ -424,7 +467,7 @@ int nbt_map_download(nbt_map map, void *dst, int64_t bytes, void *stream_) {
 }
 
 int nbt_map_info(nbt_map map, nbt_map_desc *desc, int64_t *device_bytes) {
-  if (!map) return NBT_EINVAL;
+  if (!map || !map_alive(map, 0)) return NBT_EINVAL;
   if (desc) *desc = map->desc;
   if (device_bytes) {
     int64_t b = map->payload_bytes + (int64_t)(map->desc.nx + map->desc.ny + map->desc.nz) * 4 + map->stage_bytes;

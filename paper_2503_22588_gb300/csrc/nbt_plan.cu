@@ -16,6 +16,7 @@
 
 struct nbt_plan_s {
   nbt_map map = nullptr;
+  uint64_t map_id = 0;  // the map's creation id: a destroyed map is detected at launch
   nbt_ig_params params;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -74,6 +75,7 @@ int nbt_plan_create_traj(nbt_map map, const nbt_pose *poses, int64_t n_poses, co
     return rc;
   }
   p->map = map;
+  p->map_id = map->id;
   p->params = *params;
   *out = p;
   return NBT_OK;
@@ -81,6 +83,7 @@ int nbt_plan_create_traj(nbt_map map, const nbt_pose *poses, int64_t n_poses, co
 
 int nbt_plan_launch(nbt_plan plan, void *stream) {
   if (!plan || !plan->exec) return NBT_EINVAL;
+  if (!map_alive(plan->map, plan->map_id)) return NBT_EINVAL;  // the plan's map was destroyed
   int rc = check_map(plan->map);
   if (rc != NBT_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;

@@ -24,10 +24,11 @@
 
 #include <algorithm>
 
+#include <cuda.h>
+
 #include "nbt_internal.cuh"
 
 namespace nbt {
-namespace {
 
 bool valid_camera(const nbt_camera *c) {
   if (!c) return false;
@@ -47,6 +48,8 @@ bool valid_params(const nbt_ig_params *p) {
   if (!isfinite(p->occ_threshold) || !isfinite(p->free_threshold)) return false;
   return true;
 }
+
+namespace {
 
 // Section III endpoint grid: d_h = d_Cam tan(FoV_h / 2), d_v likewise, in
 // FP64 on the host; the grid start and spacing are each rounded once to FP32.
@@ -935,7 +938,8 @@ int nbt_camera_from_grid_scale(float fov_h, float fov_v, float max_range, float 
 }
 
 int nbt_workspace_size(int64_t n_poses, const nbt_camera *cam, int64_t *bytes) {
-  if (!bytes || n_poses < 0 || !valid_camera(cam)) return NBT_EINVAL;
+  // n_poses <= INT32_MAX keeps n_poses * tiles * 16 below 2^59 (tiles < 2^24)
+  if (!bytes || n_poses < 0 || n_poses > INT32_MAX || !valid_camera(cam)) return NBT_EINVAL;
   const int64_t tiles = (int64_t)((cam->width + kTileW - 1) / kTileW) * ((cam->height + kTileH - 1) / kTileH);
   *bytes = workspace_bytes_for(n_poses * tiles);
   return NBT_OK;
@@ -946,7 +950,7 @@ int nbt_views_ig(nbt_map map, const nbt_pose *poses, int64_t n_views, const nbt_
                  int64_t workspace_bytes, void *stream_) {
   int rc = check_map(map);
   if (rc != NBT_OK) return rc;
-  if (n_views < 0 || !valid_camera(cam) || !valid_params(params)) return NBT_EINVAL;
+  if (n_views < 0 || n_views > INT32_MAX || !valid_camera(cam) || !valid_params(params)) return NBT_EINVAL;
   if (n_views == 0) return NBT_OK;
   if (!poses || !ig_out) return NBT_EINVAL;
   cudaStream_t stream = (cudaStream_t)stream_;
@@ -1021,7 +1025,7 @@ int nbt_view_segments(nbt_map map, const nbt_pose *poses, int64_t n_views, const
                       float *d_out, void *stream_) {
   int rc = check_map(map);
   if (rc != NBT_OK) return rc;
-  if (n_views < 0 || !valid_camera(cam)) return NBT_EINVAL;
+  if (n_views < 0 || n_views > INT32_MAX || !valid_camera(cam)) return NBT_EINVAL;
   if (n_views == 0) return NBT_OK;
   if (!poses || !o_out || !d_out) return NBT_EINVAL;
   const CamConst cc = make_cam(map, cam);
@@ -1049,13 +1053,46 @@ namespace {
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+unsigned long long g_noalloc_ctx[kNoallocMaxDevices] = {0};
 
-// Device address of the scratch array on `device` (the current device),
-// looked up once per device.
+// Unique id of the calling thread's current CUDA context (0 if it cannot be
+// read).  The driver calls are looked up through the runtime, so the library
+// does not link the driver library itself.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void *a = nullptr, *b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+        qb == cudaDriverEntryPointSuccess) {
+      get_current = (GetCurrent)a;
+      get_id = (GetId)b;
+    }
+    (void)cudaGetLastError();
+    looked_up = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array on `device` (the current device).
+// Looked up once per device and context: if the device's context was torn
+// down and created again (cudaDeviceReset), the module is loaded anew and
+// the array may have moved, so a new context id triggers a new lookup.
 int noalloc_scratch(int device, void **ptr) {
   if (device < 0 || device >= kNoallocMaxDevices) return NBT_EINVAL;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[device]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_noalloc_ptr[device] || ctx == 0 || ctx != g_noalloc_ctx[device]) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, nbt_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) {
@@ -1063,6 +1100,7 @@ int noalloc_scratch(int device, void **ptr) {
       return NBT_ECUDA;
     }
     g_noalloc_ptr[device] = p;
+    g_noalloc_ctx[device] = ctx;
   }
   *ptr = g_noalloc_ptr[device];
   return NBT_OK;
@@ -1078,6 +1116,9 @@ extern "C" int nbt_views_ig_noalloc(nbt_map map, const nbt_pose *poses, int64_t 
   if (n_views < 0 || !valid_camera(cam) || !valid_params(params)) return NBT_EINVAL;
   if (n_views == 0) return NBT_OK;
   if (!poses || !ig_out) return NBT_EINVAL;
+  // bound n_views before any product: at most this many views fit the array
+  const int64_t tiles = (int64_t)((cam->width + kTileW - 1) / kTileW) * ((cam->height + kTileH - 1) / kTileH);
+  if (n_views > ((int64_t)NBT_NOALLOC_SCRATCH_BYTES - 256) / ((int64_t)kPartialBytes * tiles)) return NBT_ESCRATCH;
   int64_t need = 0;
   rc = nbt_workspace_size(n_views, cam, &need);
   if (rc != NBT_OK) return rc;
@@ -1100,7 +1141,7 @@ extern "C" int nbt_views_ig_noalloc(nbt_map map, const nbt_pose *poses, int64_t 
 }
 
 extern "C" int nbt_map_set_tuning(nbt_map map, const nbt_tuning *tuning) {
-  if (!map || !tuning) return NBT_EINVAL;
+  if (!map || !tuning || !map_alive(map, 0)) return NBT_EINVAL;
   const int pw = tuning->packet_w == 0 ? 8 : tuning->packet_w;
   if (pw != 4 && pw != 8 && pw != 16 && pw != 32) return NBT_EINVAL;
   map->packet_w = pw;
@@ -1108,7 +1149,7 @@ extern "C" int nbt_map_set_tuning(nbt_map map, const nbt_tuning *tuning) {
 }
 
 extern "C" int nbt_map_get_tuning(nbt_map map, nbt_tuning *tuning) {
-  if (!map || !tuning) return NBT_EINVAL;
+  if (!map || !tuning || !map_alive(map, 0)) return NBT_EINVAL;
   tuning->packet_w = map->packet_w;
   tuning->brick = map->brick;
   return NBT_OK;

@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 
 #include "nbt_internal.cuh"
@@ -528,7 +529,7 @@ __device__ __forceinline__ bool wait_abortable(uint64_t *bar, uint32_t par, vola
   const uint64_t t0 = tc::globaltimer();
   while (!tc::mbar_try_wait(bar, par)) {
     if (*abort) return false;
-    if (tc::globaltimer() - t0 > tc::kWaitNs) {
+    if (tc::globaltimer() - t0 > tc::c_wait_ns) {
       *abort = 1;
       return false;
     }
@@ -672,7 +673,7 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
     // before TMEM is freed: the last commit done (bounded, whatever the abort flag says)
     if (last_bar) {
       const uint64_t t0 = tc::globaltimer();
-      while (!tc::mbar_try_wait(last_bar, last_par) && tc::globaltimer() - t0 < tc::kWaitNs) {
+      while (!tc::mbar_try_wait(last_bar, last_par) && tc::globaltimer() - t0 < tc::c_wait_ns) {
       }
     }
   } else {
@@ -938,7 +939,7 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 2)
     }
     if (last_bar) {  // before TMEM is freed (bounded)
       const uint64_t t0 = tc::globaltimer();
-      while (!tc::mbar_try_wait(last_bar, last_par) && tc::globaltimer() - t0 < tc::kWaitNs) {
+      while (!tc::mbar_try_wait(last_bar, last_par) && tc::globaltimer() - t0 < tc::c_wait_ns) {
       }
     }
   } else {
@@ -1137,17 +1138,20 @@ __global__ void fc2_forward_kernel(const bf16 *__restrict__ h1, const float *__r
   if (lane == 0) y[b] = acc + params[kP.g2];
 }
 
-// Loss head (one block of 256 threads): loss = mean (y - t)^2, dy = 2 (y - t) / n;
-// grads of f2 and g2; dh1 = dy f2 [h1 > 0] (BF16, and transposed to [128][ldn]).
-__global__ void head_backward_kernel(const float *__restrict__ y, const float *__restrict__ t, const bf16 *__restrict__ h1,
-                                     const float *__restrict__ params, int n, int ldn, float *__restrict__ grads,
-                                     float *__restrict__ loss, bf16 *__restrict__ dh1, bf16 *__restrict__ dh1t) {
+// Loss head (one block of 256 threads): loss = mean (y - c t)^2 with the
+// net's target scale c (the product rounded to FP32 on its own), dy = 2 (y -
+// c t) / n; grads of f2 and g2; dh1 = dy f2 [h1 > 0] (BF16, and transposed to
+// [128][ldn]).
+__global__ void head_backward_kernel(const float *__restrict__ y, const float *__restrict__ t, float tscale,
+                                     const bf16 *__restrict__ h1, const float *__restrict__ params, int n, int ldn,
+                                     float *__restrict__ grads, float *__restrict__ loss, bf16 *__restrict__ dh1,
+                                     bf16 *__restrict__ dh1t) {
   __shared__ float red[256];
   __shared__ float s_dy[1024];
   const int tid = threadIdx.x;
   float l = 0.0f, gb = 0.0f;
   for (int b = tid; b < n; b += 256) {
-    const float e = y[b] - t[b];
+    const float e = y[b] - __fmul_rn(t[b], tscale);
     l += e * e;
     const float d = 2.0f * e / (float)n;
     gb += d;
@@ -1352,6 +1356,29 @@ __global__ void segment_argmax_kernel(const float *__restrict__ vals, const int3
   }
 }
 
+// Test kernel of the bounded waits: the CTA holds all 512 TMEM columns of
+// its SM and waits on an mbarrier that nothing ever completes, through the
+// same bounded wait as the GEMM kernels; when the wait gives up it sets the
+// error word, frees its tensor memory and returns.
+__global__ void __launch_bounds__(128) tc_wait_probe_kernel(int *err) {
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const bool ok = __syncthreads_and(tc::mbar_wait(&bar, 0)) != 0;  // phase 0 never completes
+  if (!ok && tid == 0) atomicExch(err, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem_base, 512);
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -1426,6 +1453,7 @@ struct nbt_surrogate_s {
   bf16 *x = nullptr, *xt = nullptr, *h1 = nullptr, *dh1 = nullptr, *dh1t = nullptr;
   float *y = nullptr, *loss = nullptr, *part = nullptr;
   int64_t step = 0;
+  float target_scale = 1.0f;  // training targets are multiplied by this in the loss
 };
 
 namespace {
@@ -1542,8 +1570,8 @@ int backward_batch(nbt_surrogate net, const uint8_t *crops, const bf16 *feats, c
   int rc = forward_batch(net, crops, feats, n, net->y, s);
   if (rc != NBT_OK) return rc;
   const int ldn = net->ldn;
-  head_backward_kernel<<<1, 256, 0, s>>>(net->y, targets, net->h1, net->params, n, ldn, net->grads, net->loss,
-                                         net->dh1, net->dh1t);
+  head_backward_kernel<<<1, 256, 0, s>>>(net->y, targets, net->target_scale, net->h1, net->params, n, ldn,
+                                         net->grads, net->loss, net->dh1, net->dh1t);
   NBT_CUDA_TRY(cudaGetLastError());
   // fc1: dW1 = dh1^T X, db1 = colsum(dh1), dX = dh1 F1 (ReLU mask of the flattened conv output)
   {
@@ -1827,6 +1855,51 @@ int nbt_surrogate_train_step(nbt_surrogate net, const void *crops, const void *f
   return sync_weights(net, s);
 }
 
+int nbt_surrogate_set_target_scale(nbt_surrogate net, float scale) {
+  int rc = check_net(net);
+  if (rc != NBT_OK) return rc;
+  if (!std::isfinite(scale) || !(scale > 0.0f)) return NBT_EINVAL;
+  net->target_scale = scale;
+  return NBT_OK;
+}
+
+int nbt_surrogate_get_adam(nbt_surrogate net, float *m_host, float *v_host, int64_t n, int64_t *step) {
+  int rc = check_net(net);
+  if (rc != NBT_OK) return rc;
+  if (!m_host || !v_host || !step || n != kP.total) return NBT_EINVAL;
+  NBT_CUDA_TRY(cudaDeviceSynchronize());
+  NBT_CUDA_TRY(cudaMemcpy(m_host, net->adam_m, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  NBT_CUDA_TRY(cudaMemcpy(v_host, net->adam_v, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  *step = net->step;
+  return NBT_OK;
+}
+
+int nbt_surrogate_set_adam(nbt_surrogate net, const float *m_host, const float *v_host, int64_t n, int64_t step) {
+  int rc = check_net(net);
+  if (rc != NBT_OK) return rc;
+  if (!m_host || !v_host || n != kP.total || step < 0) return NBT_EINVAL;
+  NBT_CUDA_TRY(cudaDeviceSynchronize());
+  NBT_CUDA_TRY(cudaMemcpy(net->adam_m, m_host, (size_t)n * 4, cudaMemcpyHostToDevice));
+  NBT_CUDA_TRY(cudaMemcpy(net->adam_v, v_host, (size_t)n * 4, cudaMemcpyHostToDevice));
+  net->step = step;
+  return NBT_OK;
+}
+
+int nbt_tc_set_wait_limit(uint64_t ns) {
+  if (ns < 1000ull || ns > 60000000000ull) return NBT_EINVAL;
+  NBT_CUDA_TRY(cudaMemcpyToSymbol(tc::c_wait_ns, &ns, sizeof(ns)));
+  return NBT_OK;
+}
+
+int nbt_tc_wait_probe(void *stream) {
+  int *err = nullptr;
+  int rc = dev_err_word(&err);
+  if (rc != NBT_OK) return rc;
+  tc_wait_probe_kernel<<<(unsigned)sm_count(), 128, 0, (cudaStream_t)stream>>>(err);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
 }  // extern "C"
 
 extern "C" {
@@ -1855,6 +1928,111 @@ int nbt_segment_argmax(const float *values, const int32_t *idx, int64_t n, int32
                                                                                               best_idx, best_val);
   NBT_CUDA_TRY(cudaGetLastError());
   return NBT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Surrogate-pruned next-best-view selection in one call: crops and the
+// network's score for every candidate, the keep best of each segment, the
+// exact raycast (Section III IG) of those, and the best of them per segment.
+// The exact IG judges the kept candidates, so pruning can miss the best view
+// but never reports a wrong IG.  Scratch comes from the caller's workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kCropBytes = (int64_t)kCrop * kCrop * kCrop;  // one uint8 class code per sample
+
+int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
+
+struct PrunedLayout {
+  int64_t crops, feats, scores, idx, kept, ig, ws, ws_bytes, total;
+};
+
+// Workspace regions (each 256-byte aligned): crops and features of one batch
+// of max_batch candidates, all scores, the kept indices, kept poses and
+// their exact IGs, and the raycast workspace of the kept views.
+int pruned_layout(nbt_surrogate net, int64_t n, int32_t seg, int32_t keep, const nbt_camera *cam, PrunedLayout *L) {
+  const int64_t chunk = std::min<int64_t>(n, net->max_batch);
+  const int64_t n_kept = n / seg * keep;
+  int64_t ws_bytes = 0;
+  const int rc = nbt_workspace_size(n_kept, cam, &ws_bytes);
+  if (rc != NBT_OK) return rc;
+  int64_t o = 0;
+  L->crops = o;
+  o += align256(chunk * kCropBytes);
+  L->feats = o;
+  o += align256(chunk * kFeat * 2);
+  L->scores = o;
+  o += align256(n * 4);
+  L->idx = o;
+  o += align256(n_kept * 4);
+  L->kept = o;
+  o += align256(n_kept * 28);
+  L->ig = o;
+  o += align256(n_kept * 4);
+  L->ws = o;
+  L->ws_bytes = ws_bytes;
+  L->total = o + align256(ws_bytes);
+  return NBT_OK;
+}
+
+bool pruned_shape_ok(int64_t n, int32_t seg, int32_t keep) {
+  return n >= 0 && n <= INT32_MAX && seg >= 1 && seg <= 8192 && keep >= 1 && keep <= seg && n % seg == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nbt_pruned_workspace_size(nbt_surrogate net, int64_t n, int32_t seg, int32_t keep, const nbt_camera *cam,
+                              int64_t *bytes) {
+  if (!net || !bytes || !pruned_shape_ok(n, seg, keep) || !valid_camera(cam)) return NBT_EINVAL;
+  PrunedLayout L;
+  const int rc = pruned_layout(net, n, seg, keep, cam, &L);
+  if (rc != NBT_OK) return rc;
+  *bytes = L.total;
+  return NBT_OK;
+}
+
+int nbt_plan_pruned(nbt_map map, nbt_surrogate net, const nbt_pose *poses, int64_t n, int32_t seg, int32_t keep,
+                    const nbt_camera *cam, const nbt_ig_params *params, int32_t *best_out, float *best_ig_out,
+                    int32_t *kept_out, void *workspace, int64_t workspace_bytes, void *stream) {
+  int rc = check_map(map);
+  if (rc != NBT_OK) return rc;
+  rc = check_net(net);
+  if (rc != NBT_OK) return rc;
+  if (!pruned_shape_ok(n, seg, keep) || !valid_camera(cam) || !valid_params(params)) return NBT_EINVAL;
+  if (n == 0) return NBT_OK;
+  if (!poses || !best_out) return NBT_EINVAL;
+  PayloadKind kind;
+  const void *payload = nullptr;
+  rc = payload_kind(map, params, &kind, &payload);  // NBT_EUNSUPPORTED before anything is enqueued
+  if (rc != NBT_OK) return rc;
+  PrunedLayout L;
+  rc = pruned_layout(net, n, seg, keep, cam, &L);
+  if (rc != NBT_OK) return rc;
+  if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255u)) return NBT_EWORKSPACE;
+  char *w = (char *)workspace;
+  uint8_t *crops = (uint8_t *)(w + L.crops);
+  void *feats = w + L.feats;
+  float *scores = (float *)(w + L.scores);
+  int32_t *idx = kept_out ? kept_out : (int32_t *)(w + L.idx);
+  nbt_pose *kept = (nbt_pose *)(w + L.kept);
+  float *ig = (float *)(w + L.ig);
+  const int64_t n_kept = n / seg * keep;
+  for (int64_t c0 = 0; c0 < n; c0 += net->max_batch) {
+    const int64_t nc = std::min<int64_t>(net->max_batch, n - c0);
+    rc = nbt_surrogate_crops(map, poses + c0, nc, cam, params, crops, feats, stream);
+    if (rc != NBT_OK) return rc;
+    rc = nbt_surrogate_forward(net, crops, feats, nc, scores + c0, stream);
+    if (rc != NBT_OK) return rc;
+  }
+  rc = nbt_segment_topk(scores, n, seg, keep, idx, poses, kept, stream);
+  if (rc != NBT_OK) return rc;
+  rc = nbt_views_ig(map, kept, n_kept, cam, params, ig, nullptr, w + L.ws, L.ws_bytes, stream);
+  if (rc != NBT_OK) return rc;
+  return nbt_segment_argmax(ig, idx, n_kept, keep, best_out, best_ig_out, stream);
 }
 
 }  // extern "C"

@@ -15,8 +15,9 @@
 //   - the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 //     lanes 32w .. 32w+31 = rows of the tile) and hands each row's values
 //     to an epilogue functor.
-// Every mbarrier wait is bounded (%globaltimer); on timeout the kernel sets
-// an error word, waits once more (bounded) for its MMAs and frees its TMEM.
+// Every mbarrier wait is bounded (%globaltimer, c_wait_ns); on timeout the
+// kernel sets an error word, waits once more (bounded) for its MMAs and
+// frees its TMEM.
 // The helpers below (descriptors, MMAs with A in shared or tensor memory,
 // TMEM loads and stores, bounded waits) also serve the fused surrogate
 // kernels.
@@ -39,7 +40,11 @@ namespace tc {
 constexpr int kBM = 128;        // tile rows (UMMA M)
 constexpr int kBK = 64;         // K per stage (4 MMAs of K = 16)
 constexpr int kThreads = 128;
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;  // default bound on any mbarrier wait: 2 s
+
+// The bound in use (nanoseconds of %globaltimer), per device; set by
+// nbt_tc_set_wait_limit.  This header is compiled into one translation unit.
+__constant__ uint64_t c_wait_ns = kDefaultWaitNs;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -85,7 +90,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > c_wait_ns) return false;
   }
   return true;
 }

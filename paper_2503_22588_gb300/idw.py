@@ -1,4 +1,4 @@
-"""Binding of the IG-between-perspectives entry points (Section III, Eq. 3,
+"""Binding of the IG-between-perspectives entry points (Section IV, Eq. 3,
 orientation factor, c_I): the ID buffer, G(x) and the trajectory IG cost.
 
 Argument marshalling only; the arithmetic runs in libnbt.so.

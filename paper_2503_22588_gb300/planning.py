@@ -2,12 +2,12 @@
 
 Candidates come in segments of ``seg`` perspectives (typically the views
 around one PoI).  Exact selection raycasts every candidate (Section III) and
-takes the best per segment.  Pruned selection scores every candidate with
-the learned surrogate, keeps the ``keep`` best per segment, raycasts only
-those exactly, and takes the best of them; exact raycasting judges the kept
-candidates, so a pruning mistake can only lose the best view, never report
-a wrong IG.  All arithmetic runs in the library's kernels; this module only
-sequences the calls.
+takes the best per segment.  Pruned selection (``nbt_plan_pruned``, one C
+call) scores every candidate with the learned surrogate, keeps the ``keep``
+best per segment, raycasts only those exactly, and takes the best of them;
+exact raycasting judges the kept candidates, so a pruning mistake can only
+lose the best view, never report a wrong IG.  All arithmetic runs in the
+library's kernels; this module only sequences the calls.
 """
 
 from __future__ import annotations
@@ -21,7 +21,7 @@ from ._lib import check, lib
 from .api import Camera, IgParams, Map, _dev, _stream, views_ig, workspace
 from .surrogate import Surrogate, crops as make_crops
 
-TARGET_SCALE = 100.0  # training target = mean ray IG / 100
+TARGET_SCALE = 0.01  # the network predicts g_P x 0.01 (applied to the targets in the loss kernel)
 
 
 def segment_argmax(values: torch.Tensor, seg: int, idx: torch.Tensor | None = None, stream=None):
@@ -65,21 +65,46 @@ def surrogate_scores(net: Surrogate, m: Map, poses: torch.Tensor, cam: Camera, p
     return out
 
 
+def pruned_workspace(net: Surrogate, n: int, seg: int, keep: int, cam: Camera, device=None) -> torch.Tensor:
+    """A device workspace for nbt_plan_pruned (crops of one batch, scores, kept views, raycast scratch)."""
+    b = C.c_int64()
+    check(lib().nbt_pruned_workspace_size(net.handle, int(n), int(seg), int(keep), C.byref(cam), C.byref(b)),
+          "nbt_pruned_workspace_size")
+    return torch.empty(max(b.value, 256), dtype=torch.uint8,
+                       device=device if device is not None else torch.device("cuda"))
+
+
 def pruned_best(net: Surrogate, m: Map, poses: torch.Tensor, seg: int, keep: int, cam: Camera, params: IgParams,
-                chunk: int | None = None, stream=None):
-    """Surrogate-pruned selection: (best index, its exact IG, kept indices [n/seg, keep])."""
-    scores = surrogate_scores(net, m, poses, cam, params, chunk, stream)
-    idx, kept = segment_topk(scores, seg, keep, poses, stream)
-    ig, _ = views_ig(m, kept, cam, params, stream=stream, want_steps=False)
-    best, val = segment_argmax(ig, keep, idx.reshape(-1), stream)
-    return best, val, idx
+                ws: torch.Tensor | None = None, stream=None, out=None, want_kept: bool = True):
+    """nbt_plan_pruned: (best index, its exact IG, kept indices [n/seg, keep] or None) per segment.
+
+    ``ws``: a workspace from ``pruned_workspace`` (allocated here if not given);
+    ``out``: optional preallocated (best int32 [n/seg], best IG float32 [n/seg]).
+    """
+    n = poses.shape[0]
+    nseg = n // seg if seg > 0 else 0
+    if ws is None:
+        ws = pruned_workspace(net, n, seg, keep, cam, poses.device)
+    if out is None:
+        best = torch.empty(nseg, dtype=torch.int32, device=poses.device)
+        val = torch.empty(nseg, dtype=torch.float32, device=poses.device)
+    else:
+        best, val = out
+    kept = torch.empty((nseg, keep), dtype=torch.int32, device=poses.device) if want_kept else None
+    if ws.data_ptr() % 256:
+        raise ValueError("workspace must be 256-byte aligned")
+    check(lib().nbt_plan_pruned(m.handle, net.handle, _dev(poses, torch.float32, "poses", (7,)), n, int(seg),
+                                int(keep), C.byref(cam), C.byref(params), _dev(best, torch.int32, "best"),
+                                _dev(val, torch.float32, "best_ig"), kept.data_ptr() if kept is not None else None,
+                                _dev(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)), "nbt_plan_pruned")
+    return best, val, kept
 
 
 def label_views(m: Map, poses: torch.Tensor, cam: Camera, params: IgParams, stream=None) -> torch.Tensor:
-    """Training targets: exact mean ray IG (Section III's g_P) / 100."""
+    """Training targets: exact mean ray IG (Section III's g_P); the net scales them (TARGET_SCALE)."""
     prm = IgParams(params.metric, params.occ_threshold, params.free_threshold, params.include_hit, 1)  # mean
     ig, _ = views_ig(m, poses, cam, prm, stream=stream, want_steps=False)
-    return ig / TARGET_SCALE
+    return ig
 
 
 def train(net: Surrogate, maps: list, poses: list, targets: list, cam: Camera, params: IgParams, epochs: int,

@@ -84,14 +84,42 @@ def crops(m: Map, poses: torch.Tensor, cam: Camera, params: IgParams, stream=Non
 class Surrogate:
     """nbt_surrogate: network, Adam state and activation buffers on the current device."""
 
-    def __init__(self, max_batch: int = 256, params: dict | None = None):
+    def __init__(self, max_batch: int = 256, params: dict | None = None, target_scale: float = 1.0):
         h = C.c_void_p()
         check(lib().nbt_surrogate_create(int(max_batch), C.byref(h)), "nbt_surrogate_create")
         self._h = h
         self.max_batch = int(max_batch)
         self.n_params = param_count()
+        self.target_scale = 1.0
         if params is not None:
             self.set_params(params)
+        if target_scale != 1.0:
+            self.set_target_scale(target_scale)
+
+    def set_target_scale(self, scale: float) -> None:
+        """nbt_surrogate_set_target_scale: training targets are multiplied by ``scale`` in the loss."""
+        check(lib().nbt_surrogate_set_target_scale(self.handle, float(scale)), "nbt_surrogate_set_target_scale")
+        self.target_scale = float(scale)
+
+    def checkpoint(self) -> dict:
+        """The whole training state: parameters, Adam moments, Adam step count and target scale."""
+        m = np.empty(self.n_params, np.float32)
+        v = np.empty(self.n_params, np.float32)
+        step = C.c_int64()
+        check(lib().nbt_surrogate_get_adam(self.handle, m.ctypes.data, v.ctypes.data, m.size, C.byref(step)),
+              "nbt_surrogate_get_adam")
+        return {"params": pack(self.get_params()), "adam_m": m, "adam_v": v, "step": int(step.value),
+                "target_scale": self.target_scale}
+
+    def restore(self, state: dict) -> None:
+        """Load a ``checkpoint()``: training continues from it bit for bit."""
+        flat = np.ascontiguousarray(state["params"], np.float32)
+        check(lib().nbt_surrogate_set_params(self.handle, flat.ctypes.data, flat.size), "nbt_surrogate_set_params")
+        m = np.ascontiguousarray(state["adam_m"], np.float32)
+        v = np.ascontiguousarray(state["adam_v"], np.float32)
+        check(lib().nbt_surrogate_set_adam(self.handle, m.ctypes.data, v.ctypes.data, m.size, int(state["step"])),
+              "nbt_surrogate_set_adam")
+        self.set_target_scale(state["target_scale"])
 
     @property
     def handle(self) -> int:

@@ -181,3 +181,35 @@ def test_null_handles_are_rejected_on_the_host(libnbt):
         assert getattr(L, name)(*args) == -1, name
     for name in ("nbt_map_destroy", "nbt_plan_destroy", "nbt_surrogate_destroy", "nbt_id_buffer_destroy"):
         assert getattr(L, name)(None) == 0, name
+
+
+def test_sizes_are_bounded_before_they_are_multiplied(libnbt):
+    """nbt_workspace_size takes n_poses in [0, INT32_MAX]: a huge count (whose byte size would wrap
+    around int64) is refused on the host instead of returning a wrapped, small size."""
+    from paper_2503_22588_gb300 import _lib
+    L = _lib.lib()
+    cam = libnbt.camera(1, 1, 1.0, 0.8, 1.0)
+    b = C.c_int64(-5)
+    for n in (2 ** 31, 2 ** 60, 2 ** 63 - 1):
+        assert L.nbt_workspace_size(n, C.byref(cam), C.byref(b)) == -1, n
+    assert b.value == -5
+    assert L.nbt_workspace_size(2 ** 31 - 1, C.byref(cam), C.byref(b)) == 0
+    assert b.value == 256 + (2 ** 31 - 1) * 16
+
+
+def test_handles_that_name_no_live_map_are_rejected_without_reading_them(libnbt):
+    """A map handle that was never created (or was destroyed) is checked against the live-map
+    registry before it is read: NBT_EINVAL, no GPU needed, no memory behind the pointer touched."""
+    from paper_2503_22588_gb300 import _lib
+    L = _lib.lib()
+    bogus = C.c_void_p(0x10)          # not a valid address: reading it would crash the test
+    cam = libnbt.camera(8, 8, 1.0, 0.8, 1.0)
+    prm = libnbt.ig_params("count")
+    assert L.nbt_map_destroy(bogus) == -1
+    assert L.nbt_map_info(bogus, None, None) == -1
+    assert L.nbt_views_ig(bogus, None, 1, C.byref(cam), C.byref(prm), None, None, None, 0, None) == -1
+    assert L.nbt_views_ig_noalloc(bogus, None, 1, C.byref(cam), C.byref(prm), None, None, None) == -1
+    assert L.nbt_map_upload(bogus, None, 0, 0, None) == -1
+    t = _lib.Tuning(8, 0)
+    assert L.nbt_map_set_tuning(bogus, C.byref(t)) == -1
+    assert L.nbt_map_get_tuning(bogus, C.byref(t)) == -1

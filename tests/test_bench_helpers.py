@@ -73,7 +73,7 @@ def test_reference_arm_lines(arm):
 
 def test_step_defaults_per_workload_and_explicit_flags_win():
     a = bench.parse_args([])
-    assert (a.workload, a.steps, a.warmup, a.gpus, a.impl) == ("prob256", 1000, 20, 1, "native")
+    assert (a.workload, a.steps, a.warmup, a.gpus, a.impl) == ("room512-pruned", 25, 3, 1, "native")
     assert set(bench.DEFAULT_STEPS) == set(bench.WORKLOAD_CHOICES)
     assert all(w >= 3 for _, w in bench.DEFAULT_STEPS.values())
     b = bench.parse_args(["--workload", "room512"])
@@ -81,3 +81,25 @@ def test_step_defaults_per_workload_and_explicit_flags_win():
     c = bench.parse_args(["--workload", "room512", "--steps", "7", "--warmup", "4"])
     assert (c.steps, c.warmup) == (7, 4)
     assert bench.parse_args(["--warmup", "1"]).warmup == 3        # never fewer than three warm-up steps
+
+
+def test_wilson_interval_against_closed_cases():
+    """The 95 % Wilson score interval: 39/40 gives a lower bound near 0.87 (far below a 95 % target),
+    190/200 about 0.91, and k = n has an upper bound of exactly 1; the interval contains k / n."""
+    lo, hi = bench.wilson_interval(39, 40)
+    assert abs(lo - 0.8709) < 2e-3 and hi < 1.0
+    lo, hi = bench.wilson_interval(190, 200)
+    assert abs(lo - 0.9103) < 2e-3 and lo < 0.95 < hi
+    lo, hi = bench.wilson_interval(200, 200)
+    assert hi == 1.0 and abs(lo - 0.9812) < 2e-3
+    for k, n in ((0, 10), (3, 7), (10, 10)):
+        lo, hi = bench.wilson_interval(k, n)
+        assert lo <= k / n <= hi
+
+
+def test_surrogate_flop_counts():
+    """Dense-equivalent forward: 2 x (16^3 16 216 + 8^3 32 432 + 4^3 64 864 + 4^3 64 1728) + fc; the method's
+    own count replaces layer 0's K = 216 by the K = 112 one-hot GEMM the kernels run."""
+    dense = 2 * (16 ** 3 * 16 * 216 + 8 ** 3 * 32 * 432 + 4 ** 3 * 64 * 864 + 4 ** 3 * 64 * 1728) + 2 * 4104 * 128 + 256
+    assert bench.surrogate_flops_per_view() == dense
+    assert dense - bench.surrogate_method_flops_per_view() == 2 * 16 ** 3 * 16 * (216 - 112)

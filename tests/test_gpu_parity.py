@@ -451,3 +451,24 @@ def test_autotune_returns_a_valid_fastest_config():
     ig, st = views_gpu(m, w.poses, cam, prm)
     rig, rst = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(w.camera), oracle.params("count"))
     assert np.array_equal(st, rst) and np.array_equal(ig, rig)
+
+
+def test_plan_launch_after_its_map_was_destroyed_is_refused():
+    """A plan keeps its map's handle and creation id; once the map is destroyed the launch returns
+    NBT_EINVAL and enqueues nothing, also when a new map was created in the meantime."""
+    w = configs.traj256(seed=5, n_traj=4, n=48, len_range=(2, 4))
+    w.camera = configs.Camera(16, 12)
+    gm = gpu_map(w)
+    cam = gpu_camera(w.camera)
+    pz = torch.from_numpy(w.poses).cuda()
+    off = torch.from_numpy(w.offsets).cuda()
+    plan = nbt.TrajPlan(gm, pz, off, cam, nbt.ig_params("count"))
+    plan.launch()
+    torch.cuda.synchronize()
+    gm.close()
+    others = [gpu_map(w) for _ in range(3)]    # may reuse the freed address
+    from paper_2503_22588_gb300 import _lib
+    assert _lib.lib().nbt_plan_launch(plan._h, None) == -1
+    plan.close()
+    for m in others:
+        m.close()

@@ -226,3 +226,104 @@ def test_pruned_selection_keeps_the_exact_best_when_everything_is_kept():
     bp2, vp2, kept2 = P.pruned_best(net, m, pz, 16, 3, cam, prm)
     assert kept2.shape == (4, 3) and torch.all(vp2 <= vx)
     net.close()
+
+
+def test_plan_pruned_kept_indices_are_the_top_scores_and_best_is_their_exact_argmax():
+    """nbt_plan_pruned in one call equals its steps run one by one: the kept indices are the per-segment
+    top-k of the network's scores of the crops, and the best view is the exact argmax among them."""
+    from paper_2503_22588_gb300 import planning as P
+    w = configs.exact64(seed=6, n_views=64)
+    cam = nbt.camera(32, 24, w.camera.fov_h, w.camera.fov_v, 1.0)
+    prm = nbt.ig_params("count")
+    m = nbt.Map.from_grid(torch.from_numpy(w.grid).cuda(), 0.01)
+    pz = torch.from_numpy(w.poses).cuda()
+    net = gs.Surrogate(max_batch=24, params=S.init_params(3))      # 64 candidates: three batches
+    best, val, kept = P.pruned_best(net, m, pz, 16, 5, cam, prm)
+    scores = P.surrogate_scores(net, m, pz, cam, prm)
+    idx, kp = P.segment_topk(scores, 16, 5, pz)
+    assert torch.equal(kept, idx)
+    ig, _ = nbt.views_ig(m, kp, cam, prm)
+    b2, v2 = P.segment_argmax(ig, 5, idx.reshape(-1).contiguous())
+    assert torch.equal(best, b2) and torch.equal(val, v2)
+    exact, _ = nbt.views_ig(m, pz, cam, prm)
+    assert torch.equal(val, exact[best.long()])                   # the reported IG is the exact one
+    assert no_device_timeout()
+    net.close()
+    m.close()
+
+
+def test_plan_pruned_refuses_bad_arguments_before_enqueueing():
+    from paper_2503_22588_gb300 import planning as P
+    w = configs.exact64(seed=6, n_views=32)
+    cam = nbt.camera(16, 12, w.camera.fov_h, w.camera.fov_v, 1.0)
+    m = nbt.Map.from_grid(torch.from_numpy(w.grid).cuda(), 0.01)
+    pz = torch.from_numpy(w.poses).cuda()
+    net = gs.Surrogate(max_batch=8, params=S.init_params(3))
+    ws = P.pruned_workspace(net, 32, 16, 4, cam)
+    best = torch.full((2,), -5, dtype=torch.int32, device="cuda")
+    L = _lib.lib()
+
+    def call(n=32, seg=16, keep=4, prm=nbt.ig_params("count"), ws_bytes=None, wsp=None):
+        return L.nbt_plan_pruned(m.handle, net.handle, pz.data_ptr(), n, seg, keep, C.byref(cam), C.byref(prm),
+                                 best.data_ptr(), None, None, wsp if wsp is not None else ws.data_ptr(),
+                                 ws.numel() if ws_bytes is None else ws_bytes, None)
+
+    assert call(n=30) == -1                 # not a multiple of seg
+    assert call(keep=17) == -1 and call(keep=0) == -1
+    assert call(seg=9000, n=9000) == -1
+    assert call(prm=nbt.ig_params("entropy")) == -5     # entropy on a state map: unsupported
+    assert call(ws_bytes=ws.numel() - 1) == -6          # workspace too small
+    assert call(wsp=ws.data_ptr() + 16) == -6          # not 256-byte aligned
+    torch.cuda.synchronize()
+    assert torch.all(best == -5)                        # nothing was enqueued
+    assert call() == 0
+    torch.cuda.synchronize()
+    assert torch.all(best >= 0)
+    net.close()
+    m.close()
+
+
+def test_target_scale_equals_prescaled_targets_bitwise():
+    """nbt_surrogate_set_target_scale: loss and gradients with scale c and targets t equal those with
+    scale 1 and targets c t rounded to FP32, bit for bit."""
+    cr, ft = _batch(8, seed=7)
+    params = S.init_params(5)
+    t = torch.linspace(10.0, 80.0, 8, device="cuda")
+    a = gs.Surrogate(max_batch=8, params=params, target_scale=0.01)
+    b = gs.Surrogate(max_batch=8, params=params)
+    la, ga = a.backward(cr, ft, t)
+    lb, gb = b.backward(cr, ft, (t * 0.01).contiguous())
+    torch.cuda.synchronize()
+    assert torch.equal(la, lb) and torch.equal(ga, gb)
+    a.close()
+    b.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    """N Adam steps in one go equal k steps, a checkpoint restored into a fresh network, and N - k
+    more steps: parameters, Adam moments and step count bit for bit."""
+    cr, ft = _batch(16, seed=9)
+    t = torch.rand(16, device="cuda", generator=torch.Generator(device="cuda").manual_seed(2))
+    params = S.init_params(10)
+    ref = gs.Surrogate(max_batch=16, params=params, target_scale=0.5)
+    for i in range(7):
+        ref.train_step(cr, ft, t, lr=1e-3 * (1 + i % 3))
+    a = gs.Surrogate(max_batch=16, params=params, target_scale=0.5)
+    for i in range(3):
+        a.train_step(cr, ft, t, lr=1e-3 * (1 + i % 3))
+    state = a.checkpoint()
+    assert state["step"] == 3
+    a.close()
+    b = gs.Surrogate(max_batch=16)
+    b.restore(state)
+    for i in range(3, 7):
+        b.train_step(cr, ft, t, lr=1e-3 * (1 + i % 3))
+    want, got = ref.checkpoint(), b.checkpoint()
+    assert got["step"] == want["step"] == 7
+    for k in ("params", "adam_m", "adam_v"):
+        assert np.array_equal(got[k], want[k]), k
+    # and the next predictions agree too
+    assert torch.equal(ref.forward(cr, ft), b.forward(cr, ft))
+    assert no_device_timeout()
+    ref.close()
+    b.close()

@@ -103,4 +103,14 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     assert _lib.lib().nbt_status_string(-7).startswith(b"NBT_ESCRATCH")
     assert _noalloc_call(m, poses[: n - 2], cam, nbt.ig_params("count"), out, steps) == 0
     torch.cuda.synchronize()
+    # a view count whose byte size would wrap around int64 is refused as well (bounded before any
+    # product), and nothing is enqueued: the last good results stay in place
+    before = out.clone()
+    for huge in (2 ** 31, 2 ** 60, 2 ** 63 - 1):
+        rc = _lib.lib().nbt_views_ig_noalloc(m.handle, poses.data_ptr(), huge, C.byref(cam),
+                                             C.byref(nbt.ig_params("count")), out.data_ptr(), steps.data_ptr(),
+                                             torch.cuda.current_stream().cuda_stream)
+        assert rc == -7, huge
+    torch.cuda.synchronize()
+    assert torch.equal(out, before)
     m.close()
