@@ -169,9 +169,17 @@ def cpu_baseline(w, budget_s: float = 12.0) -> dict:
     t0 = time.perf_counter()
     _, st = oracle.views_ig(m, w.poses[:n], cam, prm, "f32", threads)
     dt = time.perf_counter() - t0
+    # one thread as well: the paper's CPU version was sequential
+    n1 = int(max(1, min(w.n_poses, 0.5 * budget_s / max(t_cal / n_cal * threads, 1e-6))))
+    t0 = time.perf_counter()
+    _, st1 = oracle.views_ig(m, w.poses[:n1], cam, prm, "f32", 1)
+    dt1 = time.perf_counter() - t0
     return {"value": n / dt, "unit": "views/s", "cores": threads, "kind": "oracle",
             "sample": f"first {n} of {w.n_poses} views of the same workload ({int(st.sum())} voxel steps)",
-            "voxel_steps_per_s": float(st.sum()) / dt}
+            "voxel_steps_per_s": float(st.sum()) / dt,
+            "single_thread": {"value": n1 / dt1, "unit": "views/s", "cores": 1,
+                              "sample": f"first {n1} views ({int(st1.sum())} voxel steps)",
+                              "voxel_steps_per_s": float(st1.sum()) / dt1}}
 
 
 def traj_cpu_baseline(w, budget_s: float = 12.0) -> dict:
@@ -413,6 +421,14 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="room512-pruned", choices=WORKLOAD_CHOICES)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip", type=int, default=None, choices=[0, 1],
+                    help="state-map count walks: skip uniform 8^3 bricks (1) or not (0); default: the library's")
+    ap.add_argument("--views", type=int, default=None,
+                    help="view workloads: only the first N views (a reduced launch, for profiling)")
+    ap.add_argument("--train-epochs", type=int, default=12,
+                    help="room512-pruned: surrogate training epochs before timing (0: untrained, for profiling)")
+    ap.add_argument("--scenes", type=int, default=PRUNED_MIN_SCENES,
+                    help="room512-pruned: scenes scored for the same-best-view rate (at least the timed steps)")
     args = ap.parse_args(argv)
     steps, warmup = DEFAULT_STEPS[args.workload]
     args.steps = steps if args.steps is None else args.steps
@@ -460,11 +476,15 @@ def main() -> None:
     if w.offsets is not None:
         run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist)
         return
+    if args.views is not None:   # a reduced launch of the same workload (profiling)
+        w.poses = np.ascontiguousarray(w.poses[:args.views])
     cam = nbt.camera(w.camera.width, w.camera.height, w.camera.fov_h, w.camera.fov_v, w.camera.max_range)
     prm = nbt.ig_params(w.metric)
     grid_dev = torch.from_numpy(np.ascontiguousarray(w.grid)).to(dev)
     poses_dev = torch.from_numpy(w.poses).to(dev)
     m = nbt.Map(w.n, w.n, w.n, w.voxel_size, w.origin, w.encoding)
+    if args.skip is not None:
+        m.set_tuning(8, skip=bool(args.skip))
     ws = nbt.workspace(w.n_poses, cam, dev)
     ig = torch.empty(w.n_poses, dtype=torch.float32, device=dev)
     steps = torch.empty(w.n_poses, dtype=torch.int64, device=dev)
@@ -551,7 +571,8 @@ def main() -> None:
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": describe(w), "views_per_gpu": w.n_poses, "rays_per_view": w.rays_per_pose,
+        "config": {"workload": describe(w) + (f" (reduced: first {w.n_poses} views)" if args.views else ""),
+                   "views_per_gpu": w.n_poses, "rays_per_view": w.rays_per_pose,
                    "map": f"{w.n}^3 {w.encoding}", "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "step": "map upload+gain derivation + views_ig (tile kernel + reduce)"},
@@ -589,7 +610,7 @@ def run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist) -> None
     poses_dev = torch.from_numpy(w.poses).to(dev)
     off_dev = torch.from_numpy(w.offsets).to(dev)
     m, tuned, _ = nbt.autotune(grid_dev, w.voxel_size, w.origin, w.encoding, poses_dev, cam, prm, offsets=off_dev,
-                               reps=2)
+                               skips=(0, 1), reps=2)
     _, st = nbt.views_ig(m, poses_dev, cam, prm)
     n_steps_voxel = int(st.sum().item())
     plan = nbt.TrajPlan(m, poses_dev, off_dev, cam, prm)
@@ -1150,7 +1171,7 @@ def room_scenes(seeds, workers: int):
         return list(ex.map(configs.room512, seeds))
 
 
-def train_room_surrogate(nbt, torch, dev, cam, prm, log=None):
+def train_room_surrogate(nbt, torch, dev, cam, prm, epochs: int = 12, log=None):
     """The surrogate trained inside the run on exact labels (mean ray IG) of 24 seeded 256^3 rooms."""
     from paper_2503_22588_gb300 import planning as P, surrogate as gs
     from workload import poses as wp, scenes
@@ -1167,13 +1188,13 @@ def train_room_surrogate(nbt, torch, dev, cam, prm, log=None):
         targets.append(P.label_views(m, pt, cam, prm))
     net = gs.Surrogate(max_batch=4096, params=gs.he_init(0), target_scale=P.TARGET_SCALE)
     t0 = time.perf_counter()
-    losses = P.train(net, maps, poses, targets, cam, prm, epochs=12, lr=1e-3, batch=256, log=log)
+    losses = P.train(net, maps, poses, targets, cam, prm, epochs=epochs, lr=1e-3, batch=256, log=log)
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
     for m in maps:
         m.close()
-    return net, {"seconds": train_s, "final_loss": losses[-1], "samples": 24 * 8 * 1024, "epochs": 12,
-                 "target": "mean ray IG x 0.01 (scale applied in the loss kernel)"}
+    return net, {"seconds": train_s, "final_loss": losses[-1] if losses else None, "samples": 24 * 8 * 1024,
+                 "epochs": epochs, "target": "mean ray IG x 0.01 (scale applied in the loss kernel)"}
 
 
 def pruned_cpu_baseline(w, budget_s: float = 12.0, single_s: float = 6.0) -> dict:
@@ -1219,17 +1240,19 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
     prm = nbt.ig_params("count")
     seg, keep = PRUNED_SEG, PRUNED_KEEP
     stream = torch.cuda.current_stream(dev)
-    n_eval = max(PRUNED_MIN_SCENES, args.steps)
+    n_eval = max(args.scenes, args.steps)
     seeds = [1000 * rank + k for k in range(n_eval)]
     t0 = time.perf_counter()
     scenes_w = room_scenes(seeds, min(8, os.cpu_count() or 1))
     gen_s = time.perf_counter() - t0
-    net, train_info = train_room_surrogate(nbt, torch, dev, cam, prm)
+    net, train_info = train_room_surrogate(nbt, torch, dev, cam, prm, args.train_epochs)
     n_views = scenes_w[0].n_poses
     nseg = n_views // seg
     grids = [torch.from_numpy(np.ascontiguousarray(w.grid)).to(dev) for w in scenes_w]
     poses = [torch.from_numpy(w.poses).to(dev) for w in scenes_w]
     m = nbt.Map(512, 512, 512, 0.01, (0.0, 0.0, 0.0), "u2")
+    if args.skip is not None:
+        m.set_tuning(8, skip=bool(args.skip))
     ws_exact = nbt.workspace(n_views, cam, dev)
     ws_pruned = P.pruned_workspace(net, n_views, seg, keep, cam, dev)
     ig_all = torch.empty(n_views, dtype=torch.float32, device=dev)

@@ -309,12 +309,17 @@ int nbt_plan_destroy(nbt_plan plan);
 /* Launch tuning of the IG kernels for one map (chosen by the autotuner in
  * the Python package).  packet_w: width of a warp's ray packet in pixels,
  * 4, 8, 16 or 32 (height 32 / packet_w; 0 = default 8).  brick: read-only
- * in nbt_map_get_tuning (the brick edge is fixed at nbt_map_create).  Only
- * speed changes: every setting visits the same voxels and returns the same
- * per-ray sums (per-perspective sums may differ in FP32 rounding order). */
+ * in nbt_map_get_tuning (the brick edge is fixed at nbt_map_create).
+ * skip: 1 lets unknown-count walks on linear state maps (1-byte and 2-bit)
+ * replace the voxel-by-voxel walk through 8^3 bricks whose voxels are all
+ * unknown or all free by per-axis crossing counts (used by calls with
+ * enough rays to fill the GPU; default 0).  Only speed changes: every
+ * setting visits the same voxels and returns the same per-ray sums
+ * (per-perspective sums may differ in FP32 rounding order). */
 typedef struct {
   int32_t packet_w;
   int32_t brick;
+  int32_t skip;
 } nbt_tuning;
 
 /* Set / read a map's kernel tuning.  Errors: NBT_EINVAL. */

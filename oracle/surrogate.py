@@ -207,27 +207,36 @@ def forward(params, crops, feats, layers=LAYERS, bf16_activations=False):
     return y, {"acts": acts, "X": X, "h": h}
 
 
-def loss_and_grads(params, crops, feats, targets, layers=LAYERS, bf16_activations=False):
-    """MSE loss and the gradient of every parameter (dict like ``params``)."""
+def loss_and_grads(params, crops, feats, targets, layers=LAYERS, bf16_activations=False, target_scale=1.0):
+    """MSE loss and the gradient of every parameter (dict like ``params``).
+
+    The loss is mean (y - c t)^2 with the target scale c.  With ``bf16_activations`` the
+    quantities the GPU stores in BF16 are rounded to BF16 here too: the forward activations
+    (see ``forward``), and in the backward pass the hidden-layer gradient dh and the gradient
+    with respect to every convolution's input after its ReLU mask (each computed in full
+    precision, then rounded once), so that the remaining differences are those of FP32 versus
+    FP64 accumulation.
+    """
+    rnd = _bf16 if bf16_activations else (lambda a: np.asarray(a, np.float64))
     y, c = forward(params, crops, feats, layers, bf16_activations)
     n = len(y)
-    t = np.asarray(targets, np.float64)
+    t = np.asarray(targets, np.float64) * float(target_scale)
     loss = float(np.mean((y - t) ** 2))
     dy = 2.0 * (y - t) / n
     g = {"g2": np.array([dy.sum()]), "f2": c["h"].T @ dy}
-    dh = np.outer(dy, np.asarray(params["f2"], np.float64)) * (c["h"] > 0)
+    dh = rnd(np.outer(dy, np.asarray(params["f2"], np.float64)) * (c["h"] > 0))
     g["f1"] = dh.T @ c["X"]
     g["g1"] = dh.sum(axis=0)
     dX = dh @ np.asarray(params["f1"], np.float64)
     acts = c["acts"]
-    da = dX[:, :acts[-1][0].size].reshape(acts[-1].shape) * (acts[-1] > 0)
+    da = rnd(dX[:, :acts[-1][0].size].reshape(acts[-1].shape) * (acts[-1] > 0))
     for i in range(len(layers) - 1, -1, -1):
         cin, cout, s = layers[i]
         dxin, dw, db = conv3d_backward(acts[i], np.asarray(params[f"w{i}"], np.float64), da, s)
         g[f"w{i}"] = dw
         g[f"b{i}"] = db
         if i > 0:
-            da = dxin * (acts[i] > 0)
+            da = rnd(dxin * (acts[i] > 0))
     return loss, g
 
 

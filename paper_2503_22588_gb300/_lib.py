@@ -38,7 +38,7 @@ class Camera(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("packet_w", C.c_int32), ("brick", C.c_int32)]
+    _fields_ = [("packet_w", C.c_int32), ("brick", C.c_int32), ("skip", C.c_int32)]
 
 
 class IgParams(C.Structure):

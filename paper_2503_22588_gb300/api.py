@@ -139,14 +139,16 @@ class Map:
         check(lib().nbt_map_insert_points(self.handle, _dev(points, torch.float32, "points", (3,)) if n else None, n,
                                           s, C.byref(prm), st, _stream(stream)), "nbt_map_insert_points")
 
-    def set_tuning(self, packet_w: int = 8) -> None:
-        """nbt_map_set_tuning: warp ray-packet width (4, 8, 16 or 32 pixels)."""
-        check(lib().nbt_map_set_tuning(self.handle, C.byref(Tuning(int(packet_w), 0))), "nbt_map_set_tuning")
+    def set_tuning(self, packet_w: int = 8, skip: bool | None = None) -> None:
+        """nbt_map_set_tuning: warp ray-packet width (4, 8, 16 or 32 pixels); ``skip``: count walks on
+        linear state maps skip uniform 8^3 bricks (None keeps the current setting)."""
+        sk = self.tuning()["skip"] if skip is None else int(bool(skip))
+        check(lib().nbt_map_set_tuning(self.handle, C.byref(Tuning(int(packet_w), 0, sk))), "nbt_map_set_tuning")
 
     def tuning(self) -> dict:
         t = Tuning()
         check(lib().nbt_map_get_tuning(self.handle, C.byref(t)), "nbt_map_get_tuning")
-        return {"packet_w": t.packet_w, "brick": t.brick}
+        return {"packet_w": t.packet_w, "brick": t.brick, "skip": t.skip}
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:

@@ -31,10 +31,11 @@ def _time(fn, reps: int, stream) -> float:
 
 
 def autotune(grid, voxel_size: float, origin, encoding: str, poses: torch.Tensor, cam: Camera, params: IgParams,
-             offsets: torch.Tensor | None = None, layouts=LAYOUTS, packets=PACKETS, reps: int = 5):
-    """Return (best Map, {"brick", "packet_w", "ms"}, {(brick, packet_w): ms}).
+             offsets: torch.Tensor | None = None, layouts=LAYOUTS, packets=PACKETS, skips=(0,), reps: int = 5):
+    """Return (best Map, {"brick", "packet_w", "skip", "ms"}, {(brick, packet_w, skip): ms}).
 
-    ``grid`` is the dense (nz, ny, nx) map (CUDA tensor or numpy).  The maps
+    ``grid`` is the dense (nz, ny, nx) map (CUDA tensor or numpy).  ``skips``:
+    brick skipping off / on (it applies to linear state maps only).  The maps
     built for the other layouts are closed before returning.
     """
     stream = torch.cuda.current_stream()
@@ -43,18 +44,20 @@ def autotune(grid, voxel_size: float, origin, encoding: str, poses: torch.Tensor
     out = torch.empty(n if offsets is None else offsets.shape[0] - 1, dtype=torch.float32, device=poses.device)
     maps = {brick: Map.from_grid(grid, voxel_size, origin, encoding, brick) for brick in layouts}
     timings = {}
+    state_map = encoding != "f32"
     for brick, m in maps.items():
         for pw in packets:
-            m.set_tuning(pw)
-            if offsets is None:
-                fn = lambda: views_ig(m, poses, cam, params, out, None, ws, stream, want_steps=False)  # noqa: E731
-            else:
-                fn = lambda: traj_ig(m, poses, offsets, cam, params, out, None, ws, stream)  # noqa: E731
-            timings[(brick, pw)] = _time(fn, reps, stream)
-    (brick, pw), ms = min(timings.items(), key=lambda kv: kv[1])
+            for sk in (skips if state_map and brick == 1 else (0,)):
+                m.set_tuning(pw, sk)
+                if offsets is None:
+                    fn = lambda: views_ig(m, poses, cam, params, out, None, ws, stream, want_steps=False)  # noqa: E731
+                else:
+                    fn = lambda: traj_ig(m, poses, offsets, cam, params, out, None, ws, stream)  # noqa: E731
+                timings[(brick, pw, sk)] = _time(fn, reps, stream)
+    (brick, pw, sk), ms = min(timings.items(), key=lambda kv: kv[1])
     for b, m in maps.items():
         if b != brick:
             m.close()
     best = maps[brick]
-    best.set_tuning(pw)
-    return best, {"brick": brick, "packet_w": pw, "ms": ms}, timings
+    best.set_tuning(pw, sk)
+    return best, {"brick": brick, "packet_w": pw, "skip": sk, "ms": ms}, timings

@@ -50,6 +50,7 @@ struct nbt_map_s {
   int device = 0;
   int brick = 8;
   int packet_w = 8;                  // warp ray packet width (nbt_map_set_tuning)
+  int skip = 0;                      // 1: count walks skip uniform bricks (nbt_map_set_tuning)
   int nbx = 0, nby = 0, nbz = 0;     // bricks per axis
   int64_t elems = 0;                 // padded element count of the bricked payload
   int64_t payload_bytes = 0;
@@ -65,6 +66,12 @@ struct nbt_map_s {
   int gain_metric = -1;
   float gain_occ = 0.0f, gain_free = 0.0f;
   uint64_t gain_version = 0;
+  // brick summaries of linear state maps (count walks skip uniform bricks):
+  // one byte per kSkipB^3 brick, derived from the payload, rebuilt when stale
+  uint8_t *d_bsum = nullptr;
+  int bsx = 0, bsy = 0, bsz = 0;     // summary bricks per axis
+  bool bsum_valid = false;
+  uint64_t bsum_version = 0;
   // point-cloud insertion scratch (nbt_map_insert_points), allocated on first use
   uint32_t *ins_hit = nullptr;       // hit bitmap, one bit per voxel, zero between calls
   uint32_t *ins_miss = nullptr;      // miss bitmap, likewise
@@ -78,11 +85,21 @@ struct nbt_map_s {
 
 namespace nbt {
 
+// Brick summaries (count walks on linear state maps): the map is cut into
+// kSkipB^3 bricks aligned to the origin; a brick's byte says whether every
+// voxel of it inside the map is unknown (kSumUnknown), every one is free
+// (kSumFree), or neither (kSumOther: mixed, or holding an occupied voxel).
+constexpr int kSkipLog = 3;
+constexpr int kSkipB = 1 << kSkipLog;
+constexpr uint32_t kSumUnknown = 0, kSumFree = 1, kSumOther = 3;
+
 // Map view passed to kernels by value.
 struct DevMap {
   const void *payload;
   const int32_t *tab;
   int nx, ny, nz;
+  const uint8_t *bsum;               // brick summaries (count walks), else null
+  int bsx, bsy;                      // summary bricks along x and y
 };
 
 // Per-call camera constants (Section III endpoint grid), computed on the host.
@@ -456,6 +473,7 @@ int check_map(nbt_map map);                 // NBT_EINVAL unless a live map on t
 bool map_alive(nbt_map map, uint64_t id);   // live, and (id != 0) created with that id
 void free_map(nbt_map map);                 // release a map's memory (no registry update)
 int prepare_gain(nbt_map map, const nbt_ig_params *params, cudaStream_t stream);
+int prepare_bsum(nbt_map map, cudaStream_t stream);  // (re)build the brick summaries of a linear state map
 int payload_kind(nbt_map map, const nbt_ig_params *params, PayloadKind *kind, const void **payload);
 int sm_count();
 int ensure_insert_scratch(nbt_map map, int64_t n_points);  // defined in nbt_insert.cu

@@ -177,6 +177,38 @@ __global__ void derive_gain_kernel(const float *__restrict__ p, float *__restric
   }
 }
 
+// Brick summaries of a linear state map (one thread per kSkipB^3 brick):
+// the class (0 unknown, 1 free, 2 occupied) of every voxel of the brick that
+// lies inside the map; kSumUnknown / kSumFree if all equal, else kSumOther.
+template <int ENC>
+__global__ void brick_summary_kernel(const uint8_t *__restrict__ payload, int nx, int ny, int nz, int bsx, int bsy,
+                                     int bsz, uint8_t *__restrict__ bsum) {
+  const int64_t nb = (int64_t)bsx * bsy * bsz;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    const int x0 = (int)(b % bsx) * kSkipB;
+    const int y0 = (int)((b / bsx) % bsy) * kSkipB;
+    const int z0 = (int)(b / ((int64_t)bsx * bsy)) * kSkipB;
+    const int x1 = min(x0 + kSkipB, nx), y1 = min(y0 + kSkipB, ny), z1 = min(z0 + kSkipB, nz);
+    uint32_t first = 4u;
+    bool uniform = true;
+    for (int z = z0; z < z1 && uniform; ++z)
+      for (int y = y0; y < y1 && uniform; ++y) {
+        const int64_t row = ((int64_t)z * ny + y) * nx;
+        for (int x = x0; x < x1; ++x) {
+          const int64_t v = row + x;
+          uint32_t st = ENC == NBT_U2_STATE ? (payload[v >> 2] >> ((v & 3) << 1)) & 3u : payload[v];
+          st = st > 2u ? 2u : st;
+          if (first == 4u) first = st;
+          if (st != first || st == 2u) {
+            uniform = false;
+            break;
+          }
+        }
+      }
+    bsum[b] = (uint8_t)(uniform ? first : kSumOther);
+  }
+}
+
 int grid_for(int64_t n) {
   const int64_t blocks = (n + 255) / 256;
   return (int)std::min<int64_t>(std::max<int64_t>(blocks, 1), (int64_t)sm_count() * 16);
@@ -247,6 +279,25 @@ int prepare_gain(nbt_map map, const nbt_ig_params *prm, cudaStream_t stream) {
   map->gain_occ = prm->occ_threshold;
   map->gain_free = prm->free_threshold;
   map->gain_version = map->version;
+  return NBT_OK;
+}
+
+int prepare_bsum(nbt_map map, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lock(map->mu);
+  if (!map->d_bsum) return NBT_OK;
+  if (map->bsum_valid && map->bsum_version == map->version) return NBT_OK;
+  const nbt_map_desc &d = map->desc;
+  const int64_t nb = (int64_t)map->bsx * map->bsy * map->bsz;
+  const uint8_t *p = (const uint8_t *)map->d_payload;
+  if (d.encoding == NBT_U2_STATE)
+    brick_summary_kernel<NBT_U2_STATE><<<grid_for(nb), 256, 0, stream>>>(p, d.nx, d.ny, d.nz, map->bsx, map->bsy,
+                                                                         map->bsz, map->d_bsum);
+  else
+    brick_summary_kernel<NBT_U8_STATE><<<grid_for(nb), 256, 0, stream>>>(p, d.nx, d.ny, d.nz, map->bsx, map->bsy,
+                                                                         map->bsz, map->d_bsum);
+  NBT_CUDA_TRY(cudaGetLastError());
+  map->bsum_valid = true;
+  map->bsum_version = map->version;
   return NBT_OK;
 }
 
@@ -359,6 +410,12 @@ int nbt_map_create(const nbt_map_desc *desc, nbt_map *out) {
     rc = NBT_ENOMEM;
   if (rc == NBT_OK && cudaMalloc((void **)&m->d_tab, tab.size() * sizeof(int32_t)) != cudaSuccess) rc = NBT_ENOMEM;
   if (rc == NBT_OK && cudaMalloc(&m->d_stage, (size_t)m->stage_bytes) != cudaSuccess) rc = NBT_ENOMEM;
+  if (rc == NBT_OK && brick == 1 && d.encoding != NBT_F32_PROB) {
+    m->bsx = (d.nx + kSkipB - 1) / kSkipB;
+    m->bsy = (d.ny + kSkipB - 1) / kSkipB;
+    m->bsz = (d.nz + kSkipB - 1) / kSkipB;
+    if (cudaMalloc((void **)&m->d_bsum, (size_t)m->bsx * m->bsy * m->bsz) != cudaSuccess) rc = NBT_ENOMEM;
+  }
   if (rc == NBT_OK && cudaMemset(m->d_payload, 0, (size_t)m->payload_bytes) != cudaSuccess) rc = NBT_ECUDA;
   if (rc == NBT_OK && cudaMemcpy(m->d_tab, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
                           cudaSuccess)
@@ -393,6 +450,7 @@ void free_map(nbt_map map) {
   if (map->d_gain) cudaFree(map->d_gain);
   if (map->d_tab) cudaFree(map->d_tab);
   if (map->d_stage) cudaFree(map->d_stage);
+  if (map->d_bsum) cudaFree(map->d_bsum);
   if (map->ins_hit) cudaFree(map->ins_hit);
   if (map->ins_miss) cudaFree(map->ins_miss);
   if (map->ins_count) cudaFree(map->ins_count);
@@ -472,6 +530,7 @@ int nbt_map_info(nbt_map map, nbt_map_desc *desc, int64_t *device_bytes) {
   if (device_bytes) {
     int64_t b = map->payload_bytes + (int64_t)(map->desc.nx + map->desc.ny + map->desc.nz) * 4 + map->stage_bytes;
     if (map->d_gain) b += map->elems * 4;
+    if (map->d_bsum) b += (int64_t)map->bsx * map->bsy * map->bsz;
     *device_bytes = b;
   }
   return NBT_OK;

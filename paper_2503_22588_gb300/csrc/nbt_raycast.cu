@@ -90,6 +90,9 @@ DevMap dev_map(nbt_map map, const void *payload) {
   m.nx = map->desc.nx;
   m.ny = map->desc.ny;
   m.nz = map->desc.nz;
+  m.bsum = map->d_bsum;
+  m.bsx = map->bsx;
+  m.bsy = map->bsy;
   return m;
 }
 
@@ -288,6 +291,219 @@ __device__ __forceinline__ void walk_count(Walk &w, int &lin, uint32_t raw, uint
 }
 #undef NBT_WALK_PART
 
+// ---------------------------------------------------------------------------
+// Count walks that skip uniform bricks (linear 1-byte and 2-bit state maps).
+//
+// The walk takes plane crossings in (t, axis) order, and on each axis the
+// crossing parameters t_a(k) = ((b_a + k s_a) - o_a) (1/d_a), each operation
+// rounded, do not decrease with k.  So the state after every crossing that
+// comes before a key (T, A) is known from per-axis counts alone: axis a has
+// taken the crossings with t_a(k) < T, or t_a(k) == T when a < A (the x-y-z
+// tie-break).  Inside a brick whose voxels are all unknown or all free (brick
+// summary), nothing depends on the voxels' values, so the walk through it is
+// replaced by those counts: with (T, A) the first crossing of the brick's
+// boundary (or t_max if the walk ends inside), the brick contributes
+// 1 + sum_a c_a visited voxels (each crossing enters one new voxel), all
+// unknown or none, and the walk continues from the state after them -- the
+// same voxels, the same counts and the same final state as stepping voxel
+// by voxel.  A warp takes such a macro step only when all its active lanes
+// sit in uniform bricks; otherwise every lane walks voxel by voxel (the PTX
+// loop of walk_count, with the brick exit as an extra limit) up to the exit
+// of its current brick, so the lanes stay converged.
+// ---------------------------------------------------------------------------
+
+// Crossings k of one axis that come before the key: t(k) < T, or t(k) == T
+// when tie; the answer lies in [0, kmax].  A real-arithmetic estimate from
+// the current crossing t0 and |d| is corrected by exact evaluations, which
+// are monotone in k, so the result does not depend on the estimate.
+__device__ __forceinline__ int skip_axis_count(float b, float s, float o, float v, float ad, float t0, float T,
+                                               bool tie, int kmax) {
+  auto before = [&](int k) {
+    const float t = fmul(fsub(fadd(b, (float)k * s), o), v);
+    return t < T || (tie && t == T);
+  };
+  const float e = ceilf((T - t0) * ad);
+  int c = e > 0.0f ? (e < (float)kmax ? (int)e : kmax) : 0;
+  while (c > 0 && !before(c - 1)) --c;
+  while (c < kmax && before(c)) ++c;
+  return c;
+}
+
+// The walk_count loop from the current voxel (payload entry raw, already
+// loaded) up to the first occupied voxel or the first crossing not before
+// tlim.  The walk state ends one crossing past the last visited voxel (so the
+// plane travel is the number visited); last = state of the last visited
+// voxel, ts_out = the crossing the loop stopped on.
+template <int KIND>
+__device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, uint32_t addr, const uint8_t *payload,
+                                               uint32_t addr_max, float tlim, uint32_t &iacc, uint32_t &last,
+                                               float &ts_out) {
+#define NBT_RUN_PART                                                                             \
+  "min.f32 ts, %0, %1, %2;\n\t"                                                                 \
+  "setp.geu.f32 pm, ts, %20;\n\t"                                                               \
+  "setp.eq.f32 px, %0, ts;\n\t"                                                                 \
+  "setp.eq.and.f32 py, %1, ts, !px;\n\t"                                                        \
+  "setp.neu.and.f32 pz, %1, ts, !px;\n\t"                                                       \
+  "@px add.rn.f32 %3, %3, %11;\n\t"                                                             \
+  "@px sub.rn.f32 u, %3, %14;\n\t"                                                              \
+  "@px mul.rn.f32 %0, u, %17;\n\t"                                                              \
+  "@px mad.lo.s32 %6, %21, %26, %6;\n\t"                                                        \
+  "@py add.rn.f32 %4, %4, %12;\n\t"                                                             \
+  "@py sub.rn.f32 u, %4, %15;\n\t"                                                              \
+  "@py mul.rn.f32 %1, u, %18;\n\t"                                                              \
+  "@py mad.lo.s32 %6, %22, %26, %6;\n\t"                                                        \
+  "@pz add.rn.f32 %5, %5, %13;\n\t"                                                             \
+  "@pz sub.rn.f32 u, %5, %16;\n\t"                                                              \
+  "@pz mul.rn.f32 %2, u, %19;\n\t"                                                              \
+  "@pz mad.lo.s32 %6, %23, %26, %6;\n\t"                                                        \
+  "min.u32 lc, %6, %25;\n\t"
+  const int unit = c_unit, two = unit + unit;
+  if constexpr (KIND == PAYLOAD_U8) {
+#define NBT_U8_RUN(CUR, NXT)                                                                     \
+  NBT_RUN_PART                                                                                   \
+  "mad.wide.u32 a, lc, %26, %24;\n\t"                                                           \
+  "@!pm ld.global.nc.u8 " NXT ", [a];\n\t"                                                      \
+  "setp.eq.u32 pu, " CUR ", 0;\n\t"                                                             \
+  "@pu mad.lo.s32 %7, %26, %26, %7;\n\t"                                                        \
+  "setp.gt.or.u32 pe, " CUR ", 1, pm;\n\t"
+    asm volatile(
+        "{\n\t"
+        ".reg .pred px, py, pz, pm, pu, pe;\n\t"
+        ".reg .f32 ts, u;\n\t"
+        ".reg .b32 r0, r1, r2, lc;\n\t"
+        ".reg .b64 a;\n\t"
+        "mov.b32 r0, %10;\n\t"
+        "LOOP:\n\t" NBT_U8_RUN("r0", "r1") "@pe bra D0;\n\t"
+        NBT_U8_RUN("r1", "r2") "@pe bra D1;\n\t"
+        NBT_U8_RUN("r2", "r0") "@!pe bra LOOP;\n\t"
+        "mov.b32 %8, r2;\n\t"
+        "bra DONE;\n\t"
+        "D0:\n\t"
+        "mov.b32 %8, r0;\n\t"
+        "bra DONE;\n\t"
+        "D1:\n\t"
+        "mov.b32 %8, r1;\n\t"
+        "DONE:\n\t"
+        "mov.f32 %9, ts;\n\t"
+        "}"
+        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+r"(iacc),
+          "=r"(last), "=f"(ts_out)
+        : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
+          "f"(w.vz), "f"(tlim), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit)
+        : "memory");
+#undef NBT_U8_RUN
+  } else {
+#define NBT_U2_RUN(CUR, SC, NXT, SN)                                                             \
+  NBT_RUN_PART                                                                                   \
+  "shr.u32 wb, lc, 2;\n\t"                                                                       \
+  "mad.wide.u32 a, wb, %26, %24;\n\t"                                                           \
+  "@!pm ld.global.nc.u8 " NXT ", [a];\n\t"                                                      \
+  "mad.lo.s32 " SN ", lc, %27, 0;\n\t"                                                          \
+  "mul.lo.u32 st, " CUR ", 16843009;\n\t"                                                       \
+  "shf.r.wrap.b32 st, st, st, " SC ";\n\t"                                                      \
+  "and.b32 st, st, 3;\n\t"                                                                      \
+  "setp.eq.u32 pu, st, 0;\n\t"                                                                  \
+  "@pu mad.lo.s32 %7, %26, %26, %7;\n\t"                                                        \
+  "setp.gt.or.u32 pe, st, 1, pm;\n\t"
+    const uint32_t s_first = addr * 2u;
+    asm volatile(
+        "{\n\t"
+        ".reg .pred px, py, pz, pm, pu, pe;\n\t"
+        ".reg .f32 ts, u;\n\t"
+        ".reg .b32 r0, r1, r2, s0, s1, s2, lc, wb, st;\n\t"
+        ".reg .b64 a;\n\t"
+        "mov.b32 r0, %10;\n\t"
+        "mov.b32 s0, %28;\n\t"
+        "LOOP:\n\t" NBT_U2_RUN("r0", "s0", "r1", "s1") "@pe bra DONE;\n\t"
+        NBT_U2_RUN("r1", "s1", "r2", "s2") "@pe bra DONE;\n\t"
+        NBT_U2_RUN("r2", "s2", "r0", "s0") "@!pe bra LOOP;\n\t"
+        "DONE:\n\t"
+        "mov.b32 %8, st;\n\t"
+        "mov.f32 %9, ts;\n\t"
+        "}"
+        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+r"(iacc),
+          "=r"(last), "=f"(ts_out)
+        : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
+          "f"(w.vz), "f"(tlim), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit),
+          "r"(two), "r"(s_first)
+        : "memory");
+#undef NBT_U2_RUN
+  }
+#undef NBT_RUN_PART
+}
+
+// Unknown count and visited voxels of one ray on a linear state map, skipping
+// uniform bricks (see above).  Called by all 32 lanes of a warp together
+// (valid = the lane has a ray); per-ray results equal ray_ig's exactly.
+template <int KIND>
+__device__ __forceinline__ void ray_count_skip(const DevMap &m, uint32_t addr_max, const float o[3], const float d[3],
+                                               bool valid, uint32_t &iacc, uint32_t &steps) {
+  Walk w;
+  bool done = !valid || !walk_init(w, o, d, m.nx, m.ny, m.nz);
+  int lin = 0;
+  float adx = 0.0f, ady = 0.0f, adz = 0.0f;
+  if (!done) {
+    walk_linear_steps(w, m.nx, m.ny);
+    lin = walk_linear_index(w, m.nx, m.ny);
+    adx = fabsf(d[0]);
+    ady = fabsf(d[1]);
+    adz = fabsf(d[2]);
+  }
+  const uint8_t *payload = (const uint8_t *)m.payload;
+  constexpr int kMask = kSkipB - 1;
+  while (__any_sync(0xffffffffu, !done)) {
+    int ix = 0, iy = 0, iz = 0;
+    uint32_t sum = kSumOther;
+    if (!done) {
+      ix = walk_index(w.bx, w.sx);
+      iy = walk_index(w.by, w.sy);
+      iz = walk_index(w.bz, w.sz);
+      sum = __ldg(m.bsum + ((int64_t)(iz >> kSkipLog) * m.bsy + (iy >> kSkipLog)) * m.bsx + (ix >> kSkipLog));
+    }
+    const bool macro = __all_sync(0xffffffffu, done || sum <= kSumFree);
+    if (done) continue;
+    // the crossings of this brick's boundary planes on each axis (index kA on axis a; t = +inf without a step)
+    const int kx = w.sx > 0.0f ? kMask - (ix & kMask) : (w.sx < 0.0f ? (ix & kMask) : 0);
+    const int ky = w.sy > 0.0f ? kMask - (iy & kMask) : (w.sy < 0.0f ? (iy & kMask) : 0);
+    const int kz = w.sz > 0.0f ? kMask - (iz & kMask) : (w.sz < 0.0f ? (iz & kMask) : 0);
+    const float tex = fmul(fsub(fadd(w.bx, (float)kx * w.sx), w.ox), w.vx);
+    const float tey = fmul(fsub(fadd(w.by, (float)ky * w.sy), w.oy), w.vy);
+    const float tez = fmul(fsub(fadd(w.bz, (float)kz * w.sz), w.oz), w.vz);
+    const float T = fminf(tex, fminf(tey, tez));
+    const int A = tex == T ? 0 : (tey == T ? 1 : 2);  // the walk's tie-break: x, then y, then z
+    if (macro) {
+      const bool end = !(T < w.tmax);                 // the walk ends inside this brick
+      const float key = end ? w.tmax : T;
+      const int cx = !end && A == 0 ? kx : skip_axis_count(w.bx, w.sx, w.ox, w.vx, adx, w.tx, key, !end && 0 < A, kx);
+      const int cy = !end && A == 1 ? ky : skip_axis_count(w.by, w.sy, w.oy, w.vy, ady, w.ty, key, !end && 1 < A, ky);
+      const int cz = !end && A == 2 ? kz : skip_axis_count(w.bz, w.sz, w.oz, w.vz, adz, w.tz, key, !end && 2 < A, kz);
+      w.bx = fadd(w.bx, (float)cx * w.sx);
+      w.by = fadd(w.by, (float)cy * w.sy);
+      w.bz = fadd(w.bz, (float)cz * w.sz);
+      w.tx = fmul(fsub(w.bx, w.ox), w.vx);
+      w.ty = fmul(fsub(w.by, w.oy), w.vy);
+      w.tz = fmul(fsub(w.bz, w.oz), w.vz);
+      lin += cx * w.qx + cy * w.qy + cz * w.qz;
+      const uint32_t nvis = 1u + (uint32_t)(cx + cy + cz);
+      steps += nvis;
+      if (sum == kSumUnknown) iacc += nvis;
+      if (end)
+        done = true;
+      else
+        walk_take_lin(w, A, lin);                     // the boundary crossing (T, A) itself
+    } else {
+      const float bx0 = w.bx, by0 = w.by, bz0 = w.bz;
+      const uint32_t addr = min((uint32_t)lin, addr_max);
+      const uint32_t raw = raw_load<KIND>(payload, addr);
+      uint32_t last = 0u;
+      float ts = 0.0f;
+      walk_count_run<KIND>(w, lin, raw, addr, payload, addr_max, fminf(T, w.tmax), iacc, last, ts);
+      steps += (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
+      done = last >= 2u || !(ts < w.tmax);           // occluded, or the walk's end reached
+    }
+  }
+}
+
 // IG of one ray: walk, read, accumulate, stop after the first occupied voxel.
 // HIT: the occupied voxel adds its gain (the Section III sum runs to N_O).
 // LINEAR: linear layout with stride steps; else bricked with table reads.
@@ -401,9 +617,10 @@ __device__ __forceinline__ void ray_ig_chunked(const void *payload, uint32_t add
 // Items = (pose, 32 x 8 ray tile).  A CTA takes one item at a time; warp w
 // casts packet w of the tile; the 8 packet sums are added in warp order
 // into partials[item].  CHUNK > 0 (linear layout only) walks CHUNK voxels
-// ahead of the reads (ray_ig_chunked).
-template <int KIND, bool HIT, bool LINEAR, int CHUNK>
-__global__ void __launch_bounds__(kThreads, CHUNK ? 4 : (LINEAR ? 6 : 5))
+// ahead of the reads (ray_ig_chunked).  SKIP (linear state maps, count
+// metric) skips uniform bricks (ray_count_skip).
+template <int KIND, bool HIT, bool LINEAR, int CHUNK, bool SKIP = false>
+__global__ void __launch_bounds__(kThreads, SKIP ? 4 : (CHUNK ? 4 : (LINEAR ? 6 : 5)))
     ig_tiles_kernel(DevMap m, CamConst cc, const float *__restrict__ poses, int64_t n_items, uint32_t addr_max,
                     unsigned long long *queue, Partial *partials) {
   extern __shared__ int32_t stab[];
@@ -445,7 +662,12 @@ __global__ void __launch_bounds__(kThreads, CHUNK ? 4 : (LINEAR ? 6 : 5))
     const int j = s_y0 + dj;
     float facc = 0.0f;
     uint32_t iacc = 0u, steps = 0u;
-    if (i < cc.W && j < cc.H) {
+    const bool inside = i < cc.W && j < cc.H;
+    if constexpr (SKIP) {
+      float o[3] = {0.0f, 0.0f, 0.0f}, d[3] = {0.0f, 0.0f, 0.0f};
+      if (inside) ray_segment_rot(cc, s_pose, s_rot, i, j, o, d);
+      ray_count_skip<KIND>(m, addr_max, o, d, inside, iacc, steps);   // all lanes together
+    } else if (inside) {
       float o[3], d[3];
       ray_segment_rot(cc, s_pose, s_rot, i, j, o, d);
       if constexpr (CHUNK > 0)
@@ -770,7 +992,7 @@ uint32_t addr_max_of(nbt_map map) { return (uint32_t)(map->elems - 1); }
 // Resident CTAs per SM of one tile-kernel instantiation: queried once per
 // device for the linear layout (no dynamic shared memory), per call for
 // bricked layouts (their table size varies).
-template <int KIND, bool HIT, bool LINEAR, int CHUNK>
+template <int KIND, bool HIT, bool LINEAR, int CHUNK, bool SKIP = false>
 int tiles_per_sm(nbt_map map, size_t smem, int *per_sm) {
   static int cached[64] = {0};
   const int dev = map->device;
@@ -779,25 +1001,25 @@ int tiles_per_sm(nbt_map map, size_t smem, int *per_sm) {
     return NBT_OK;
   }
   int n = 0;
-  NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ig_tiles_kernel<KIND, HIT, LINEAR, CHUNK>, kThreads,
-                                                             smem));
+  NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ig_tiles_kernel<KIND, HIT, LINEAR, CHUNK, SKIP>,
+                                                             kThreads, smem));
   *per_sm = std::max(n, 1);
   if (LINEAR && dev >= 0 && dev < 64) cached[dev] = *per_sm;
   return NBT_OK;
 }
 
-template <int KIND, bool HIT, bool LINEAR, int CHUNK>
+template <int KIND, bool HIT, bool LINEAR, int CHUNK, bool SKIP = false>
 int launch_tiles_t(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
                    void *workspace, cudaStream_t stream) {
   const size_t smem = LINEAR ? 0 : tile_smem(map);
   int per_sm = 1;
-  int rc = tiles_per_sm<KIND, HIT, LINEAR, CHUNK>(map, smem, &per_sm);
+  int rc = tiles_per_sm<KIND, HIT, LINEAR, CHUNK, SKIP>(map, smem, &per_sm);
   if (rc != NBT_OK) return rc;
   const int64_t grid = std::min<int64_t>(n_items, (int64_t)sm_count() * per_sm);
   unsigned long long *queue = (unsigned long long *)workspace;
   Partial *partials = (Partial *)((char *)workspace + 256);
   NBT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream));
-  ig_tiles_kernel<KIND, HIT, LINEAR, CHUNK><<<(unsigned)grid, kThreads, smem, stream>>>(
+  ig_tiles_kernel<KIND, HIT, LINEAR, CHUNK, SKIP><<<(unsigned)grid, kThreads, smem, stream>>>(
       dev_map(map, payload), cc, poses, n_items, addr_max_of(map), queue, partials);
   NBT_CUDA_TRY(cudaGetLastError());
   return NBT_OK;
@@ -852,6 +1074,11 @@ int launch_tiles_linear(nbt_map map, const void *payload, const CamConst &cc, co
   if (n_rays <= kSplit8Rays) return launch_split<KIND, HIT, 8>(map, payload, cc, poses, n_items, workspace, stream);
   if (n_rays <= 2 * (int64_t)sm_count() * per_sm * kThreads)
     return launch_tiles_t<KIND, HIT, true, kChunk>(map, payload, cc, poses, n_items, workspace, stream);
+  if constexpr (KIND != PAYLOAD_GAIN_F32) {
+    // state maps (unknown count): skip uniform bricks; the occupied voxel adds nothing, so HIT is moot
+    if (map->skip && map->d_bsum && map->bsum_valid)
+      return launch_tiles_t<KIND, true, true, 0, true>(map, payload, cc, poses, n_items, workspace, stream);
+  }
   return launch_tiles_t<KIND, HIT, true, 0>(map, payload, cc, poses, n_items, workspace, stream);
 }
 
@@ -891,6 +1118,9 @@ int run_tiles(nbt_map map, const nbt_pose *poses, int64_t n_poses, const nbt_cam
     return NBT_EWORKSPACE;
   if (kind == PAYLOAD_GAIN_F32) {
     rc = prepare_gain(map, params, stream);
+    if (rc != NBT_OK) return rc;
+  } else if (map->skip) {
+    rc = prepare_bsum(map, stream);
     if (rc != NBT_OK) return rc;
   }
   const float *pp = (const float *)poses;
@@ -1144,7 +1374,9 @@ extern "C" int nbt_map_set_tuning(nbt_map map, const nbt_tuning *tuning) {
   if (!map || !tuning || !map_alive(map, 0)) return NBT_EINVAL;
   const int pw = tuning->packet_w == 0 ? 8 : tuning->packet_w;
   if (pw != 4 && pw != 8 && pw != 16 && pw != 32) return NBT_EINVAL;
+  if (tuning->skip != 0 && tuning->skip != 1) return NBT_EINVAL;
   map->packet_w = pw;
+  map->skip = tuning->skip;
   return NBT_OK;
 }
 
@@ -1152,5 +1384,6 @@ extern "C" int nbt_map_get_tuning(nbt_map map, nbt_tuning *tuning) {
   if (!map || !tuning || !map_alive(map, 0)) return NBT_EINVAL;
   tuning->packet_w = map->packet_w;
   tuning->brick = map->brick;
+  tuning->skip = map->skip;
   return NBT_OK;
 }

@@ -71,7 +71,7 @@ def test_structs_match_header_sizes():
     assert C.sizeof(_lib.MapDesc) == 36
     assert C.sizeof(_lib.Camera) == 28
     assert C.sizeof(_lib.IgParams) == 20
-    assert C.sizeof(_lib.Tuning) == 8
+    assert C.sizeof(_lib.Tuning) == 12
     assert C.sizeof(_lib.CostParams) == 12
 
 
@@ -210,6 +210,6 @@ def test_handles_that_name_no_live_map_are_rejected_without_reading_them(libnbt)
     assert L.nbt_views_ig(bogus, None, 1, C.byref(cam), C.byref(prm), None, None, None, 0, None) == -1
     assert L.nbt_views_ig_noalloc(bogus, None, 1, C.byref(cam), C.byref(prm), None, None, None) == -1
     assert L.nbt_map_upload(bogus, None, 0, 0, None) == -1
-    t = _lib.Tuning(8, 0)
+    t = _lib.Tuning(8, 0, 0)
     assert L.nbt_map_set_tuning(bogus, C.byref(t)) == -1
     assert L.nbt_map_get_tuning(bogus, C.byref(t)) == -1

@@ -389,7 +389,7 @@ def test_packet_shapes_same_results(packet_w):
     w = configs.exact64(seed=9, n_views=16)
     gm = gpu_map(w)
     gm.set_tuning(packet_w)
-    assert gm.tuning() == {"packet_w": packet_w, "brick": 1}
+    assert gm.tuning() == {"packet_w": packet_w, "brick": 1, "skip": 0}
     ig, st = views_gpu(gm, w.poses, gpu_camera(w.camera), nbt.ig_params("count"))
     rig, rst = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(w.camera), oracle.params("count"))
     assert np.array_equal(st, rst) and np.array_equal(ig, rig)
@@ -445,9 +445,10 @@ def test_autotune_returns_a_valid_fastest_config():
     prm = nbt.ig_params("count")
     pz = torch.from_numpy(w.poses).cuda()
     m, cfg, timings = nbt.autotune(torch.from_numpy(w.grid).cuda(), w.voxel_size, w.origin, "u8", pz, cam, prm,
-                                   layouts=(1, 8), packets=(8, 16), reps=2)
-    assert set(timings) == {(1, 8), (1, 16), (8, 8), (8, 16)}
-    assert cfg["ms"] == min(timings.values()) and m.tuning() == {"packet_w": cfg["packet_w"], "brick": cfg["brick"]}
+                                   layouts=(1, 8), packets=(8, 16), skips=(0, 1), reps=2)
+    assert set(timings) == {(1, 8, 0), (1, 8, 1), (1, 16, 0), (1, 16, 1), (8, 8, 0), (8, 16, 0)}
+    assert cfg["ms"] == min(timings.values())
+    assert m.tuning() == {"packet_w": cfg["packet_w"], "brick": cfg["brick"], "skip": cfg["skip"]}
     ig, st = views_gpu(m, w.poses, cam, prm)
     rig, rst = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(w.camera), oracle.params("count"))
     assert np.array_equal(st, rst) and np.array_equal(ig, rig)

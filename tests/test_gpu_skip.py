@@ -1,0 +1,142 @@
+"""Count walks that skip uniform bricks, against the oracle (GPU required).
+
+On linear 1-byte and 2-bit state maps with brick skipping switched on (nbt_map_set_tuning), calls
+with many rays run the tile kernel that replaces the walk through a brick of 8^3 voxels that are all unknown or all free by per-axis crossing counts
+(the same FP32 crossing parameters as the voxel-by-voxel walk).  Every case here has more than
+466,944 rays per call, so that kernel runs, and the voxel steps and unknown counts of every view
+must equal the oracle's exactly: maps of every brick class, sides that are not multiples of 8,
+an origin off the voxel grid, cameras inside and outside the map, both grid and range modes, the
+map updated between calls (the summaries must be rebuilt), and trajectory IG.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2503_22588_gb300 as nbt
+from workload import configs, poses, scenes
+
+pytestmark = pytest.mark.gpu
+
+THREADS = 16
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    nbt.build()
+    oracle.build()
+
+
+def run_case(grid, enc, pz, cam, origin=(0.0, 0.0, 0.0), voxel=0.01):
+    assert len(pz) * cam.width * cam.height > 466944        # the brick-skipping kernel's range
+    m = nbt.Map.from_grid(torch.from_numpy(np.ascontiguousarray(grid)).cuda(), voxel, origin, enc)
+    m.set_tuning(8, skip=True)
+    ig, st = nbt.views_ig(m, torch.from_numpy(pz).cuda(), cam, nbt.ig_params("count"))
+    torch.cuda.synchronize()
+    om = oracle.Map(np.ascontiguousarray(grid), voxel, origin)
+    ocam = oracle.camera(cam.width, cam.height, cam.fov_h, cam.fov_v, cam.max_range,
+                         ["corners", "centers"][cam.grid_mode], ["planar", "spherical"][cam.range_mode])
+    rig, rst = oracle.views_ig(om, pz, ocam, oracle.params("count"), "f32", THREADS)
+    assert np.array_equal(st.cpu().numpy(), rst)
+    assert np.array_equal(ig.cpu().numpy().astype(np.float64), rig)
+    m.close()
+    return rst
+
+
+def shell(center, n, r0, r1, seed):
+    return poses.shell_views(np.asarray(center, np.float64), n, r0, r1, seed)
+
+
+@pytest.mark.parametrize("enc", ["u8", "u2"])
+def test_boxes_spheres_half_unknown(enc):
+    grid = scenes.boxes_spheres(96, 40, 3, half_unknown=True)
+    pz = shell((0.48, 0.48, 0.48), 128, 0.3, 0.7, 1)
+    cam = nbt.camera(64, 64, 1.0, 0.8, 1.0)
+    run_case(grid, enc, pz, cam)
+
+
+@pytest.mark.parametrize("enc", ["u8", "u2"])
+def test_room_with_partial_bricks_and_an_offset_origin(enc):
+    """Sides 101 x 77 x 90 (no multiple of 8), origin off the grid, cameras inside and outside."""
+    grid = scenes.room_states(128, 150, 0.4, seed=5)[:90, :77, :101]
+    origin = (-0.0123, 0.0377, 0.0049)
+    c = np.array([0.5, 0.38, 0.45])
+    pz = np.concatenate([shell(c, 64, 0.05, 0.3, 2), shell(c, 64, 0.6, 1.2, 3)])
+    cam = nbt.camera(80, 56, 1.1, 0.9, 1.5)
+    run_case(grid, enc, pz, cam, origin)
+
+
+@pytest.mark.parametrize("fill", [0, 1])
+def test_uniform_maps(fill):
+    """All unknown (every voxel counts) or all free (none does): whole walks of macro steps."""
+    grid = np.full((64, 72, 80), fill, np.uint8)
+    pz = shell((0.4, 0.36, 0.32), 128, 0.1, 0.9, 4)
+    cam = nbt.camera(64, 64, 1.0, 0.8, 1.2, "centers", "spherical")
+    st = run_case(grid, "u2", pz, cam)
+    assert st.sum() > 0
+
+
+def test_occupied_shell_and_thin_walls():
+    """Bricks that hold occupied voxels are never skipped: a closed shell of thin walls."""
+    n = 96
+    grid = np.zeros((n, n, n), np.uint8)
+    grid[8:88, 8:88, 8:88] = 1
+    grid[8:88, 8:88, 20] = 2
+    grid[8:88, 47, 8:88] = 2
+    grid[63, 8:88, 8:88] = 2
+    grid[30:50, 30:50, 30:50] = 0
+    pz = shell((0.48, 0.48, 0.48), 128, 0.2, 0.6, 6)
+    cam = nbt.camera(64, 64, 1.2, 1.0, 1.0)
+    run_case(grid, "u8", pz, cam)
+
+
+def test_summaries_follow_uploads_and_inserts():
+    """The brick summaries are derived data: rebuilt after an upload and after a depth-scan insert."""
+    grid = scenes.room_states(96, 80, 0.4, seed=9)
+    pz = shell((0.48, 0.48, 0.48), 128, 0.3, 0.7, 7)
+    cam = nbt.camera(64, 64, 1.0, 0.8, 1.0)
+    m = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01, (0.0, 0.0, 0.0), "u2")
+    m.set_tuning(8, skip=True)
+    ptc = torch.from_numpy(pz).cuda()
+    prm = nbt.ig_params("count")
+    ocam = oracle.camera(64, 64, 1.0, 0.8, 1.0)
+    for step in range(3):
+        ig, st = nbt.views_ig(m, ptc, cam, prm)
+        torch.cuda.synchronize()
+        rig, rst = oracle.views_ig(oracle.Map(grid), pz, ocam, oracle.params("count"), "f32", THREADS)
+        assert np.array_equal(st.cpu().numpy(), rst), step
+        assert np.array_equal(ig.cpu().numpy().astype(np.float64), rig), step
+        if step == 0:
+            grid = grid.copy()
+            grid[:, :, 40:56] = 0                            # a new unknown slab, uploaded
+            m.upload(torch.from_numpy(grid).cuda())
+        elif step == 1:
+            pts = np.stack(np.meshgrid(np.linspace(0.1, 0.85, 60), np.linspace(0.1, 0.85, 60), [0.7]), -1)
+            pts = pts.reshape(-1, 3).astype(np.float32)
+            m.insert_points(torch.from_numpy(pts).cuda(), (0.48, 0.48, 0.1))
+            grid = m.download().cpu().numpy()
+    m.close()
+
+
+def test_trajectories_on_a_state_map():
+    w = configs.traj256(seed=2, n_traj=48, n=128, len_range=(5, 20))
+    w.camera = configs.Camera(96, 72)
+    m = nbt.Map.from_grid(torch.from_numpy(w.grid).cuda(), w.voxel_size, w.origin, "u2")
+    m.set_tuning(8, skip=True)
+    cam = nbt.camera(96, 72, w.camera.fov_h, w.camera.fov_v, 1.0)
+    assert len(w.poses) * 96 * 72 > 466944
+    pose_out = torch.empty(len(w.poses), dtype=torch.float32, device="cuda")
+    tig = nbt.traj_ig(m, torch.from_numpy(w.poses).cuda(), torch.from_numpy(w.offsets).cuda(), cam,
+                      nbt.ig_params("count"), pose_out=pose_out)
+    torch.cuda.synchronize()
+    om = oracle.Map(w.grid)
+    rig, _ = oracle.traj_ig(om, w.poses, w.offsets, oracle.camera_of(w.camera), oracle.params("count"), "f32",
+                            THREADS)
+    pig, _ = oracle.views_ig(om, w.poses, oracle.camera_of(w.camera), oracle.params("count"), "f32", THREADS)
+    assert np.array_equal(pose_out.cpu().numpy().astype(np.float64), pig)     # counts below 2^24: exact
+    assert np.array_equal(tig.cpu().numpy(), rig.astype(np.float32))          # sums returned as FP32
+    assert rig.max() > 2 ** 24                                                # (some exceed 2^24)
+    m.close()

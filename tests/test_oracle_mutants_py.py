@@ -75,7 +75,12 @@ MUTANTS = [
      "int(math.floor((2.0 * half) / step))"),
     ("endpoints", "half_width_as_span", "(2.0 * half) / step", "half / step"),
     ("surrogate", "conv_tap_order_transposed", "tap = (dz * 3 + dy) * 3 + dx", "tap = (dx * 3 + dy) * 3 + dz"),
-    ("surrogate", "relu_mask_dropped_in_backward", "da = dxin * (acts[i] > 0)", "da = dxin"),
+    ("surrogate", "relu_mask_dropped_in_backward", "da = rnd(dxin * (acts[i] > 0))", "da = rnd(dxin)"),
+    ("surrogate", "backward_rounding_not_modelled", "dh = rnd(np.outer(", "dh = (np.outer("),
+    ("surrogate", "input_gradient_rounding_not_modelled", "da = rnd(dxin * (acts[i] > 0))",
+     "da = (dxin * (acts[i] > 0))"),
+    ("surrogate", "target_scale_ignored", "t = np.asarray(targets, np.float64) * float(target_scale)",
+     "t = np.asarray(targets, np.float64)"),
     ("surrogate", "mse_gradient_factor_dropped", "dy = 2.0 * (y - t) / n", "dy = (y - t) / n"),
     ("surrogate", "adam_without_bias_correction", "mh = mk / (1.0 - beta1 ** step)", "mh = mk"),
     ("surrogate", "adam_second_moment_unsquared", "(1.0 - beta2) * g * g", "(1.0 - beta2) * g"),

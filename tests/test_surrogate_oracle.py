@@ -88,6 +88,80 @@ def test_network_gradients_match_finite_differences():
             assert abs(num - g[k].reshape(-1)[j]) <= 1e-6 + 1e-5 * abs(num), (k, j, num, g[k].reshape(-1)[j])
 
 
+def test_target_scale_is_the_loss_of_scaled_targets():
+    """loss_and_grads(t, target_scale=c) is the loss of the targets c t: the finite difference of
+    mean (y - c t)^2 in a parameter matches its gradient, and it equals passing c t directly."""
+    rng = np.random.default_rng(4)
+    p = S.init_params(6, layers=TINY, crop=8, hidden=6)
+    p = {k: v.astype(np.float64) + 0.05 * rng.standard_normal(v.shape) for k, v in p.items()}
+    crops = (rng.random((3, 8, 8, 8, 8)) < 0.3).astype(np.float64)
+    feats = rng.standard_normal((3, 8))
+    t = rng.uniform(20.0, 90.0, 3)
+    loss, g = S.loss_and_grads(p, crops, feats, t, layers=TINY, target_scale=0.01)
+    y, _ = S.forward(p, crops, feats, layers=TINY)
+    assert abs(loss - np.mean((y - 0.01 * t) ** 2)) < 1e-15
+    loss2, g2 = S.loss_and_grads(p, crops, feats, 0.01 * t, layers=TINY)
+    assert loss == loss2 and all(np.array_equal(g[k], g2[k]) for k in g)
+    eps = 1e-6
+    pp = {kk: vv.copy() for kk, vv in p.items()}
+    pm = {kk: vv.copy() for kk, vv in p.items()}
+    pp["g2"][0] += eps
+    pm["g2"][0] -= eps
+    num = (S.loss_and_grads(pp, crops, feats, t, layers=TINY, target_scale=0.01)[0]
+           - S.loss_and_grads(pm, crops, feats, t, layers=TINY, target_scale=0.01)[0]) / (2 * eps)
+    assert abs(num - g["g2"][0]) < 1e-7
+
+
+def test_bf16_modelling_of_the_backward_pass():
+    """With BF16 modelling the backward pass rounds dh and the masked input gradients: it stays close
+    to the exact gradients (within a few BF16 units) but is not identical on random parameters, and it
+    is identical when every such value is exactly representable (weights in {-1, 0, 1}, integer
+    biases and inputs, dyadic residuals)."""
+    rng = np.random.default_rng(7)
+    p = S.init_params(8, layers=TINY, crop=8, hidden=6)
+    p = {k: v.astype(np.float64) + 0.05 * rng.standard_normal(v.shape) for k, v in p.items()}
+    crops = (rng.random((3, 8, 8, 8, 8)) < 0.3).astype(np.float64)
+    feats = S._bf16(rng.standard_normal((3, 8)))
+    t = rng.standard_normal(3)
+    _, g = S.loss_and_grads(p, crops, feats, t, layers=TINY)
+    _, gb = S.loss_and_grads(p, crops, feats, t, layers=TINY, bf16_activations=True)
+    rel = {k: np.linalg.norm(gb[k] - g[k]) / max(np.linalg.norm(g[k]), 1e-30) for k in g}
+    assert max(rel.values()) < 5e-2 and any(r > 0 for r in rel.values()), rel
+    # exact case: integer weights and biases, dyadic residuals
+    q = {k: np.sign(rng.standard_normal(v.shape)) * (rng.random(v.shape) < 0.15) for k, v in p.items()}
+    for k in q:
+        if k.startswith("b") or k.startswith("g"):
+            q[k] = np.abs(q[k])
+    crops4 = (rng.random((4, 8, 8, 8, 8)) < 0.3).astype(np.float64)
+    ones = np.ones((4, 8))
+    y, _ = S.forward(q, crops4, ones, layers=TINY)
+    tq = y - np.array([1.0, -2.0, 1.0, 1.0])              # batch of 4: dy = 2 e / 4 is dyadic
+    crops = crops4
+    _, g = S.loss_and_grads(q, crops, ones, tq, layers=TINY)
+    _, gb = S.loss_and_grads(q, crops, ones, tq, layers=TINY, bf16_activations=True)
+    assert all(np.array_equal(g[k], gb[k]) for k in g)
+    assert all(np.abs(g[k]).max() > 0 for k in g)
+
+
+def test_bf16_modelling_rounds_the_stored_backward_values():
+    """One sample through convolutions whose outputs are single voxels: the bias gradient of layer 0
+    is then the (masked) input gradient at that voxel and g1's gradient is dh itself -- with BF16
+    modelling both are BF16 values, without it they are not."""
+    rng = np.random.default_rng(11)
+    layers = ((8, 4, 8), (4, 4, 1))          # crop 8: stride 8 leaves one voxel, then one voxel
+    p = S.init_params(12, layers=layers, crop=8, hidden=6)
+    p = {k: v.astype(np.float64) + 0.3 * rng.standard_normal(v.shape) + 0.2 for k, v in p.items()}
+    crops = (rng.random((1, 8, 8, 8, 8)) < 0.5).astype(np.float64)
+    feats = rng.standard_normal((1, 8))
+    t = np.array([-3.7])
+    _, gb = S.loss_and_grads(p, crops, feats, t, layers=layers, bf16_activations=True)
+    _, g = S.loss_and_grads(p, crops, feats, t, layers=layers)
+    for k in ("g1", "b0"):
+        assert np.abs(gb[k]).max() > 0, k
+        assert np.array_equal(S._bf16(gb[k]), gb[k]), k
+        assert not np.array_equal(S._bf16(g[k]), g[k]), k
+
+
 def test_adam_two_steps_by_hand():
     p = {"a": np.array([1.0])}
     m = {"a": np.zeros(1)}
