@@ -425,7 +425,7 @@ def parse_args(argv=None):
                     help="state-map count walks: skip uniform 8^3 bricks (1) or not (0); default: the library's")
     ap.add_argument("--views", type=int, default=None,
                     help="view workloads: only the first N views (a reduced launch, for profiling)")
-    ap.add_argument("--train-epochs", type=int, default=12,
+    ap.add_argument("--train-epochs", type=int, default=30,
                     help="room512-pruned: surrogate training epochs before timing (0: untrained, for profiling)")
     ap.add_argument("--scenes", type=int, default=PRUNED_MIN_SCENES,
                     help="room512-pruned: scenes scored for the same-best-view rate (at least the timed steps)")
@@ -1171,13 +1171,17 @@ def room_scenes(seeds, workers: int):
         return list(ex.map(configs.room512, seeds))
 
 
-def train_room_surrogate(nbt, torch, dev, cam, prm, epochs: int = 12, log=None):
-    """The surrogate trained inside the run on exact labels (mean ray IG) of 24 seeded 256^3 rooms."""
+TRAIN_ROOMS, TRAIN_PRIMS, TRAIN_EPOCHS = 24, 250, 30
+
+
+def train_room_surrogate(nbt, torch, dev, cam, prm, epochs: int = TRAIN_EPOCHS, log=None):
+    """The surrogate trained inside the run on exact labels (mean ray IG) of 24 seeded 256^3 rooms with
+    room512's primitive density (250 primitives in 256^3, 2000 in 512^3) and 40 % unknown."""
     from paper_2503_22588_gb300 import planning as P, surrogate as gs
     from workload import poses as wp, scenes
     maps, poses, targets = [], [], []
-    for sidx in range(24):
-        g = scenes.room_states(256, 500, 0.4, seed=1000 + sidx)
+    for sidx in range(TRAIN_ROOMS):
+        g = scenes.room_states(256, TRAIN_PRIMS, 0.4, seed=1000 + sidx)
         m = nbt.Map.from_grid(torch.from_numpy(g).to(dev), 0.01, (0, 0, 0), "u8")
         rng = np.random.default_rng(2000 + sidx)
         pois = rng.uniform(0.6, 2.56 - 0.6, size=(8, 3))
@@ -1193,8 +1197,10 @@ def train_room_surrogate(nbt, torch, dev, cam, prm, epochs: int = 12, log=None):
     train_s = time.perf_counter() - t0
     for m in maps:
         m.close()
-    return net, {"seconds": train_s, "final_loss": losses[-1] if losses else None, "samples": 24 * 8 * 1024,
-                 "epochs": epochs, "target": "mean ray IG x 0.01 (scale applied in the loss kernel)"}
+    return net, {"seconds": train_s, "final_loss": losses[-1] if losses else None,
+                 "samples": TRAIN_ROOMS * 8 * 1024, "epochs": epochs,
+                 "scenes": f"{TRAIN_ROOMS} seeded 256^3 rooms, {TRAIN_PRIMS} primitives, 40 % unknown",
+                 "target": "mean ray IG x 0.01 (scale applied in the loss kernel)"}
 
 
 def pruned_cpu_baseline(w, budget_s: float = 12.0, single_s: float = 6.0) -> dict:
@@ -1424,7 +1430,8 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         "data": "synthetic",
         "config": {"workload": pruned_describe(), "views_per_step": n_views, "rays_per_view": 320 * 240,
                    "map": "512^3 u2", "scenes": f"seeds {seeds[0]}..{seeds[-1]} (timed: first {args.steps})",
-                   "train": "24 seeded 256^3 rooms x 8 PoIs x 1024 views, exact labels, 12 epochs (before timing)",
+                   "train": f"{TRAIN_ROOMS} seeded 256^3 rooms ({TRAIN_PRIMS} primitives) x 8 PoIs x 1024 views, "
+                            f"exact labels, {args.train_epochs} epochs (before timing)",
                    "parallelism": f"replicas x{world}", "l2": "flushed before every timed arm (256 MiB write)",
                    "step": "pruned: map upload + nbt_plan_pruned (crops, forward, top-k, exact re-score, argmax); "
                            "exact: map upload + nbt_views_ig of all candidates + argmax"},

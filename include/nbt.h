@@ -369,7 +369,8 @@ int nbt_tc_wait_probe(void *stream);
  * BF16 pose features ((position - origin) / map extent, the quaternion, 1).
  * The network sees code c as the one-hot vector with a 1 in channel c - 1 of
  * 8 (all zero for code 0).  Output: the predicted mean ray IG (the training target
- * the caller chooses, e.g. g_P / 100).  Network: 3^3 convolutions 8->16,
+ * the caller chooses, e.g. g_P with a target scale of 0.01, see
+ * nbt_surrogate_set_target_scale).  Network: 3^3 convolutions 8->16,
  * 16->32, 32->64 (stride 2) and 64->64 (stride 1), ReLU; 4096 + 8 -> 128
  * (ReLU) -> 1; BF16 weights and activations, FP32 accumulation on tcgen05
  * tensor cores, FP32 master weights, MSE loss, Adam. */

@@ -69,7 +69,8 @@ struct nbt_map_s {
   // brick summaries of linear state maps (count walks skip uniform bricks):
   // one byte per kSkipB^3 brick, derived from the payload, rebuilt when stale
   uint8_t *d_bsum = nullptr;
-  int bsx = 0, bsy = 0, bsz = 0;     // summary bricks per axis
+  int bsx[4] = {0}, bsy[4] = {0}, bsz[4] = {0};  // summary bricks per axis and level
+  int64_t boff[4] = {0};             // first byte of each level; boff[3] + last level size = total
   bool bsum_valid = false;
   uint64_t bsum_version = 0;
   // point-cloud insertion scratch (nbt_map_insert_points), allocated on first use
@@ -85,12 +86,15 @@ struct nbt_map_s {
 
 namespace nbt {
 
-// Brick summaries (count walks on linear state maps): the map is cut into
-// kSkipB^3 bricks aligned to the origin; a brick's byte says whether every
-// voxel of it inside the map is unknown (kSumUnknown), every one is free
-// (kSumFree), or neither (kSumOther: mixed, or holding an occupied voxel).
+// Brick summaries (count walks on linear state maps): a pyramid of kSkipLevels
+// levels; level l cuts the map into cubic bricks of edge 2^(kSkipLog + l)
+// aligned to the origin, and a brick's byte says whether every voxel of it
+// inside the map is unknown (kSumUnknown), every one is free (kSumFree), or
+// neither (kSumOther: mixed, or holding an occupied voxel).  Level l + 1 is
+// uniform exactly where its (up to) 8 children are uniform with one class.
 constexpr int kSkipLog = 3;
 constexpr int kSkipB = 1 << kSkipLog;
+constexpr int kSkipLevels = 4;         // bricks of 8, 16, 32 and 64 voxels
 constexpr uint32_t kSumUnknown = 0, kSumFree = 1, kSumOther = 3;
 
 // Map view passed to kernels by value.
@@ -98,8 +102,9 @@ struct DevMap {
   const void *payload;
   const int32_t *tab;
   int nx, ny, nz;
-  const uint8_t *bsum;               // brick summaries (count walks), else null
-  int bsx, bsy;                      // summary bricks along x and y
+  const uint8_t *bsum;               // brick summary pyramid (count walks), else null
+  int bsx[kSkipLevels], bsy[kSkipLevels];  // bricks along x and y per level
+  int boff[kSkipLevels];             // first byte of each level
 };
 
 // Per-call camera constants (Section III endpoint grid), computed on the host.

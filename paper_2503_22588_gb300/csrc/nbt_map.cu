@@ -209,6 +209,27 @@ __global__ void brick_summary_kernel(const uint8_t *__restrict__ payload, int nx
   }
 }
 
+// Level l + 1 of the summary pyramid from level l (one thread per brick):
+// uniform with class c exactly where every child inside the map is uniform
+// with class c.
+__global__ void brick_summary_up_kernel(const uint8_t *__restrict__ child, int cx, int cy, int cz,
+                                        uint8_t *__restrict__ parent, int px, int py, int pz) {
+  const int64_t nb = (int64_t)px * py * pz;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    const int x0 = (int)(b % px) * 2, y0 = (int)((b / px) % py) * 2, z0 = (int)(b / ((int64_t)px * py)) * 2;
+    uint32_t first = 4u;
+    bool uniform = true;
+    for (int z = z0; z < min(z0 + 2, cz); ++z)
+      for (int y = y0; y < min(y0 + 2, cy); ++y)
+        for (int x = x0; x < min(x0 + 2, cx); ++x) {
+          const uint32_t c = child[((int64_t)z * cy + y) * cx + x];
+          if (first == 4u) first = c;
+          uniform = uniform && c == first && c != kSumOther;
+        }
+    parent[b] = (uint8_t)(uniform ? first : kSumOther);
+  }
+}
+
 int grid_for(int64_t n) {
   const int64_t blocks = (n + 255) / 256;
   return (int)std::min<int64_t>(std::max<int64_t>(blocks, 1), (int64_t)sm_count() * 16);
@@ -287,15 +308,22 @@ int prepare_bsum(nbt_map map, cudaStream_t stream) {
   if (!map->d_bsum) return NBT_OK;
   if (map->bsum_valid && map->bsum_version == map->version) return NBT_OK;
   const nbt_map_desc &d = map->desc;
-  const int64_t nb = (int64_t)map->bsx * map->bsy * map->bsz;
+  const int64_t nb = (int64_t)map->bsx[0] * map->bsy[0] * map->bsz[0];
   const uint8_t *p = (const uint8_t *)map->d_payload;
   if (d.encoding == NBT_U2_STATE)
-    brick_summary_kernel<NBT_U2_STATE><<<grid_for(nb), 256, 0, stream>>>(p, d.nx, d.ny, d.nz, map->bsx, map->bsy,
-                                                                         map->bsz, map->d_bsum);
+    brick_summary_kernel<NBT_U2_STATE><<<grid_for(nb), 256, 0, stream>>>(p, d.nx, d.ny, d.nz, map->bsx[0],
+                                                                         map->bsy[0], map->bsz[0], map->d_bsum);
   else
-    brick_summary_kernel<NBT_U8_STATE><<<grid_for(nb), 256, 0, stream>>>(p, d.nx, d.ny, d.nz, map->bsx, map->bsy,
-                                                                         map->bsz, map->d_bsum);
+    brick_summary_kernel<NBT_U8_STATE><<<grid_for(nb), 256, 0, stream>>>(p, d.nx, d.ny, d.nz, map->bsx[0],
+                                                                         map->bsy[0], map->bsz[0], map->d_bsum);
   NBT_CUDA_TRY(cudaGetLastError());
+  for (int l = 1; l < kSkipLevels; ++l) {
+    const int64_t np = (int64_t)map->bsx[l] * map->bsy[l] * map->bsz[l];
+    brick_summary_up_kernel<<<grid_for(np), 256, 0, stream>>>(map->d_bsum + map->boff[l - 1], map->bsx[l - 1],
+                                                             map->bsy[l - 1], map->bsz[l - 1], map->d_bsum + map->boff[l],
+                                                             map->bsx[l], map->bsy[l], map->bsz[l]);
+    NBT_CUDA_TRY(cudaGetLastError());
+  }
   map->bsum_valid = true;
   map->bsum_version = map->version;
   return NBT_OK;
@@ -411,10 +439,16 @@ int nbt_map_create(const nbt_map_desc *desc, nbt_map *out) {
   if (rc == NBT_OK && cudaMalloc((void **)&m->d_tab, tab.size() * sizeof(int32_t)) != cudaSuccess) rc = NBT_ENOMEM;
   if (rc == NBT_OK && cudaMalloc(&m->d_stage, (size_t)m->stage_bytes) != cudaSuccess) rc = NBT_ENOMEM;
   if (rc == NBT_OK && brick == 1 && d.encoding != NBT_F32_PROB) {
-    m->bsx = (d.nx + kSkipB - 1) / kSkipB;
-    m->bsy = (d.ny + kSkipB - 1) / kSkipB;
-    m->bsz = (d.nz + kSkipB - 1) / kSkipB;
-    if (cudaMalloc((void **)&m->d_bsum, (size_t)m->bsx * m->bsy * m->bsz) != cudaSuccess) rc = NBT_ENOMEM;
+    int64_t total = 0;
+    for (int l = 0; l < kSkipLevels; ++l) {
+      const int e = kSkipB << l;
+      m->bsx[l] = (d.nx + e - 1) / e;
+      m->bsy[l] = (d.ny + e - 1) / e;
+      m->bsz[l] = (d.nz + e - 1) / e;
+      m->boff[l] = total;
+      total += (int64_t)m->bsx[l] * m->bsy[l] * m->bsz[l];
+    }
+    if (cudaMalloc((void **)&m->d_bsum, (size_t)total) != cudaSuccess) rc = NBT_ENOMEM;
   }
   if (rc == NBT_OK && cudaMemset(m->d_payload, 0, (size_t)m->payload_bytes) != cudaSuccess) rc = NBT_ECUDA;
   if (rc == NBT_OK && cudaMemcpy(m->d_tab, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
@@ -530,7 +564,9 @@ int nbt_map_info(nbt_map map, nbt_map_desc *desc, int64_t *device_bytes) {
   if (device_bytes) {
     int64_t b = map->payload_bytes + (int64_t)(map->desc.nx + map->desc.ny + map->desc.nz) * 4 + map->stage_bytes;
     if (map->d_gain) b += map->elems * 4;
-    if (map->d_bsum) b += (int64_t)map->bsx * map->bsy * map->bsz;
+    if (map->d_bsum)
+      b += map->boff[kSkipLevels - 1] +
+           (int64_t)map->bsx[kSkipLevels - 1] * map->bsy[kSkipLevels - 1] * map->bsz[kSkipLevels - 1];
     *device_bytes = b;
   }
   return NBT_OK;

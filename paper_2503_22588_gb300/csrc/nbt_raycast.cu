@@ -91,8 +91,11 @@ DevMap dev_map(nbt_map map, const void *payload) {
   m.ny = map->desc.ny;
   m.nz = map->desc.nz;
   m.bsum = map->d_bsum;
-  m.bsx = map->bsx;
-  m.bsy = map->bsy;
+  for (int l = 0; l < kSkipLevels; ++l) {
+    m.bsx[l] = map->bsx[l];
+    m.bsy[l] = map->bsy[l];
+    m.boff[l] = (int)map->boff[l];
+  }
   return m;
 }
 
@@ -313,9 +316,11 @@ __device__ __forceinline__ void walk_count(Walk &w, int &lin, uint32_t raw, uint
 // ---------------------------------------------------------------------------
 
 // Crossings k of one axis that come before the key: t(k) < T, or t(k) == T
-// when tie; the answer lies in [0, kmax].  A real-arithmetic estimate from
-// the current crossing t0 and |d| is corrected by exact evaluations, which
-// are monotone in k, so the result does not depend on the estimate.
+// when tie, with t(k) = ((b + k s) - o) (1/d), the walk's own rounded
+// operations; the answer lies in [0, kmax].  A real-arithmetic estimate from
+// the current crossing t0 and |d| is checked by two exact evaluations (the
+// predicate is monotone in k) and corrected step by step when they fail, so
+// the result never depends on the estimate.
 __device__ __forceinline__ int skip_axis_count(float b, float s, float o, float v, float ad, float t0, float T,
                                                bool tie, int kmax) {
   auto before = [&](int k) {
@@ -324,6 +329,7 @@ __device__ __forceinline__ int skip_axis_count(float b, float s, float o, float 
   };
   const float e = ceilf((T - t0) * ad);
   int c = e > 0.0f ? (e < (float)kmax ? (int)e : kmax) : 0;
+  if ((c == 0 || before(c - 1)) && (c == kmax || !before(c))) return c;
   while (c > 0 && !before(c - 1)) --c;
   while (c < kmax && before(c)) ++c;
   return c;
@@ -433,8 +439,11 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
 }
 
 // Unknown count and visited voxels of one ray on a linear state map, skipping
-// uniform bricks (see above).  Called by all 32 lanes of a warp together
-// (valid = the lane has a ray); per-ray results equal ray_ig's exactly.
+// uniform bricks (see above).  Each lane looks up the largest uniform brick of
+// the summary pyramid (8 to 64 voxels) around its current voxel; when every
+// active lane of the warp has one, each replaces the walk through it by the
+// per-axis counts up to the brick's exit.  Called by all 32 lanes of a warp
+// together (valid = the lane has a ray); per-ray results equal ray_ig's.
 template <int KIND>
 __device__ __forceinline__ void ray_count_skip(const DevMap &m, uint32_t addr_max, const float o[3], const float d[3],
                                                bool valid, uint32_t &iacc, uint32_t &steps) {
@@ -442,55 +451,73 @@ __device__ __forceinline__ void ray_count_skip(const DevMap &m, uint32_t addr_ma
   bool done = !valid || !walk_init(w, o, d, m.nx, m.ny, m.nz);
   int lin = 0;
   float adx = 0.0f, ady = 0.0f, adz = 0.0f;
+  int upx = 0, upy = 0, upz = 0;            // [s_a > 0]: the current voxel is b_a - up_a
   if (!done) {
     walk_linear_steps(w, m.nx, m.ny);
     lin = walk_linear_index(w, m.nx, m.ny);
     adx = fabsf(d[0]);
     ady = fabsf(d[1]);
     adz = fabsf(d[2]);
+    upx = w.sx > 0.0f;
+    upy = w.sy > 0.0f;
+    upz = w.sz > 0.0f;
   }
   const uint8_t *payload = (const uint8_t *)m.payload;
-  constexpr int kMask = kSkipB - 1;
   while (__any_sync(0xffffffffu, !done)) {
-    int ix = 0, iy = 0, iz = 0;
-    uint32_t sum = kSumOther;
+    int ix = 0, iy = 0, iz = 0, lvl = -1;
+    uint32_t cls = kSumOther;
     if (!done) {
-      ix = walk_index(w.bx, w.sx);
-      iy = walk_index(w.by, w.sy);
-      iz = walk_index(w.bz, w.sz);
-      sum = __ldg(m.bsum + ((int64_t)(iz >> kSkipLog) * m.bsy + (iy >> kSkipLog)) * m.bsx + (ix >> kSkipLog));
+      ix = (int)w.bx - upx;
+      iy = (int)w.by - upy;
+      iz = (int)w.bz - upz;
+      // the largest uniform brick around the voxel, from the top of the pyramid
+      uint32_t sl[kSkipLevels];
+#pragma unroll
+      for (int l = 0; l < kSkipLevels; ++l) {
+        const int sh = kSkipLog + l;
+        sl[l] = __ldg(m.bsum + m.boff[l] + ((int64_t)(iz >> sh) * m.bsy[l] + (iy >> sh)) * m.bsx[l] + (ix >> sh));
+      }
+#pragma unroll
+      for (int l = 0; l < kSkipLevels; ++l)
+        if (sl[l] <= kSumFree) {
+          lvl = l;
+          cls = sl[l];
+        }
     }
-    const bool macro = __all_sync(0xffffffffu, done || sum <= kSumFree);
+    const bool macro = __all_sync(0xffffffffu, done || lvl >= 0);
     if (done) continue;
-    // the crossings of this brick's boundary planes on each axis (index kA on axis a; t = +inf without a step)
-    const int kx = w.sx > 0.0f ? kMask - (ix & kMask) : (w.sx < 0.0f ? (ix & kMask) : 0);
-    const int ky = w.sy > 0.0f ? kMask - (iy & kMask) : (w.sy < 0.0f ? (iy & kMask) : 0);
-    const int kz = w.sz > 0.0f ? kMask - (iz & kMask) : (w.sz < 0.0f ? (iz & kMask) : 0);
-    const float tex = fmul(fsub(fadd(w.bx, (float)kx * w.sx), w.ox), w.vx);
-    const float tey = fmul(fsub(fadd(w.by, (float)ky * w.sy), w.oy), w.vy);
-    const float tez = fmul(fsub(fadd(w.bz, (float)kz * w.sz), w.oz), w.vz);
+    // exit planes of the brick (macro: the uniform one; run: the 8^3 one) and their crossings
+    const int sh = kSkipLog + (macro ? lvl : 0);
+    const float ex = (float)(((ix >> sh) + upx) << sh), ey = (float)(((iy >> sh) + upy) << sh),
+                ez = (float)(((iz >> sh) + upz) << sh);
+    const float tex = fmul(fsub(ex, w.ox), w.vx);      // +inf on an axis without a step
+    const float tey = fmul(fsub(ey, w.oy), w.vy);
+    const float tez = fmul(fsub(ez, w.oz), w.vz);
     const float T = fminf(tex, fminf(tey, tez));
-    const int A = tex == T ? 0 : (tey == T ? 1 : 2);  // the walk's tie-break: x, then y, then z
     if (macro) {
-      const bool end = !(T < w.tmax);                 // the walk ends inside this brick
+      const bool end = !(T < w.tmax);                   // the walk ends inside this brick
       const float key = end ? w.tmax : T;
-      const int cx = !end && A == 0 ? kx : skip_axis_count(w.bx, w.sx, w.ox, w.vx, adx, w.tx, key, !end && 0 < A, kx);
-      const int cy = !end && A == 1 ? ky : skip_axis_count(w.by, w.sy, w.oy, w.vy, ady, w.ty, key, !end && 1 < A, ky);
-      const int cz = !end && A == 2 ? kz : skip_axis_count(w.bz, w.sz, w.oz, w.vz, adz, w.tz, key, !end && 2 < A, kz);
-      w.bx = fadd(w.bx, (float)cx * w.sx);
-      w.by = fadd(w.by, (float)cy * w.sy);
-      w.bz = fadd(w.bz, (float)cz * w.sz);
+      const int A = end ? 3 : (tex == T ? 0 : (tey == T ? 1 : 2));  // exit axis (x-y-z tie-break)
+      // crossings of each axis inside the brick; the exit axis takes exactly those
+      const int kx = w.sx != 0.0f ? (int)fabsf(ex - w.bx) : 0;
+      const int ky = w.sy != 0.0f ? (int)fabsf(ey - w.by) : 0;
+      const int kz = w.sz != 0.0f ? (int)fabsf(ez - w.bz) : 0;
+      const int cx = A == 0 ? kx : skip_axis_count(w.bx, w.sx, w.ox, w.vx, adx, w.tx, key, 0 < A && !end, kx);
+      const int cy = A == 1 ? ky : skip_axis_count(w.by, w.sy, w.oy, w.vy, ady, w.ty, key, 1 < A && !end, ky);
+      const int cz = A == 2 ? kz : skip_axis_count(w.bz, w.sz, w.oz, w.vz, adz, w.tz, key, 2 < A && !end, kz);
+      const uint32_t nvis = 1u + (uint32_t)(cx + cy + cz);
+      steps += nvis;
+      if (cls == kSumUnknown) iacc += nvis;
+      // the state after those crossings, plus the exit crossing (T, A) itself unless the walk ends
+      const int mx = cx + (A == 0), my = cy + (A == 1), mz = cz + (A == 2);
+      w.bx = fadd(w.bx, (float)mx * w.sx);
+      w.by = fadd(w.by, (float)my * w.sy);
+      w.bz = fadd(w.bz, (float)mz * w.sz);
       w.tx = fmul(fsub(w.bx, w.ox), w.vx);
       w.ty = fmul(fsub(w.by, w.oy), w.vy);
       w.tz = fmul(fsub(w.bz, w.oz), w.vz);
-      lin += cx * w.qx + cy * w.qy + cz * w.qz;
-      const uint32_t nvis = 1u + (uint32_t)(cx + cy + cz);
-      steps += nvis;
-      if (sum == kSumUnknown) iacc += nvis;
-      if (end)
-        done = true;
-      else
-        walk_take_lin(w, A, lin);                     // the boundary crossing (T, A) itself
+      lin += mx * w.qx + my * w.qy + mz * w.qz;
+      done = end;
     } else {
       const float bx0 = w.bx, by0 = w.by, bz0 = w.bz;
       const uint32_t addr = min((uint32_t)lin, addr_max);

@@ -140,3 +140,19 @@ def test_trajectories_on_a_state_map():
     assert np.array_equal(tig.cpu().numpy(), rig.astype(np.float32))          # sums returned as FP32
     assert rig.max() > 2 ** 24                                                # (some exceed 2^24)
     m.close()
+
+
+def test_pyramid_levels_and_their_boundaries():
+    """Large uniform regions (bricks of 16, 32 and 64 voxels are uniform) next to mixed ones: free and
+    unknown halves split off any brick boundary, an unknown block and a few occupied specks."""
+    n = 160
+    grid = np.ones((n, n, n), np.uint8)
+    grid[:, :, 37:] = 0
+    grid[70:133, 5:90, 90:150] = 1
+    rng = np.random.default_rng(3)
+    for _ in range(40):
+        z, y, x = rng.integers(0, n, 3)
+        grid[z, y, x] = 2
+    pz = shell((0.8, 0.8, 0.8), 96, 0.3, 1.0, 8)
+    cam = nbt.camera(80, 72, 1.0, 0.8, 1.6)
+    run_case(grid, "u2", pz, cam, (0.003, -0.004, 0.0))
