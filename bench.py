@@ -457,25 +457,22 @@ def main() -> None:
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
+    def finish():
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+
+    runners = {"idw_cost": run_cost, "fig3": run_fig3, "insert": run_insert, "surrogate": run_surrogate}
     if args.workload == "room512-pruned":
         run_pruned(args, nbt, torch, dev, world, rank, local, dist)
-        return
-    if args.workload == "idw_cost":
-        run_cost(args, nbt, torch, dev, stream, world, rank, local, dist)
-        return
-    if args.workload == "fig3":
-        run_fig3(args, nbt, torch, dev, stream, world, rank, local, dist)
-        return
-    if args.workload == "insert":
-        run_insert(args, nbt, torch, dev, stream, world, rank, local, dist)
-        return
-    if args.workload == "surrogate":
-        run_surrogate(args, nbt, torch, dev, stream, world, rank, local, dist)
-        return
+        return finish()
+    if args.workload in runners:
+        runners[args.workload](args, nbt, torch, dev, stream, world, rank, local, dist)
+        return finish()
     w = build_workload(args.workload, rank)
     if w.offsets is not None:
         run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist)
-        return
+        return finish()
     if args.views is not None:   # a reduced launch of the same workload (profiling)
         w.poses = np.ascontiguousarray(w.poses[:args.views])
     cam = nbt.camera(w.camera.width, w.camera.height, w.camera.fov_h, w.camera.fov_v, w.camera.max_range)

@@ -36,6 +36,24 @@ constexpr int kTileH = 8;
 constexpr int kThreads = 256;          // 8 warps, each working on its own tiles
 constexpr int kPartialBytes = 16;   // one per (pose, tile) item
 
+// Brick summaries (count walks on linear state maps): a pyramid of kSkipLevels
+// levels; level l cuts the map into cubic bricks of edge 2^(kSkipLog + l)
+// aligned to the origin, and a brick's byte says whether every voxel of it
+// inside the map is unknown (kSumUnknown), every one is free (kSumFree), or
+// neither (kSumOther: mixed, or holding an occupied voxel).  Level l + 1 is
+// uniform exactly where its (up to) 8 children are uniform with one class.
+// Once the pyramid is built, each level-0 byte is rewritten as class | (L <<
+// 2), L the highest level whose brick around it is uniform, so that a walk
+// finds the largest uniform brick around a voxel with one read (L < 64).
+constexpr int kSkipLog = 3;
+constexpr int kSkipB = 1 << kSkipLog;
+#ifndef NBT_SKIP_LEVELS
+#define NBT_SKIP_LEVELS 4
+#endif
+constexpr int kSkipLevels = NBT_SKIP_LEVELS;  // bricks of 8, 16, ..., 2^(2 + kSkipLevels) voxels
+constexpr uint32_t kSumUnknown = 0, kSumFree = 1, kSumOther = 3;
+
+
 struct Partial {                    // per-tile partial sums (16 bytes)
   float fsum;                       // FP32 gain sum (F32 payloads)
   uint32_t isum;                    // unknown-voxel count (state payloads)
@@ -50,7 +68,7 @@ struct nbt_map_s {
   int device = 0;
   int brick = 8;
   int packet_w = 8;                  // warp ray packet width (nbt_map_set_tuning)
-  int skip = 0;                      // 1: count walks skip uniform bricks (nbt_map_set_tuning)
+  int skip = 1;                      // 1: count walks skip uniform bricks (nbt_map_set_tuning)
   int nbx = 0, nby = 0, nbz = 0;     // bricks per axis
   int64_t elems = 0;                 // padded element count of the bricked payload
   int64_t payload_bytes = 0;
@@ -69,8 +87,10 @@ struct nbt_map_s {
   // brick summaries of linear state maps (count walks skip uniform bricks):
   // one byte per kSkipB^3 brick, derived from the payload, rebuilt when stale
   uint8_t *d_bsum = nullptr;
-  int bsx[4] = {0}, bsy[4] = {0}, bsz[4] = {0};  // summary bricks per axis and level
-  int64_t boff[4] = {0};             // first byte of each level; boff[3] + last level size = total
+  int bsx[nbt::kSkipLevels] = {0}, bsy[nbt::kSkipLevels] = {0}, bsz[nbt::kSkipLevels] = {0};  // bricks per axis, level
+  int64_t boff[nbt::kSkipLevels] = {0};  // first byte of each level
+  int3 *d_bdims = nullptr;           // device copies of the per-level brick counts and offsets
+  int64_t *d_boffs = nullptr;
   bool bsum_valid = false;
   uint64_t bsum_version = 0;
   // point-cloud insertion scratch (nbt_map_insert_points), allocated on first use
@@ -85,17 +105,6 @@ struct nbt_map_s {
 };
 
 namespace nbt {
-
-// Brick summaries (count walks on linear state maps): a pyramid of kSkipLevels
-// levels; level l cuts the map into cubic bricks of edge 2^(kSkipLog + l)
-// aligned to the origin, and a brick's byte says whether every voxel of it
-// inside the map is unknown (kSumUnknown), every one is free (kSumFree), or
-// neither (kSumOther: mixed, or holding an occupied voxel).  Level l + 1 is
-// uniform exactly where its (up to) 8 children are uniform with one class.
-constexpr int kSkipLog = 3;
-constexpr int kSkipB = 1 << kSkipLog;
-constexpr int kSkipLevels = 4;         // bricks of 8, 16, 32 and 64 voxels
-constexpr uint32_t kSumUnknown = 0, kSumFree = 1, kSumOther = 3;
 
 // Map view passed to kernels by value.
 struct DevMap {

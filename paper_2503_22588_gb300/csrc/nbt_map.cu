@@ -230,6 +230,27 @@ __global__ void brick_summary_up_kernel(const uint8_t *__restrict__ child, int c
   }
 }
 
+// Level-0 bytes rewritten as class | (L << 2): L = the highest level whose
+// brick containing this 8^3 brick is uniform (with this brick's class).
+// Reads only its own level-0 byte and levels >= 1, so it may run in place.
+__global__ void brick_summary_levels_kernel(uint8_t *__restrict__ bsum, int bx, int by, int bz,
+                                            const int3 *__restrict__ dims, const int64_t *__restrict__ offs) {
+  const int64_t nb = (int64_t)bx * by * bz;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = bsum[b];
+    if (c > kSumFree) continue;
+    const int x = (int)(b % bx), y = (int)((b / bx) % by), z = (int)(b / ((int64_t)bx * by));
+    uint32_t lvl = 0;
+    for (int l = 1; l < kSkipLevels; ++l) {
+      const int3 d = dims[l];
+      const uint32_t p = bsum[offs[l] + ((int64_t)(z >> l) * d.y + (y >> l)) * d.x + (x >> l)];
+      if (p != c) break;
+      lvl = (uint32_t)l;
+    }
+    bsum[b] = (uint8_t)(c | (lvl << 2));
+  }
+}
+
 int grid_for(int64_t n) {
   const int64_t blocks = (n + 255) / 256;
   return (int)std::min<int64_t>(std::max<int64_t>(blocks, 1), (int64_t)sm_count() * 16);
@@ -324,6 +345,9 @@ int prepare_bsum(nbt_map map, cudaStream_t stream) {
                                                              map->bsx[l], map->bsy[l], map->bsz[l]);
     NBT_CUDA_TRY(cudaGetLastError());
   }
+  brick_summary_levels_kernel<<<grid_for(nb), 256, 0, stream>>>(map->d_bsum, map->bsx[0], map->bsy[0], map->bsz[0],
+                                                               map->d_bdims, map->d_boffs);
+  NBT_CUDA_TRY(cudaGetLastError());
   map->bsum_valid = true;
   map->bsum_version = map->version;
   return NBT_OK;
@@ -449,6 +473,14 @@ int nbt_map_create(const nbt_map_desc *desc, nbt_map *out) {
       total += (int64_t)m->bsx[l] * m->bsy[l] * m->bsz[l];
     }
     if (cudaMalloc((void **)&m->d_bsum, (size_t)total) != cudaSuccess) rc = NBT_ENOMEM;
+    // per-level brick counts and offsets for the level pass
+    int3 dims[kSkipLevels];
+    for (int l = 0; l < kSkipLevels; ++l) dims[l] = make_int3(m->bsx[l], m->bsy[l], m->bsz[l]);
+    if (rc == NBT_OK && cudaMalloc((void **)&m->d_bdims, sizeof(dims)) != cudaSuccess) rc = NBT_ENOMEM;
+    if (rc == NBT_OK && cudaMalloc((void **)&m->d_boffs, sizeof(m->boff)) != cudaSuccess) rc = NBT_ENOMEM;
+    if (rc == NBT_OK && (cudaMemcpy(m->d_bdims, dims, sizeof(dims), cudaMemcpyHostToDevice) != cudaSuccess ||
+                         cudaMemcpy(m->d_boffs, m->boff, sizeof(m->boff), cudaMemcpyHostToDevice) != cudaSuccess))
+      rc = NBT_ECUDA;
   }
   if (rc == NBT_OK && cudaMemset(m->d_payload, 0, (size_t)m->payload_bytes) != cudaSuccess) rc = NBT_ECUDA;
   if (rc == NBT_OK && cudaMemcpy(m->d_tab, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
@@ -485,6 +517,8 @@ void free_map(nbt_map map) {
   if (map->d_tab) cudaFree(map->d_tab);
   if (map->d_stage) cudaFree(map->d_stage);
   if (map->d_bsum) cudaFree(map->d_bsum);
+  if (map->d_bdims) cudaFree(map->d_bdims);
+  if (map->d_boffs) cudaFree(map->d_boffs);
   if (map->ins_hit) cudaFree(map->ins_hit);
   if (map->ins_miss) cudaFree(map->ins_miss);
   if (map->ins_count) cudaFree(map->ins_count);

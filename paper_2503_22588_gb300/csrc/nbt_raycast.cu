@@ -336,14 +336,15 @@ __device__ __forceinline__ int skip_axis_count(float b, float s, float o, float 
 }
 
 // The walk_count loop from the current voxel (payload entry raw, already
-// loaded) up to the first occupied voxel or the first crossing not before
-// tlim.  The walk state ends one crossing past the last visited voxel (so the
-// plane travel is the number visited); last = state of the last visited
-// voxel, ts_out = the crossing the loop stopped on.
+// loaded) for at most `passes` passes of three voxels, up to the first
+// occupied voxel or the first crossing not before tlim.  The walk state ends
+// one crossing past the last visited voxel (so the plane travel is the number
+// visited); last = state of the last visited voxel, ts_out = the crossing the
+// loop stopped on (before tlim if it stopped on the pass count).
 template <int KIND>
 __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, uint32_t addr, const uint8_t *payload,
-                                               uint32_t addr_max, float tlim, uint32_t &iacc, uint32_t &last,
-                                               float &ts_out) {
+                                               uint32_t addr_max, float tlim, int passes, uint32_t &iacc,
+                                               uint32_t &last, float &ts_out) {
 #define NBT_RUN_PART                                                                             \
   "min.f32 ts, %0, %1, %2;\n\t"                                                                 \
   "setp.geu.f32 pm, ts, %20;\n\t"                                                               \
@@ -374,14 +375,18 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
   "setp.gt.or.u32 pe, " CUR ", 1, pm;\n\t"
     asm volatile(
         "{\n\t"
-        ".reg .pred px, py, pz, pm, pu, pe;\n\t"
+        ".reg .pred px, py, pz, pm, pu, pe, pc;\n\t"
         ".reg .f32 ts, u;\n\t"
-        ".reg .b32 r0, r1, r2, lc;\n\t"
+        ".reg .b32 r0, r1, r2, lc, cnt;\n\t"
         ".reg .b64 a;\n\t"
         "mov.b32 r0, %10;\n\t"
+        "mov.b32 cnt, %27;\n\t"
         "LOOP:\n\t" NBT_U8_RUN("r0", "r1") "@pe bra D0;\n\t"
         NBT_U8_RUN("r1", "r2") "@pe bra D1;\n\t"
-        NBT_U8_RUN("r2", "r0") "@!pe bra LOOP;\n\t"
+        NBT_U8_RUN("r2", "r0")
+        "sub.s32 cnt, cnt, 1;\n\t"
+        "setp.ne.and.s32 pc, cnt, 0, !pe;\n\t"
+        "@pc bra LOOP;\n\t"
         "mov.b32 %8, r2;\n\t"
         "bra DONE;\n\t"
         "D0:\n\t"
@@ -395,7 +400,8 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
         : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+r"(iacc),
           "=r"(last), "=f"(ts_out)
         : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
-          "f"(w.vz), "f"(tlim), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit)
+          "f"(w.vz), "f"(tlim), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit),
+          "r"(passes)
         : "memory");
 #undef NBT_U8_RUN
   } else {
@@ -414,15 +420,19 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
     const uint32_t s_first = addr * 2u;
     asm volatile(
         "{\n\t"
-        ".reg .pred px, py, pz, pm, pu, pe;\n\t"
+        ".reg .pred px, py, pz, pm, pu, pe, pc;\n\t"
         ".reg .f32 ts, u;\n\t"
-        ".reg .b32 r0, r1, r2, s0, s1, s2, lc, wb, st;\n\t"
+        ".reg .b32 r0, r1, r2, s0, s1, s2, lc, wb, st, cnt;\n\t"
         ".reg .b64 a;\n\t"
         "mov.b32 r0, %10;\n\t"
         "mov.b32 s0, %28;\n\t"
+        "mov.b32 cnt, %29;\n\t"
         "LOOP:\n\t" NBT_U2_RUN("r0", "s0", "r1", "s1") "@pe bra DONE;\n\t"
         NBT_U2_RUN("r1", "s1", "r2", "s2") "@pe bra DONE;\n\t"
-        NBT_U2_RUN("r2", "s2", "r0", "s0") "@!pe bra LOOP;\n\t"
+        NBT_U2_RUN("r2", "s2", "r0", "s0")
+        "sub.s32 cnt, cnt, 1;\n\t"
+        "setp.ne.and.s32 pc, cnt, 0, !pe;\n\t"
+        "@pc bra LOOP;\n\t"
         "DONE:\n\t"
         "mov.b32 %8, st;\n\t"
         "mov.f32 %9, ts;\n\t"
@@ -431,12 +441,21 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
           "=r"(last), "=f"(ts_out)
         : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
           "f"(w.vz), "f"(tlim), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit),
-          "r"(two), "r"(s_first)
+          "r"(two), "r"(s_first), "r"(passes)
         : "memory");
 #undef NBT_U2_RUN
   }
 #undef NBT_RUN_PART
 }
+
+#ifndef NBT_RUN_PASSES
+#define NBT_RUN_PASSES 8
+#endif
+#ifndef NBT_SKIP_LOOKUP_LEVELS
+#define NBT_SKIP_LOOKUP_LEVELS kSkipLevels
+#endif
+constexpr int kRunPasses = NBT_RUN_PASSES;               // voxel-by-voxel stretch between two votes (passes of 3)
+constexpr int kLookupLevels = NBT_SKIP_LOOKUP_LEVELS;    // pyramid levels a lane consults (bricks 8 .. 2^(2+L))
 
 // Unknown count and visited voxels of one ray on a linear state map, skipping
 // uniform bricks (see above).  Each lane looks up the largest uniform brick of
@@ -470,31 +489,23 @@ __device__ __forceinline__ void ray_count_skip(const DevMap &m, uint32_t addr_ma
       ix = (int)w.bx - upx;
       iy = (int)w.by - upy;
       iz = (int)w.bz - upz;
-      // the largest uniform brick around the voxel, from the top of the pyramid
-      uint32_t sl[kSkipLevels];
-#pragma unroll
-      for (int l = 0; l < kSkipLevels; ++l) {
-        const int sh = kSkipLog + l;
-        sl[l] = __ldg(m.bsum + m.boff[l] + ((int64_t)(iz >> sh) * m.bsy[l] + (iy >> sh)) * m.bsx[l] + (ix >> sh));
-      }
-#pragma unroll
-      for (int l = 0; l < kSkipLevels; ++l)
-        if (sl[l] <= kSumFree) {
-          lvl = l;
-          cls = sl[l];
-        }
+      // the largest uniform brick around the voxel: its level-0 byte holds class | (level << 2)
+      const uint32_t v = __ldg(m.bsum + ((int64_t)(iz >> kSkipLog) * m.bsy[0] + (iy >> kSkipLog)) * m.bsx[0] +
+                               (ix >> kSkipLog));
+      cls = v & 3u;
+      if (cls <= kSumFree) lvl = min((int)(v >> 2), kLookupLevels - 1);
     }
     const bool macro = __all_sync(0xffffffffu, done || lvl >= 0);
     if (done) continue;
-    // exit planes of the brick (macro: the uniform one; run: the 8^3 one) and their crossings
-    const int sh = kSkipLog + (macro ? lvl : 0);
-    const float ex = (float)(((ix >> sh) + upx) << sh), ey = (float)(((iy >> sh) + upy) << sh),
-                ez = (float)(((iz >> sh) + upz) << sh);
-    const float tex = fmul(fsub(ex, w.ox), w.vx);      // +inf on an axis without a step
-    const float tey = fmul(fsub(ey, w.oy), w.vy);
-    const float tez = fmul(fsub(ez, w.oz), w.vz);
-    const float T = fminf(tex, fminf(tey, tez));
     if (macro) {
+      // exit planes of the uniform brick and their crossings
+      const int sh = kSkipLog + lvl;
+      const float ex = (float)(((ix >> sh) + upx) << sh), ey = (float)(((iy >> sh) + upy) << sh),
+                  ez = (float)(((iz >> sh) + upz) << sh);
+      const float tex = fmul(fsub(ex, w.ox), w.vx);    // +inf on an axis without a step
+      const float tey = fmul(fsub(ey, w.oy), w.vy);
+      const float tez = fmul(fsub(ez, w.oz), w.vz);
+      const float T = fminf(tex, fminf(tey, tez));
       const bool end = !(T < w.tmax);                   // the walk ends inside this brick
       const float key = end ? w.tmax : T;
       const int A = end ? 3 : (tex == T ? 0 : (tey == T ? 1 : 2));  // exit axis (x-y-z tie-break)
@@ -519,12 +530,14 @@ __device__ __forceinline__ void ray_count_skip(const DevMap &m, uint32_t addr_ma
       lin += mx * w.qx + my * w.qy + mz * w.qz;
       done = end;
     } else {
+      // every lane walks the same number of voxels (kRunPasses passes of three) before the next
+      // vote, so the lanes stay in step
       const float bx0 = w.bx, by0 = w.by, bz0 = w.bz;
       const uint32_t addr = min((uint32_t)lin, addr_max);
       const uint32_t raw = raw_load<KIND>(payload, addr);
       uint32_t last = 0u;
       float ts = 0.0f;
-      walk_count_run<KIND>(w, lin, raw, addr, payload, addr_max, fminf(T, w.tmax), iacc, last, ts);
+      walk_count_run<KIND>(w, lin, raw, addr, payload, addr_max, w.tmax, kRunPasses, iacc, last, ts);
       steps += (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
       done = last >= 2u || !(ts < w.tmax);           // occluded, or the walk's end reached
     }

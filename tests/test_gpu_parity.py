@@ -389,7 +389,7 @@ def test_packet_shapes_same_results(packet_w):
     w = configs.exact64(seed=9, n_views=16)
     gm = gpu_map(w)
     gm.set_tuning(packet_w)
-    assert gm.tuning() == {"packet_w": packet_w, "brick": 1, "skip": 0}
+    assert gm.tuning() == {"packet_w": packet_w, "brick": 1, "skip": 1}
     ig, st = views_gpu(gm, w.poses, gpu_camera(w.camera), nbt.ig_params("count"))
     rig, rst = oracle.views_ig(oracle_map(w), w.poses, oracle_camera(w.camera), oracle.params("count"))
     assert np.array_equal(st, rst) and np.array_equal(ig, rig)

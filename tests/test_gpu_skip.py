@@ -31,17 +31,19 @@ def _built():
 
 
 def run_case(grid, enc, pz, cam, origin=(0.0, 0.0, 0.0), voxel=0.01):
-    assert len(pz) * cam.width * cam.height > 466944        # the brick-skipping kernel's range
+    """Both walks of the throughput kernel (skipping on and off) against the oracle, exactly."""
+    assert len(pz) * cam.width * cam.height > 466944        # the throughput kernel's range
     m = nbt.Map.from_grid(torch.from_numpy(np.ascontiguousarray(grid)).cuda(), voxel, origin, enc)
-    m.set_tuning(8, skip=True)
-    ig, st = nbt.views_ig(m, torch.from_numpy(pz).cuda(), cam, nbt.ig_params("count"))
-    torch.cuda.synchronize()
     om = oracle.Map(np.ascontiguousarray(grid), voxel, origin)
     ocam = oracle.camera(cam.width, cam.height, cam.fov_h, cam.fov_v, cam.max_range,
                          ["corners", "centers"][cam.grid_mode], ["planar", "spherical"][cam.range_mode])
     rig, rst = oracle.views_ig(om, pz, ocam, oracle.params("count"), "f32", THREADS)
-    assert np.array_equal(st.cpu().numpy(), rst)
-    assert np.array_equal(ig.cpu().numpy().astype(np.float64), rig)
+    for skip in (True, False):
+        m.set_tuning(8, skip=skip)
+        ig, st = nbt.views_ig(m, torch.from_numpy(pz).cuda(), cam, nbt.ig_params("count"))
+        torch.cuda.synchronize()
+        assert np.array_equal(st.cpu().numpy(), rst), skip
+        assert np.array_equal(ig.cpu().numpy().astype(np.float64), rig), skip
     m.close()
     return rst
 
