@@ -310,14 +310,15 @@ int nbt_plan_destroy(nbt_plan plan);
  * the Python package).  packet_w: width of a warp's ray packet in pixels,
  * 4, 8, 16 or 32 (height 32 / packet_w; 0 = default 8).  brick: read-only
  * in nbt_map_get_tuning (the brick edge is fixed at nbt_map_create).
- * skip: 1 (the default) lets unknown-count walks on linear state maps
- * (1-byte and 2-bit) replace the voxel-by-voxel walk through a brick whose
- * voxels are all unknown or all free -- the largest such cube of 8, 16, 32
- * or 64 voxels aligned to the map origin around the current voxel -- by
- * per-axis crossing counts (used by calls with enough rays to fill the GPU);
- * 0 always walks voxel by voxel.  Only speed changes: every setting visits
- * the same voxels and returns the same per-ray sums (per-perspective sums
- * may differ in FP32 rounding order). */
+ * skip: 1 (the default) lets walks on linear maps replace the voxel-by-voxel
+ * walk through a uniform brick -- the largest cube of 8, 16, 32 or 64
+ * voxels aligned to the map origin around the current voxel whose voxels
+ * are all unknown or all free (state maps), or whose derived gains are all
+ * exactly 1 or all exactly 0 (probability maps) -- by per-axis crossing
+ * counts (used by calls with enough rays to fill the GPU); 0 always walks
+ * voxel by voxel.  Only speed changes: every setting visits the same voxels
+ * and returns the same unknown counts; FP32 gain sums may differ in their
+ * rounding order (a brick's unit gains are added at once). */
 typedef struct {
   int32_t packet_w;
   int32_t brick;

@@ -84,6 +84,7 @@ struct nbt_map_s {
   int gain_metric = -1;
   float gain_occ = 0.0f, gain_free = 0.0f;
   uint64_t gain_version = 0;
+  uint64_t gain_gen = 0;             // bumped whenever the gains are derived anew
   // brick summaries of linear state maps (count walks skip uniform bricks):
   // one byte per kSkipB^3 brick, derived from the payload, rebuilt when stale
   uint8_t *d_bsum = nullptr;
@@ -92,7 +93,8 @@ struct nbt_map_s {
   int3 *d_bdims = nullptr;           // device copies of the per-level brick counts and offsets
   int64_t *d_boffs = nullptr;
   bool bsum_valid = false;
-  uint64_t bsum_version = 0;
+  uint64_t bsum_key = 0;             // what the summaries were built from: the payload version (state
+                                     // maps) or the gain generation (FP32 maps)
   // point-cloud insertion scratch (nbt_map_insert_points), allocated on first use
   uint32_t *ins_hit = nullptr;       // hit bitmap, one bit per voxel, zero between calls
   uint32_t *ins_miss = nullptr;      // miss bitmap, likewise
@@ -487,7 +489,7 @@ int check_map(nbt_map map);                 // NBT_EINVAL unless a live map on t
 bool map_alive(nbt_map map, uint64_t id);   // live, and (id != 0) created with that id
 void free_map(nbt_map map);                 // release a map's memory (no registry update)
 int prepare_gain(nbt_map map, const nbt_ig_params *params, cudaStream_t stream);
-int prepare_bsum(nbt_map map, cudaStream_t stream);  // (re)build the brick summaries of a linear state map
+int prepare_bsum(nbt_map map, cudaStream_t stream);  // (re)build stale brick summaries (after prepare_gain on FP32 maps)
 int payload_kind(nbt_map map, const nbt_ig_params *params, PayloadKind *kind, const void **payload);
 int sm_count();
 int ensure_insert_scratch(nbt_map map, int64_t n_points);  // defined in nbt_insert.cu

@@ -209,6 +209,33 @@ __global__ void brick_summary_kernel(const uint8_t *__restrict__ payload, int nx
   }
 }
 
+// Brick summaries of a linear FP32 map from its derived signed-gain table (one
+// thread per kSkipB^3 brick): kSumUnknown where every gain inside the map is
+// exactly +1 (an unknown voxel under all three metrics), kSumFree where every
+// one is exactly +0, else kSumOther (an occupied voxel, or gains that vary).
+__global__ void brick_summary_gain_kernel(const float *__restrict__ gain, int nx, int ny, int nz, int bsx, int bsy,
+                                          int bsz, uint8_t *__restrict__ bsum) {
+  const int64_t nb = (int64_t)bsx * bsy * bsz;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    const int x0 = (int)(b % bsx) * kSkipB;
+    const int y0 = (int)((b / bsx) % bsy) * kSkipB;
+    const int z0 = (int)(b / ((int64_t)bsx * bsy)) * kSkipB;
+    const int x1 = min(x0 + kSkipB, nx), y1 = min(y0 + kSkipB, ny), z1 = min(z0 + kSkipB, nz);
+    const uint32_t first = __float_as_uint(gain[((int64_t)z0 * ny + y0) * nx + x0]);
+    bool uniform = first == 0x3f800000u || first == 0u;
+    for (int z = z0; z < z1 && uniform; ++z)
+      for (int y = y0; y < y1 && uniform; ++y) {
+        const int64_t row = ((int64_t)z * ny + y) * nx;
+        for (int x = x0; x < x1; ++x)
+          if (__float_as_uint(gain[row + x]) != first) {
+            uniform = false;
+            break;
+          }
+      }
+    bsum[b] = (uint8_t)(!uniform ? kSumOther : (first == 0u ? kSumFree : kSumUnknown));
+  }
+}
+
 // Level l + 1 of the summary pyramid from level l (one thread per brick):
 // uniform with class c exactly where every child inside the map is uniform
 // with class c.
@@ -316,6 +343,7 @@ int prepare_gain(nbt_map map, const nbt_ig_params *prm, cudaStream_t stream) {
                                                                map->elems, prm->metric, prm->occ_threshold,
                                                                prm->free_threshold);
   NBT_CUDA_TRY(cudaGetLastError());
+  map->gain_gen += 1;               // summaries built from older gains are stale
   map->gain_valid = true;
   map->gain_metric = prm->metric;
   map->gain_occ = prm->occ_threshold;
@@ -324,14 +352,18 @@ int prepare_gain(nbt_map map, const nbt_ig_params *prm, cudaStream_t stream) {
   return NBT_OK;
 }
 
-int prepare_bsum(nbt_map map, cudaStream_t stream) {
-  std::lock_guard<std::mutex> lock(map->mu);
-  if (!map->d_bsum) return NBT_OK;
-  if (map->bsum_valid && map->bsum_version == map->version) return NBT_OK;
+namespace {
+
+// The pyramid from the payload (state maps) or the derived gains (FP32 maps);
+// the caller holds the map's lock.
+int build_bsum(nbt_map map, cudaStream_t stream) {
   const nbt_map_desc &d = map->desc;
   const int64_t nb = (int64_t)map->bsx[0] * map->bsy[0] * map->bsz[0];
   const uint8_t *p = (const uint8_t *)map->d_payload;
-  if (d.encoding == NBT_U2_STATE)
+  if (d.encoding == NBT_F32_PROB)
+    brick_summary_gain_kernel<<<grid_for(nb), 256, 0, stream>>>(map->d_gain, d.nx, d.ny, d.nz, map->bsx[0],
+                                                               map->bsy[0], map->bsz[0], map->d_bsum);
+  else if (d.encoding == NBT_U2_STATE)
     brick_summary_kernel<NBT_U2_STATE><<<grid_for(nb), 256, 0, stream>>>(p, d.nx, d.ny, d.nz, map->bsx[0],
                                                                          map->bsy[0], map->bsz[0], map->d_bsum);
   else
@@ -349,8 +381,21 @@ int prepare_bsum(nbt_map map, cudaStream_t stream) {
                                                                map->d_bdims, map->d_boffs);
   NBT_CUDA_TRY(cudaGetLastError());
   map->bsum_valid = true;
-  map->bsum_version = map->version;
+  map->bsum_key = d.encoding == NBT_F32_PROB ? map->gain_gen : map->version;
   return NBT_OK;
+}
+
+}  // namespace
+
+// Rebuild the summaries when the payload (state maps) or the derived gains
+// (FP32 maps; prepare_gain runs first) changed since they were built.  Only
+// the calls that run the skipping walk ask for them.
+int prepare_bsum(nbt_map map, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lock(map->mu);
+  if (!map->d_bsum) return NBT_OK;
+  const uint64_t key = map->desc.encoding == NBT_F32_PROB ? map->gain_gen : map->version;
+  if (map->bsum_valid && map->bsum_key == key) return NBT_OK;
+  return build_bsum(map, stream);
 }
 
 int payload_kind(nbt_map map, const nbt_ig_params *prm, PayloadKind *kind, const void **payload) {
@@ -462,7 +507,7 @@ int nbt_map_create(const nbt_map_desc *desc, nbt_map *out) {
     rc = NBT_ENOMEM;
   if (rc == NBT_OK && cudaMalloc((void **)&m->d_tab, tab.size() * sizeof(int32_t)) != cudaSuccess) rc = NBT_ENOMEM;
   if (rc == NBT_OK && cudaMalloc(&m->d_stage, (size_t)m->stage_bytes) != cudaSuccess) rc = NBT_ENOMEM;
-  if (rc == NBT_OK && brick == 1 && d.encoding != NBT_F32_PROB) {
+  if (rc == NBT_OK && brick == 1) {
     int64_t total = 0;
     for (int l = 0; l < kSkipLevels; ++l) {
       const int e = kSkipB << l;

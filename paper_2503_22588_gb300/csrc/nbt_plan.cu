@@ -40,7 +40,8 @@ int nbt_plan_create_traj(nbt_map map, const nbt_pose *poses, int64_t n_poses, co
   PayloadKind kind;
   const void *payload = nullptr;
   rc = payload_kind(map, params, &kind, &payload);
-  if (rc == NBT_OK) rc = kind == PAYLOAD_GAIN_F32 ? prepare_gain(map, params, s) : (map->skip ? prepare_bsum(map, s) : NBT_OK);
+  if (rc == NBT_OK && kind == PAYLOAD_GAIN_F32) rc = prepare_gain(map, params, s);
+  if (rc == NBT_OK && map->skip) rc = prepare_bsum(map, s);  // built outside the graph, refreshed per launch
   if (rc == NBT_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = NBT_ECUDA;
   nbt_plan p = nullptr;
   if (rc == NBT_OK) {
@@ -92,8 +93,8 @@ int nbt_plan_launch(nbt_plan plan, void *stream) {
   rc = payload_kind(plan->map, &plan->params, &kind, &payload);
   if (rc != NBT_OK) return rc;
   // derived data (gains, brick summaries) are refreshed outside the graph: no-ops unless the map changed
-  rc = kind == PAYLOAD_GAIN_F32 ? prepare_gain(plan->map, &plan->params, s)
-                                : (plan->map->skip ? prepare_bsum(plan->map, s) : NBT_OK);
+  if (kind == PAYLOAD_GAIN_F32) rc = prepare_gain(plan->map, &plan->params, s);
+  if (rc == NBT_OK && plan->map->skip) rc = prepare_bsum(plan->map, s);
   if (rc != NBT_OK) return rc;
   NBT_CUDA_TRY(cudaGraphLaunch(plan->exec, s));
   return NBT_OK;

@@ -448,6 +448,98 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
 #undef NBT_RUN_PART
 }
 
+// The walk_gain_f32 loop (FP32 signed gains) from the current voxel, for at
+// most `passes` passes of three voxels, up to the first occupied voxel or the
+// first crossing not before tlim; outputs as walk_count_run (last = the raw
+// gain entry of the last visited voxel: negative when occupied).
+template <bool HIT>
+__device__ __forceinline__ void walk_gain_run(Walk &w, int &lin, uint32_t raw, const float *payload,
+                                              uint32_t addr_max, float tlim, int passes, float &facc, uint32_t &last,
+                                              float &ts_out) {
+#define NBT_GRUN_PART                                                                            \
+  "min.f32 ts, %0, %1, %2;\n\t"                                                                 \
+  "setp.geu.f32 pm, ts, %20;\n\t"                                                               \
+  "setp.eq.f32 px, %0, ts;\n\t"                                                                 \
+  "setp.eq.and.f32 py, %1, ts, !px;\n\t"                                                        \
+  "setp.neu.and.f32 pz, %1, ts, !px;\n\t"                                                       \
+  "@px add.rn.f32 %3, %3, %11;\n\t"                                                             \
+  "@px sub.rn.f32 u, %3, %14;\n\t"                                                              \
+  "@px mul.rn.f32 %0, u, %17;\n\t"                                                              \
+  "@px mad.lo.s32 %6, %21, %26, %6;\n\t"                                                        \
+  "@py add.rn.f32 %4, %4, %12;\n\t"                                                             \
+  "@py sub.rn.f32 u, %4, %15;\n\t"                                                              \
+  "@py mul.rn.f32 %1, u, %18;\n\t"                                                              \
+  "@py mad.lo.s32 %6, %22, %26, %6;\n\t"                                                        \
+  "@pz add.rn.f32 %5, %5, %13;\n\t"                                                             \
+  "@pz sub.rn.f32 u, %5, %16;\n\t"                                                              \
+  "@pz mul.rn.f32 %2, u, %19;\n\t"                                                              \
+  "@pz mad.lo.s32 %6, %23, %26, %6;\n\t"                                                        \
+  "min.u32 lc, %6, %25;\n\t"                                                                    \
+  "mad.wide.u32 a, lc, 4, %24;\n\t"
+#define NBT_GRUN_HIT(CUR, NXT)                                                                   \
+  NBT_GRUN_PART                                                                                  \
+  "@!pm ld.global.nc.b32 " NXT ", [a];\n\t"                                                     \
+  "abs.f32 g, " CUR ";\n\t"                                                                     \
+  "setp.lt.or.s32 pe, " CUR ", 0, pm;\n\t"                                                      \
+  "add.rn.f32 %7, %7, g;\n\t"
+#define NBT_GRUN_MISS(CUR, NXT)                                                                  \
+  NBT_GRUN_PART                                                                                  \
+  "@!pm ld.global.nc.b32 " NXT ", [a];\n\t"                                                     \
+  "abs.f32 g, " CUR ";\n\t"                                                                     \
+  "setp.lt.s32 po, " CUR ", 0;\n\t"                                                             \
+  "or.pred pe, pm, po;\n\t"                                                                     \
+  "@!po add.rn.f32 %7, %7, g;\n\t"
+#define NBT_GRUN_LOOP(BODY)                                                                      \
+  "mov.b32 r0, %10;\n\t"                                                                        \
+  "mov.b32 cnt, %27;\n\t"                                                                       \
+  "LOOP:\n\t" BODY("r0", "r1") "@pe bra D0;\n\t" BODY("r1", "r2") "@pe bra D1;\n\t"             \
+  BODY("r2", "r0")                                                                               \
+  "sub.s32 cnt, cnt, 1;\n\t"                                                                    \
+  "setp.ne.and.s32 pc, cnt, 0, !pe;\n\t"                                                        \
+  "@pc bra LOOP;\n\t"                                                                           \
+  "mov.b32 %8, r2;\n\t"                                                                         \
+  "bra DONE;\n\t"                                                                               \
+  "D0:\n\t"                                                                                     \
+  "mov.b32 %8, r0;\n\t"                                                                         \
+  "bra DONE;\n\t"                                                                               \
+  "D1:\n\t"                                                                                     \
+  "mov.b32 %8, r1;\n\t"                                                                         \
+  "DONE:\n\t"                                                                                   \
+  "mov.f32 %9, ts;\n\t"
+  const int unit = c_unit;
+  if (HIT) {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred px, py, pz, pm, pe, pc;\n\t"
+        ".reg .f32 ts, u, g;\n\t"
+        ".reg .b32 r0, r1, r2, lc, cnt;\n\t"
+        ".reg .b64 a;\n\t" NBT_GRUN_LOOP(NBT_GRUN_HIT) "}"
+        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+f"(facc),
+          "=r"(last), "=f"(ts_out)
+        : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
+          "f"(w.vz), "f"(tlim), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit),
+          "r"(passes)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred px, py, pz, pm, po, pe, pc;\n\t"
+        ".reg .f32 ts, u, g;\n\t"
+        ".reg .b32 r0, r1, r2, lc, cnt;\n\t"
+        ".reg .b64 a;\n\t" NBT_GRUN_LOOP(NBT_GRUN_MISS) "}"
+        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+f"(facc),
+          "=r"(last), "=f"(ts_out)
+        : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
+          "f"(w.vz), "f"(tlim), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit),
+          "r"(passes)
+        : "memory");
+  }
+#undef NBT_GRUN_LOOP
+#undef NBT_GRUN_MISS
+#undef NBT_GRUN_HIT
+#undef NBT_GRUN_PART
+}
+
 #ifndef NBT_RUN_PASSES
 #define NBT_RUN_PASSES 8
 #endif
@@ -457,15 +549,17 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
 constexpr int kRunPasses = NBT_RUN_PASSES;               // voxel-by-voxel stretch between two votes (passes of 3)
 constexpr int kLookupLevels = NBT_SKIP_LOOKUP_LEVELS;    // pyramid levels a lane consults (bricks 8 .. 2^(2+L))
 
-// Unknown count and visited voxels of one ray on a linear state map, skipping
-// uniform bricks (see above).  Each lane looks up the largest uniform brick of
+// IG and visited voxels of one ray on a linear map, skipping uniform bricks
+// (see above): unknown counts on state maps (KIND U8 / U2, into iacc), or FP32
+// gains (KIND GAIN_F32, into facc: a uniform brick's voxels all have gain
+// exactly 1 or 0, so the brick adds its visited count or nothing).  Each lane looks up the largest uniform brick of
 // the summary pyramid (8 to 64 voxels) around its current voxel; when every
 // active lane of the warp has one, each replaces the walk through it by the
 // per-axis counts up to the brick's exit.  Called by all 32 lanes of a warp
 // together (valid = the lane has a ray); per-ray results equal ray_ig's.
-template <int KIND>
-__device__ __forceinline__ void ray_count_skip(const DevMap &m, uint32_t addr_max, const float o[3], const float d[3],
-                                               bool valid, uint32_t &iacc, uint32_t &steps) {
+template <int KIND, bool HIT>
+__device__ __forceinline__ void ray_skip(const DevMap &m, uint32_t addr_max, const float o[3], const float d[3],
+                                         bool valid, float &facc, uint32_t &iacc, uint32_t &steps) {
   Walk w;
   bool done = !valid || !walk_init(w, o, d, m.nx, m.ny, m.nz);
   int lin = 0;
@@ -518,7 +612,12 @@ __device__ __forceinline__ void ray_count_skip(const DevMap &m, uint32_t addr_ma
       const int cz = A == 2 ? kz : skip_axis_count(w.bz, w.sz, w.oz, w.vz, adz, w.tz, key, 2 < A && !end, kz);
       const uint32_t nvis = 1u + (uint32_t)(cx + cy + cz);
       steps += nvis;
-      if (cls == kSumUnknown) iacc += nvis;
+      if (cls == kSumUnknown) {
+        if constexpr (KIND == PAYLOAD_GAIN_F32)
+          facc = fadd(facc, (float)nvis);       // nvis voxels of gain exactly 1
+        else
+          iacc += nvis;
+      }
       // the state after those crossings, plus the exit crossing (T, A) itself unless the walk ends
       const int mx = cx + (A == 0), my = cy + (A == 1), mz = cz + (A == 2);
       w.bx = fadd(w.bx, (float)mx * w.sx);
@@ -537,9 +636,16 @@ __device__ __forceinline__ void ray_count_skip(const DevMap &m, uint32_t addr_ma
       const uint32_t raw = raw_load<KIND>(payload, addr);
       uint32_t last = 0u;
       float ts = 0.0f;
-      walk_count_run<KIND>(w, lin, raw, addr, payload, addr_max, w.tmax, kRunPasses, iacc, last, ts);
+      bool occ;
+      if constexpr (KIND == PAYLOAD_GAIN_F32) {
+        walk_gain_run<HIT>(w, lin, raw, (const float *)m.payload, addr_max, w.tmax, kRunPasses, facc, last, ts);
+        occ = (int32_t)last < 0;                     // sign bit: occupied
+      } else {
+        walk_count_run<KIND>(w, lin, raw, addr, payload, addr_max, w.tmax, kRunPasses, iacc, last, ts);
+        occ = last >= 2u;
+      }
       steps += (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
-      done = last >= 2u || !(ts < w.tmax);           // occluded, or the walk's end reached
+      done = occ || !(ts < w.tmax);                  // occluded, or the walk's end reached
     }
   }
 }
@@ -658,9 +764,12 @@ __device__ __forceinline__ void ray_ig_chunked(const void *payload, uint32_t add
 // casts packet w of the tile; the 8 packet sums are added in warp order
 // into partials[item].  CHUNK > 0 (linear layout only) walks CHUNK voxels
 // ahead of the reads (ray_ig_chunked).  SKIP (linear state maps, count
-// metric) skips uniform bricks (ray_count_skip).
+// metric, or FP32 gains) skips uniform bricks (ray_skip).
+#ifndef NBT_SKIP_MIN_BLOCKS
+#define NBT_SKIP_MIN_BLOCKS 5
+#endif
 template <int KIND, bool HIT, bool LINEAR, int CHUNK, bool SKIP = false>
-__global__ void __launch_bounds__(kThreads, SKIP ? 4 : (CHUNK ? 4 : (LINEAR ? 6 : 5)))
+__global__ void __launch_bounds__(kThreads, SKIP ? NBT_SKIP_MIN_BLOCKS : (CHUNK ? 4 : (LINEAR ? 6 : 5)))
     ig_tiles_kernel(DevMap m, CamConst cc, const float *__restrict__ poses, int64_t n_items, uint32_t addr_max,
                     unsigned long long *queue, Partial *partials) {
   extern __shared__ int32_t stab[];
@@ -706,7 +815,7 @@ __global__ void __launch_bounds__(kThreads, SKIP ? 4 : (CHUNK ? 4 : (LINEAR ? 6 
     if constexpr (SKIP) {
       float o[3] = {0.0f, 0.0f, 0.0f}, d[3] = {0.0f, 0.0f, 0.0f};
       if (inside) ray_segment_rot(cc, s_pose, s_rot, i, j, o, d);
-      ray_count_skip<KIND>(m, addr_max, o, d, inside, iacc, steps);   // all lanes together
+      ray_skip<KIND, HIT>(m, addr_max, o, d, inside, facc, iacc, steps);   // all lanes together
     } else if (inside) {
       float o[3], d[3];
       ray_segment_rot(cc, s_pose, s_rot, i, j, o, d);
@@ -1114,10 +1223,13 @@ int launch_tiles_linear(nbt_map map, const void *payload, const CamConst &cc, co
   if (n_rays <= kSplit8Rays) return launch_split<KIND, HIT, 8>(map, payload, cc, poses, n_items, workspace, stream);
   if (n_rays <= 2 * (int64_t)sm_count() * per_sm * kThreads)
     return launch_tiles_t<KIND, HIT, true, kChunk>(map, payload, cc, poses, n_items, workspace, stream);
-  if constexpr (KIND != PAYLOAD_GAIN_F32) {
-    // state maps (unknown count): skip uniform bricks; the occupied voxel adds nothing, so HIT is moot
-    if (map->skip && map->d_bsum && map->bsum_valid)
-      return launch_tiles_t<KIND, true, true, 0, true>(map, payload, cc, poses, n_items, workspace, stream);
+  if (map->skip && map->d_bsum) {
+    // skip uniform bricks (summaries built here, only for the calls that use them); on state maps the
+    // occupied voxel adds nothing, so HIT is moot there
+    rc = prepare_bsum(map, stream);
+    if (rc != NBT_OK) return rc;
+    constexpr bool H = KIND == PAYLOAD_GAIN_F32 ? HIT : true;
+    return launch_tiles_t<KIND, H, true, 0, true>(map, payload, cc, poses, n_items, workspace, stream);
   }
   return launch_tiles_t<KIND, HIT, true, 0>(map, payload, cc, poses, n_items, workspace, stream);
 }
@@ -1158,9 +1270,6 @@ int run_tiles(nbt_map map, const nbt_pose *poses, int64_t n_poses, const nbt_cam
     return NBT_EWORKSPACE;
   if (kind == PAYLOAD_GAIN_F32) {
     rc = prepare_gain(map, params, stream);
-    if (rc != NBT_OK) return rc;
-  } else if (map->skip) {
-    rc = prepare_bsum(map, stream);
     if (rc != NBT_OK) return rc;
   }
   const float *pp = (const float *)poses;
@@ -1415,6 +1524,7 @@ extern "C" int nbt_map_set_tuning(nbt_map map, const nbt_tuning *tuning) {
   const int pw = tuning->packet_w == 0 ? 8 : tuning->packet_w;
   if (pw != 4 && pw != 8 && pw != 16 && pw != 32) return NBT_EINVAL;
   if (tuning->skip != 0 && tuning->skip != 1) return NBT_EINVAL;
+  std::lock_guard<std::mutex> lock(map->mu);
   map->packet_w = pw;
   map->skip = tuning->skip;
   return NBT_OK;

@@ -1,12 +1,14 @@
-"""Count walks that skip uniform bricks, against the oracle (GPU required).
+"""Walks that skip uniform bricks, against the oracle (GPU required).
 
-On linear 1-byte and 2-bit state maps with brick skipping switched on (nbt_map_set_tuning), calls
-with many rays run the tile kernel that replaces the walk through a brick of 8^3 voxels that are all unknown or all free by per-axis crossing counts
-(the same FP32 crossing parameters as the voxel-by-voxel walk).  Every case here has more than
+On linear maps with brick skipping on (the default; nbt_map_set_tuning), calls with many rays run
+the tile kernel that replaces the walk through a uniform brick (8 to 64 voxels, all unknown or all
+free; on probability maps, all gains exactly 1 or exactly 0) by per-axis crossing counts (the same
+FP32 crossing parameters as the voxel-by-voxel walk).  Every case here has more than
 466,944 rays per call, so that kernel runs, and the voxel steps and unknown counts of every view
-must equal the oracle's exactly: maps of every brick class, sides that are not multiples of 8,
-an origin off the voxel grid, cameras inside and outside the map, both grid and range modes, the
-map updated between calls (the summaries must be rebuilt), and trajectory IG.
+must equal the oracle's exactly -- the FP32 gains of probability maps within 1e-5 relative -- with
+skipping on and off: maps of every brick class, sides that are not multiples of 8, an origin off
+the voxel grid, cameras inside and outside the map, both grid and range modes, all three metrics,
+the map updated between calls (the summaries must be rebuilt), and trajectory IG.
 """
 
 import numpy as np
@@ -158,3 +160,54 @@ def test_pyramid_levels_and_their_boundaries():
     pz = shell((0.8, 0.8, 0.8), 96, 0.3, 1.0, 8)
     cam = nbt.camera(80, 72, 1.0, 0.8, 1.6)
     run_case(grid, "u2", pz, cam, (0.003, -0.004, 0.0))
+
+
+def run_f32_case(grid, pz, cam, prm_name, origin=(0.0, 0.0, 0.0), occ=0.7, free=0.3):
+    """FP32 probability map: both walks against the FP64 oracle -- voxel steps exactly, IG within
+    1e-5 relative (skipping adds a brick's unit gains at once, so per-ray FP32 sums round differently)."""
+    assert len(pz) * cam.width * cam.height > 466944
+    m = nbt.Map.from_grid(torch.from_numpy(np.ascontiguousarray(grid)).cuda(), 0.01, origin, "f32")
+    om = oracle.Map(np.ascontiguousarray(grid), 0.01, origin)
+    ocam = oracle.camera(cam.width, cam.height, cam.fov_h, cam.fov_v, cam.max_range)
+    rig, rst = oracle.views_ig(om, pz, ocam, oracle.params(prm_name, occ, free), "f32", THREADS)
+    for skip in (True, False):
+        m.set_tuning(8, skip=skip)
+        ig, st = nbt.views_ig(m, torch.from_numpy(pz).cuda(), cam, nbt.ig_params(prm_name, occ, free))
+        torch.cuda.synchronize()
+        assert np.array_equal(st.cpu().numpy(), rst), (prm_name, skip)
+        rel = np.abs(ig.cpu().numpy().astype(np.float64) - rig) / np.maximum(np.abs(rig), 1e-30)
+        assert rel.max() <= 1e-5, (prm_name, skip, rel.max())
+    m.close()
+
+
+@pytest.mark.parametrize("metric", ["entropy", "eq2", "count"])
+def test_probability_tabletop_every_metric(metric):
+    """The tabletop's unknown half and the unknown space under the table are uniform bricks of gain 1."""
+    w = configs.prob256(seed=2, n_views=64, n=128, n_prims=60)
+    cam = nbt.camera(96, 96, w.camera.fov_h, w.camera.fov_v, 1.0)
+    run_f32_case(w.grid, w.poses, cam, metric)
+
+
+def test_probability_summaries_follow_metric_thresholds_and_uploads():
+    """Gains (and with them the brick summaries) are derived per metric and thresholds and after an
+    upload: alternate them on one map and compare every call with the oracle."""
+    w = configs.prob256(seed=3, n_views=64, n=96, n_prims=40)
+    cam = nbt.camera(96, 96, w.camera.fov_h, w.camera.fov_v, 1.0)
+    grid = w.grid.copy()
+    m = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01, (0.0, 0.0, 0.0), "f32")
+    m.set_tuning(8, skip=True)
+    ocam = oracle.camera(96, 96, w.camera.fov_h, w.camera.fov_v, 1.0)
+    pt = torch.from_numpy(w.poses).cuda()
+    for step, (metric, occ, free) in enumerate([("entropy", 0.7, 0.3), ("count", 0.7, 0.3), ("eq2", 0.6, 0.45),
+                                                ("entropy", 0.7, 0.3), ("count", 0.7, 0.3)]):
+        if step == 3:
+            grid[:, :, 20:40] = 0.5                          # a new unknown slab, uploaded
+            m.upload(torch.from_numpy(grid).cuda())
+        ig, st = nbt.views_ig(m, pt, cam, nbt.ig_params(metric, occ, free))
+        torch.cuda.synchronize()
+        rig, rst = oracle.views_ig(oracle.Map(grid), w.poses, ocam, oracle.params(metric, occ, free), "f32",
+                                   THREADS)
+        assert np.array_equal(st.cpu().numpy(), rst), step
+        rel = np.abs(ig.cpu().numpy().astype(np.float64) - rig) / np.maximum(np.abs(rig), 1e-30)
+        assert rel.max() <= 1e-5, (step, rel.max())
+    m.close()
