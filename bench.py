@@ -71,7 +71,7 @@ def load_peaks() -> tuple[float, str]:
 
 
 def ncu_traffic(workload: str):
-    """DRAM bytes per launch of the tile kernel from the committed ncu summary, if current."""
+    """DRAM bytes per launch (per forward of the batch, for the surrogate) from the committed ncu summary, if current."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     t = json.load(open(TRAFFIC_FILE)).get(workload)
@@ -1454,7 +1454,7 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
                      "algorithmic": f"0.25 B per voxel step x {steps_per_launch:.0f} steps per launch",
                      "peak_kind": f"{hbm_kind} (hbm_gbs)"},
         "roofline_surrogate": {"bound": "tensor", "achieved": s_achieved, "peak": bf16, "unit": "TFLOP/s",
-                               "frac": s_achieved / bf16, "traffic": None,
+                               "frac": s_achieved / bf16, "traffic": ncu_traffic("surrogate_forward"),
                                "kernel": "surrogate forward (fused layers 0-1, layers 2-3, fc1, fc2)",
                                "algorithmic": f"{fl} FLOP per view (layer 0 as its K = 112 one-hot GEMM) x {n_views}",
                                "forward_ms_per_step": fwd_mean, "peak_kind": bf16_kind},
