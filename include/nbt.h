@@ -368,7 +368,9 @@ int nbt_tc_wait_probe(void *stream);
  * samples on the rays through the pixel centres of a 32 x 32 image of the
  * field of view, at depth fractions (k + 1/2) / 32 of d_Cam, each the class
  * of the voxel holding it as a uint8 code (0 outside the map, 1 unknown,
- * 2 free, 3 occupied), [n][32 (depth k)][32 (row j)][32 (column i)] -- and 8
+ * 2 free, 3 occupied), [n][32 (depth k)][32 (row j)][32 (column i)], the
+ * array 16-byte aligned (every call that takes crops returns NBT_EINVAL
+ * otherwise) -- and 8
  * BF16 pose features ((position - origin) / map extent, the quaternion, 1).
  * The network sees code c as the one-hot vector with a 1 in channel c - 1 of
  * 8 (all zero for code 0).  Output: the predicted mean ray IG (the training target

@@ -302,32 +302,34 @@ __global__ void __launch_bounds__(256) crop_kernel(DevMap m, CropConst cc, const
     const int dims[3] = {m.nx, m.ny, m.nz};
     uint8_t *cv = crops + v * (int64_t)(kCrop * kCrop * kCrop);
     // Sample (i, j, k) of cell i + 32 j + 1024 k.  With 256 threads a thread
-    // keeps i = tid % 32 and takes j = tid / 32 + 8 q (q = 0..3) for every
-    // k, so the factors that depend on i or k alone are formed once per k;
-    // each sample still runs the same operations in the same order.
-    const int i = threadIdx.x & 31, j0 = threadIdx.x >> 5;
-    const float cx = fadd(cc.x0, fmul((float)i, cc.xs));
-    float cyq[4];
+    // keeps the four samples i = 4 (tid % 8) .. 4 (tid % 8) + 3 of row j =
+    // tid / 8 for every k, so the factors that depend on i, j or k alone are
+    // formed once and the row's four codes leave in one 32-bit store; each
+    // sample still runs the same operations in the same order.
+    const int i0 = (threadIdx.x & 7) * 4, j = threadIdx.x >> 3;
+    float cxq[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) cyq[q] = fadd(cc.y0, fmul((float)(j0 + 8 * q), cc.ys));
+    for (int q = 0; q < 4; ++q) cxq[q] = fadd(cc.x0, fmul((float)(i0 + q), cc.xs));
+    const float cy = fadd(cc.y0, fmul((float)j, cc.ys));
+    uint32_t *cw = (uint32_t *)(cv + j * 32 + i0);
     for (int k = 0; k < kCrop; ++k) {
       const float fr = fmul(fadd((float)k, 0.5f), 0.03125f);  // (k + 1/2) / 32, exact
-      const float px = fmul(cx, fr), pz = fmul(cc.zc, fr);
-      float rx[3], rz[3];
+      const float py = fmul(cy, fr), pz = fmul(cc.zc, fr);
+      float ry[3], rz[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        rx[a] = fmul(r[3 * a], px);
+        ry[a] = fmul(r[3 * a + 1], py);
         rz[a] = fmul(r[3 * a + 2], pz);
       }
+      uint32_t word = 0u;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float py = fmul(cyq[q], fr);
-        const int cell = k * 1024 + (j0 + 8 * q) * 32 + i;
+        const float px = fmul(cxq[q], fr);
         int idx[3];
         bool inside = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const float w = fadd(fadd(rx[a], fmul(r[3 * a + 1], py)), rz[a]);
+          const float w = fadd(fadd(fmul(r[3 * a], px), ry[a]), rz[a]);
           const float qa = fadd(o[a], fmul(w, cc.inv_s));
           const float fl = floorf(qa);
           inside = inside && fl >= 0.0f && fl < (float)dims[a];
@@ -350,8 +352,9 @@ __global__ void __launch_bounds__(256) crop_kernel(DevMap m, CropConst cc, const
           }
         }
         // code: 0 outside the map, else 1 + class (unknown, free, occupied)
-        cv[cell] = (uint8_t)(cls < 3u ? cls + 1u : 0u);
+        word |= (cls < 3u ? cls + 1u : 0u) << (8 * q);
       }
+      cw[k * 256] = word;  // cells k * 1024 + j * 32 + i0 .. i0 + 3
     }
     if (threadIdx.x == 0) {
       const float ext[3] = {cc.ext_x, cc.ext_y, cc.ext_z};
@@ -1754,6 +1757,7 @@ int nbt_surrogate_crops(nbt_map map, const nbt_pose *poses, int64_t n, const nbt
   if (n < 0 || !cam || !params) return NBT_EINVAL;
   if (n == 0) return NBT_OK;
   if (!poses || !crops || !feats) return NBT_EINVAL;
+  if ((uintptr_t)crops & 15u) return NBT_EINVAL;  // crops are written in 4-byte and read in 16-byte vectors
   if (!(cam->fov_h > 0.0f && cam->fov_h < 3.14159f) || !(cam->fov_v > 0.0f && cam->fov_v < 3.14159f) ||
       !(cam->max_range > 0.0f))
     return NBT_EINVAL;
@@ -1816,7 +1820,7 @@ int nbt_surrogate_forward(nbt_surrogate net, const void *crops, const void *feat
   if (rc != NBT_OK) return rc;
   if (n < 0) return NBT_EINVAL;
   if (n == 0) return NBT_OK;
-  if (!crops || !feats || !pred) return NBT_EINVAL;
+  if (!crops || !feats || !pred || ((uintptr_t)crops & 15u)) return NBT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t per = (int64_t)kCrop * kCrop * kCrop;
   for (int64_t b0 = 0; b0 < n; b0 += net->max_batch) {
@@ -1832,7 +1836,8 @@ int nbt_surrogate_backward(nbt_surrogate net, const void *crops, const void *fea
                            float *grads_out, float *loss_out, void *stream) {
   int rc = check_net(net);
   if (rc != NBT_OK) return rc;
-  if (n < 1 || n > net->max_batch || n > 1024 || !crops || !feats || !targets) return NBT_EINVAL;
+  if (n < 1 || n > net->max_batch || n > 1024 || !crops || !feats || !targets || ((uintptr_t)crops & 15u))
+    return NBT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   rc = backward_batch(net, (const uint8_t *)crops, (const bf16 *)feats, targets, n, s);
   if (rc != NBT_OK) return rc;

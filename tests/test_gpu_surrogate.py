@@ -368,6 +368,37 @@ def test_plan_pruned_refuses_bad_arguments_before_enqueueing():
     m.close()
 
 
+def test_crop_arrays_that_are_not_16_byte_aligned_are_refused_before_enqueueing():
+    """Crops are written in 4-byte and read in 16-byte vectors: every call that takes a crop array
+    refuses one that does not start on a 16-byte boundary, on the host, before any launch."""
+    grid, p = small_scene("u8", seed=1)
+    cam = nbt.camera(64, 48, math.radians(60), math.radians(45), 0.5)
+    prm = nbt.ig_params("count")
+    m = nbt.Map.from_grid(torch.from_numpy(grid).cuda(), 0.01)
+    pz = torch.from_numpy(p[:2]).cuda()
+    raw = torch.full((2 * 32768 + 64,), 7, dtype=torch.uint8, device="cuda")
+    ft = torch.zeros((2, 8), dtype=torch.bfloat16, device="cuda")
+    net = gs.Surrogate(max_batch=8, params=S.init_params(2))
+    pred = torch.zeros(2, dtype=torch.float32, device="cuda")
+    tgt = torch.zeros(2, dtype=torch.float32, device="cuda")
+    L = _lib.lib()
+    for off in (1, 4, 8):
+        ptr = raw.data_ptr() + off
+        assert L.nbt_surrogate_crops(m.handle, pz.data_ptr(), 2, C.byref(cam), C.byref(prm), ptr, ft.data_ptr(),
+                                     None) == -1
+        assert L.nbt_surrogate_forward(net.handle, ptr, ft.data_ptr(), 2, pred.data_ptr(), None) == -1
+        assert L.nbt_surrogate_backward(net.handle, ptr, ft.data_ptr(), tgt.data_ptr(), 2, None, None, None) == -1
+    torch.cuda.synchronize()
+    assert torch.all(raw == 7)                          # nothing was written
+    assert L.nbt_surrogate_crops(m.handle, pz.data_ptr(), 2, C.byref(cam), C.byref(prm), raw.data_ptr() + 16,
+                                 ft.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    ref, _ = gs.crops(m, pz, cam, prm)
+    assert torch.equal(raw[16:16 + 2 * 32768].view(2, 32, 32, 32), ref)
+    net.close()
+    m.close()
+
+
 def test_target_scale_equals_prescaled_targets_bitwise():
     """nbt_surrogate_set_target_scale: loss and gradients with scale c and targets t equal those with
     scale 1 and targets c t rounded to FP32, bit for bit."""
