@@ -70,6 +70,29 @@ def load_peaks() -> tuple[float, str]:
     return 6800.0, "fallback"
 
 
+# The reference walk's lane operations per visited voxel (its FP32 operation order): the axis choice
+# (3 comparisons), the chosen crossing (1 min) and its end test (1), the plane step (1 add), the
+# crossing recomputed from the plane (1 sub + 1 mul), the element index step (1 add), the address
+# and the payload read (2), the gain test and sum (2) and the occlusion test (1).  Unpacking 2-bit
+# states is not counted.
+WALK_OPS_PER_STEP = 14
+ISSUE_LANES_PER_CLK_PER_SM = 128     # 4 schedulers x one 32-lane warp instruction per clock
+
+
+def walk_alu_roofline(steps: float, ms: float, kernel: str) -> dict:
+    """The walk against the instruction-issue bound that binds it: the reference walk's lane operations
+    per voxel step x the launch's voxel steps, over the launch time, against the SMs' issue rate
+    (uniform bricks resolved without stepping count their voxels' operations as done, as the gather
+    roofline counts their bytes)."""
+    peak = ISSUE_LANES_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9      # G lane-ops/s
+    achieved = WALK_OPS_PER_STEP * steps / (ms * 1e-3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-op/s", "frac": achieved / peak,
+            "kernel": kernel,
+            "algorithmic": f"{WALK_OPS_PER_STEP} lane ops per voxel step of the reference walk x {steps:.0f} steps",
+            "peak_kind": f"derived: {ISSUE_LANES_PER_CLK_PER_SM} lane ops/clk/SM (4 schedulers x 32 lanes) x "
+                         f"{SM_COUNT} SMs x {SM_MAX_MHZ:.0f} MHz"}
+
+
 def ncu_traffic(workload: str):
     """DRAM bytes per launch (per forward of the batch, for the surrogate) from the committed ncu summary, if current."""
     if not os.path.exists(TRAFFIC_FILE):
@@ -581,6 +604,7 @@ def main() -> None:
                      "traffic": traffic, "kernel": "ig_tiles_kernel (+views_reduce)",
                      "algorithmic": f"{bps} B per voxel step x {n_steps_voxel} steps",
                      "peak_kind": f"{peak_kind} (hbm_gbs)"},
+        "roofline_alu": walk_alu_roofline(n_steps_voxel, ig_mean_ms, "ig_tiles_kernel (+views_reduce)"),
         "e2e": {"value": job_throughput(w.n_poses * args.steps, world, e2e_total), "unit": "views/s",
                 "h2d_bytes_per_step": int(grid_host.numel() * grid_host.element_size()
                                           + poses_host.numel() * 4),
@@ -676,6 +700,7 @@ def run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist) -> None
                      "traffic": ncu_traffic(args.workload), "kernel": "ig_tiles_kernel (+traj_reduce)",
                      "algorithmic": f"{bps} B per voxel step x {n_steps_voxel} steps",
                      "peak_kind": f"{peak_kind} (hbm_gbs)"},
+        "roofline_alu": walk_alu_roofline(n_steps_voxel, ig_ms, "ig_tiles_kernel (+traj_reduce)"),
         "e2e": {"value": job_throughput(w.n_poses * args.steps, world, e2e_total), "unit": "views/s",
                 "h2d_bytes_per_step": int(grid_host.numel() + poses_host.numel() * 4 + off_host.numel() * 4),
                 "d2h_bytes_per_step": int(out_host.numel() * 4)},
@@ -1453,6 +1478,7 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
                      "traffic": ncu_traffic("room512"), "kernel": "ig_tiles_kernel<u2> (exact arm, + views_reduce)",
                      "algorithmic": f"0.25 B per voxel step x {steps_per_launch:.0f} steps per launch",
                      "peak_kind": f"{hbm_kind} (hbm_gbs)"},
+        "roofline_alu": walk_alu_roofline(steps_per_launch, kern_mean, "ig_tiles_kernel<u2> (exact arm, + views_reduce)"),
         "roofline_surrogate": {"bound": "tensor", "achieved": s_achieved, "peak": bf16, "unit": "TFLOP/s",
                                "frac": s_achieved / bf16, "traffic": ncu_traffic("surrogate_forward"),
                                "kernel": "surrogate forward (fused layers 0-1, layers 2-3, fc1, fc2)",

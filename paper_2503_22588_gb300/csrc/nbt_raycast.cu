@@ -315,23 +315,38 @@ __device__ __forceinline__ void walk_count(Walk &w, int &lin, uint32_t raw, uint
 // of its current brick, so the lanes stay converged.
 // ---------------------------------------------------------------------------
 
-// Crossings k of one axis that come before the key: t(k) < T, or t(k) == T
-// when tie, with t(k) = ((b + k s) - o) (1/d), the walk's own rounded
-// operations; the answer lies in [0, kmax].  A real-arithmetic estimate from
-// the current crossing t0 and |d| is checked by two exact evaluations (the
-// predicate is monotone in k) and corrected step by step when they fail, so
-// the result never depends on the estimate.
-__device__ __forceinline__ int skip_axis_count(float b, float s, float o, float v, float ad, float t0, float T,
-                                               bool tie, int kmax) {
-  auto before = [&](int k) {
-    const float t = fmul(fsub(fadd(b, (float)k * s), o), v);
-    return t < T || (tie && t == T);
-  };
-  const float e = ceilf((T - t0) * ad);
-  int c = e > 0.0f ? (e < (float)kmax ? (int)e : kmax) : 0;
-  if ((c == 0 || before(c - 1)) && (c == kmax || !before(c))) return c;
-  while (c > 0 && !before(c - 1)) --c;
-  while (c < kmax && before(c)) ++c;
+// One axis of a jump to the key: its crossings k before the key, t(k) < T,
+// or t(k) == T when tie, with t(k) = ((b + k s) - o) (1/d), the walk's own
+// rounded operations (the answer lies in [0, kin], kin = the axis' planes
+// inside the brick); the exit axis takes all kin of them and then the exit
+// plane itself.  The plane b and its crossing t move past the crossings
+// taken, as kin single steps would move them.  A real-arithmetic estimate
+// from the current crossing t and |d| is checked by two exact evaluations --
+// one of them the new crossing itself -- (the predicate is monotone in k)
+// and corrected step by step when they fail, so the result never depends on
+// the estimate.  Returns the crossings before the key (kin on the exit axis).
+__device__ __forceinline__ int skip_axis_jump(float &b, float s, float o, float v, float ad, float &t, float T,
+                                              int kin, bool exit, bool tie) {
+  auto before = [&](float tk) { return tk < T || (tie && tk == T); };
+  int c = kin;
+  if (!exit) {
+    const float e = ceilf((T - t) * ad);
+    c = e > 0.0f ? (e < (float)kin ? (int)e : kin) : 0;
+  }
+  float bn = fadd(b, (float)(c + (int)exit) * s);
+  float tn = fmul(fsub(bn, o), v);
+  if (!exit) {
+    const float tp = fmul(fsub(fsub(bn, s), o), v);   // t(c - 1): b + (c - 1) s is exact
+    if (!((c == 0 || before(tp)) && (c == kin || !before(tn)))) {
+      auto tk = [&](int k) { return fmul(fsub(fadd(b, (float)k * s), o), v); };
+      while (c > 0 && !before(tk(c - 1))) --c;
+      while (c < kin && before(tk(c))) ++c;
+      bn = fadd(b, (float)c * s);
+      tn = fmul(fsub(bn, o), v);
+    }
+  }
+  b = bn;
+  t = tn;
   return c;
 }
 
@@ -607,9 +622,9 @@ __device__ __forceinline__ void ray_skip(const DevMap &m, uint32_t addr_max, con
       const int kx = w.sx != 0.0f ? (int)fabsf(ex - w.bx) : 0;
       const int ky = w.sy != 0.0f ? (int)fabsf(ey - w.by) : 0;
       const int kz = w.sz != 0.0f ? (int)fabsf(ez - w.bz) : 0;
-      const int cx = A == 0 ? kx : skip_axis_count(w.bx, w.sx, w.ox, w.vx, adx, w.tx, key, 0 < A && !end, kx);
-      const int cy = A == 1 ? ky : skip_axis_count(w.by, w.sy, w.oy, w.vy, ady, w.ty, key, 1 < A && !end, ky);
-      const int cz = A == 2 ? kz : skip_axis_count(w.bz, w.sz, w.oz, w.vz, adz, w.tz, key, 2 < A && !end, kz);
+      const int cx = skip_axis_jump(w.bx, w.sx, w.ox, w.vx, adx, w.tx, key, kx, A == 0, 0 < A && !end);
+      const int cy = skip_axis_jump(w.by, w.sy, w.oy, w.vy, ady, w.ty, key, ky, A == 1, 1 < A && !end);
+      const int cz = skip_axis_jump(w.bz, w.sz, w.oz, w.vz, adz, w.tz, key, kz, A == 2, 2 < A && !end);
       const uint32_t nvis = 1u + (uint32_t)(cx + cy + cz);
       steps += nvis;
       if (cls == kSumUnknown) {
@@ -618,14 +633,8 @@ __device__ __forceinline__ void ray_skip(const DevMap &m, uint32_t addr_max, con
         else
           iacc += nvis;
       }
-      // the state after those crossings, plus the exit crossing (T, A) itself unless the walk ends
+      // the walk state now sits past those crossings and, unless the walk ends, the exit crossing (T, A)
       const int mx = cx + (A == 0), my = cy + (A == 1), mz = cz + (A == 2);
-      w.bx = fadd(w.bx, (float)mx * w.sx);
-      w.by = fadd(w.by, (float)my * w.sy);
-      w.bz = fadd(w.bz, (float)mz * w.sz);
-      w.tx = fmul(fsub(w.bx, w.ox), w.vx);
-      w.ty = fmul(fsub(w.by, w.oy), w.vy);
-      w.tz = fmul(fsub(w.bz, w.oz), w.vz);
       lin += mx * w.qx + my * w.qy + mz * w.qz;
       done = end;
     } else {

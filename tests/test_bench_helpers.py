@@ -103,3 +103,12 @@ def test_surrogate_flop_counts():
     dense = 2 * (16 ** 3 * 16 * 216 + 8 ** 3 * 32 * 432 + 4 ** 3 * 64 * 864 + 4 ** 3 * 64 * 1728) + 2 * 4104 * 128 + 256
     assert bench.surrogate_flops_per_view() == dense
     assert dense - bench.surrogate_method_flops_per_view() == 2 * 16 ** 3 * 16 * (216 - 112)
+
+
+def test_walk_alu_roofline_by_hand():
+    # 2e9 voxel steps in 10 ms at 14 lane ops per step, against 128 lanes x 152 SMs x 2070 MHz
+    r = bench.walk_alu_roofline(2e9, 10.0, "k")
+    assert r["bound"] == "alu" and r["unit"] == "Glane-op/s"
+    assert r["peak"] == pytest.approx(128 * 152 * 2070e6 / 1e9)
+    assert r["achieved"] == pytest.approx(14 * 2e9 / 10e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
