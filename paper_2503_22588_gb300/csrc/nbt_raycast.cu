@@ -12,9 +12,11 @@
 // camera and stay close, and their loads share L1 lines.  Each ray's walk is
 // branch-free (see Walk), and the payload element of the next voxel is
 // loaded before the current one is accumulated (the voxel sequence does not
-// depend on the map, only the occlusion test does).  Per-ray sums go
-// through a fixed warp-shuffle tree and a fixed 8-warp sum into one 16-byte
-// partial per item; a second kernel adds the partials of each perspective
+// depend on the map, only the occlusion test does).  (Walks that skip
+// uniform bricks on state maps let each warp take whole items instead, its
+// 8 packets in turn.)  Per-ray sums go through a fixed warp-shuffle tree and
+// a fixed 8-packet sum into one 16-byte partial per item; a second kernel
+// adds the partials of each perspective
 // (or trajectory) in a fixed order in FP64, so results do not depend on
 // scheduling.
 
@@ -865,6 +867,89 @@ __global__ void __launch_bounds__(kThreads, SKIP ? NBT_SKIP_MIN_BLOCKS : (CHUNK 
   }
 }
 
+// Uniform-brick skipping walks on state maps (linear layout, many rays):
+// each warp takes whole items from the device queue and casts the item's 8
+// packets one after another, so no warp waits at a CTA barrier for a slower
+// one (the walks of one packet take very different times once uniform
+// bricks are skipped).  Lane 0 forms the item's rotation into the warp's
+// shared slot.
+// The per-item sum is the same fixed shuffle tree per packet and the same
+// packet order as ig_tiles_kernel's 8-warp sum, so partials are
+// bit-identical to it.
+template <int KIND, bool HIT>
+__global__ void __launch_bounds__(kThreads, NBT_SKIP_MIN_BLOCKS)
+    ig_warp_tiles_kernel(DevMap m, CamConst cc, const float *__restrict__ poses, int64_t n_items, uint32_t addr_max,
+                         unsigned long long *queue, Partial *partials) {
+  constexpr int kPk = kThreads / 32;   // packets per item
+  // per warp: the item's pose, rotation and first pixel; the packets' sums (kept out of registers)
+  __shared__ float s_pose[kThreads / 32][8], s_rot[kThreads / 32][9];
+  __shared__ int s_xy[kThreads / 32][2];
+  __shared__ long long s_item[kThreads / 32];
+  __shared__ float s_f[kThreads / 32][kPk];
+  __shared__ uint32_t s_i[kThreads / 32][kPk], s_s[kThreads / 32][kPk];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pw = cc.packet_w, ph = 32 / pw, across = 32 / pw;
+  float *sp = s_pose[warp], *sr = s_rot[warp];
+  for (;;) {
+    long long item = 0;
+    if (lane == 0) {
+      item = (long long)atomicAdd(queue, 1ull);
+      s_item[warp] = item;
+      if (item < n_items) {
+        const long long pose = item / cc.tiles_per_pose;
+        const int tile = (int)(item - pose * cc.tiles_per_pose);
+        float q[7], r[9];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) sp[k] = q[k] = __ldg(poses + pose * 7 + k);
+        quat_rot_f32(q + 3, r);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) sr[k] = r[k];
+        s_xy[warp][0] = (tile % cc.tiles_x) * kTileW;
+        s_xy[warp][1] = (tile / cc.tiles_x) * kTileH;
+      }
+    }
+    if (__shfl_sync(0xffffffffu, item, 0) >= n_items) break;
+    __syncwarp();
+    for (int pk = 0; pk < kPk; ++pk) {
+      const int i = s_xy[warp][0] + (pk % across) * pw + lane % pw;
+      const int j = s_xy[warp][1] + (pk / across) * ph + lane / pw;
+      float facc = 0.0f;
+      uint32_t iacc = 0u, steps = 0u;
+      const bool inside = i < cc.W && j < cc.H;
+      float o[3] = {0.0f, 0.0f, 0.0f}, d[3] = {0.0f, 0.0f, 0.0f};
+      if (inside) ray_segment_rot(cc, sp, sr, i, j, o, d);
+      ray_skip<KIND, HIT>(m, addr_max, o, d, inside, facc, iacc, steps);   // all lanes together
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        if (KIND == PAYLOAD_GAIN_F32)
+          facc += __shfl_xor_sync(0xffffffffu, facc, s);
+        else
+          iacc += __shfl_xor_sync(0xffffffffu, iacc, s);
+        steps += __shfl_xor_sync(0xffffffffu, steps, s);
+      }
+      if (lane == 0) {
+        s_f[warp][pk] = facc;
+        s_i[warp][pk] = iacc;
+        s_s[warp][pk] = steps;
+      }
+    }
+    __syncwarp();   // every lane is done with the slot before lane 0 refills it
+    if (lane == 0) {
+      Partial p;
+      p.fsum = 0.0f;
+      p.isum = 0u;
+      p.steps = 0u;
+      p.pad = 0u;
+      for (int k = 0; k < kPk; ++k) {
+        p.fsum += s_f[warp][k];
+        p.isum += s_i[warp][k];
+        p.steps += s_s[warp][k];
+      }
+      partials[s_item[warp]] = p;
+    }
+  }
+}
+
 // Few rays (the paper's operating point: a few thousand rays per call):
 // LANES lanes walk each ray (walk_lane_part), each its share of the
 // crossings, kSplitChunk voxels ahead of its reads.  A lane stops at its
@@ -1183,6 +1268,28 @@ int launch_tiles_t(nbt_map map, const void *payload, const CamConst &cc, const f
   return NBT_OK;
 }
 
+template <int KIND, bool HIT>
+int launch_warp_tiles(nbt_map map, const void *payload, const CamConst &cc, const float *poses, int64_t n_items,
+                      void *workspace, cudaStream_t stream) {
+  static int cached[64] = {0};
+  const int dev = map->device;
+  int per_sm = dev >= 0 && dev < 64 ? cached[dev] : 0;
+  if (per_sm <= 0) {
+    NBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ig_warp_tiles_kernel<KIND, HIT>, kThreads, 0));
+    per_sm = std::max(per_sm, 1);
+    if (dev >= 0 && dev < 64) cached[dev] = per_sm;
+  }
+  const int64_t warps = (int64_t)sm_count() * per_sm * (kThreads / 32);
+  const int64_t grid = (std::min<int64_t>(n_items, warps) + kThreads / 32 - 1) / (kThreads / 32);
+  unsigned long long *queue = (unsigned long long *)workspace;
+  Partial *partials = (Partial *)((char *)workspace + 256);
+  NBT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream));
+  ig_warp_tiles_kernel<KIND, HIT><<<(unsigned)grid, kThreads, 0, stream>>>(dev_map(map, payload), cc, poses, n_items,
+                                                                          addr_max_of(map), queue, partials);
+  NBT_CUDA_TRY(cudaGetLastError());
+  return NBT_OK;
+}
+
 // Voxels the latency-bound variant walks ahead of its reads.
 constexpr int kChunk = 8;
 
@@ -1238,7 +1345,12 @@ int launch_tiles_linear(nbt_map map, const void *payload, const CamConst &cc, co
     rc = prepare_bsum(map, stream);
     if (rc != NBT_OK) return rc;
     constexpr bool H = KIND == PAYLOAD_GAIN_F32 ? HIT : true;
-    return launch_tiles_t<KIND, H, true, 0, true>(map, payload, cc, poses, n_items, workspace, stream);
+    // state maps: warps take whole items (no CTA barrier between packets, measured +3 % on the
+    // tabletop trajectories); FP32 gains keep the 8-warp CTA items, which measured 3 % faster there
+    if constexpr (KIND == PAYLOAD_GAIN_F32)
+      return launch_tiles_t<KIND, H, true, 0, true>(map, payload, cc, poses, n_items, workspace, stream);
+    else
+      return launch_warp_tiles<KIND, H>(map, payload, cc, poses, n_items, workspace, stream);
   }
   return launch_tiles_t<KIND, HIT, true, 0>(map, payload, cc, poses, n_items, workspace, stream);
 }
