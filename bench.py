@@ -601,10 +601,10 @@ def main() -> None:
         "views_ig_ms": ig_mean_ms,
         "upload_ms": upload_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "ig_tiles_kernel (+views_reduce)",
+                     "traffic": traffic, "kernel": "the tile kernel the call selects (ig_tiles_kernel or ig_warp_tiles_kernel) + views_reduce",
                      "algorithmic": f"{bps} B per voxel step x {n_steps_voxel} steps",
                      "peak_kind": f"{peak_kind} (hbm_gbs)"},
-        "roofline_alu": walk_alu_roofline(n_steps_voxel, ig_mean_ms, "ig_tiles_kernel (+views_reduce)"),
+        "roofline_alu": walk_alu_roofline(n_steps_voxel, ig_mean_ms, "the tile kernel the call selects + views_reduce"),
         "e2e": {"value": job_throughput(w.n_poses * args.steps, world, e2e_total), "unit": "views/s",
                 "h2d_bytes_per_step": int(grid_host.numel() * grid_host.element_size()
                                           + poses_host.numel() * 4),
@@ -697,10 +697,10 @@ def run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist) -> None
         "voxel_steps_per_step": n_steps_voxel, "traj_ig_ms": ig_ms,
         "roofline": {"bound": "hbm", "achieved": n_steps_voxel * bps / (ig_ms * 1e-3) / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": n_steps_voxel * bps / (ig_ms * 1e-3) / 1e9 / peak,
-                     "traffic": ncu_traffic(args.workload), "kernel": "ig_tiles_kernel (+traj_reduce)",
+                     "traffic": ncu_traffic(args.workload), "kernel": "the tile kernel the plan selects (ig_tiles_kernel or ig_warp_tiles_kernel) + traj_reduce",
                      "algorithmic": f"{bps} B per voxel step x {n_steps_voxel} steps",
                      "peak_kind": f"{peak_kind} (hbm_gbs)"},
-        "roofline_alu": walk_alu_roofline(n_steps_voxel, ig_ms, "ig_tiles_kernel (+traj_reduce)"),
+        "roofline_alu": walk_alu_roofline(n_steps_voxel, ig_ms, "the tile kernel the plan selects + traj_reduce"),
         "e2e": {"value": job_throughput(w.n_poses * args.steps, world, e2e_total), "unit": "views/s",
                 "h2d_bytes_per_step": int(grid_host.numel() + poses_host.numel() * 4 + off_host.numel() * 4),
                 "d2h_bytes_per_step": int(out_host.numel() * 4)},
@@ -1475,10 +1475,10 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         "train": train_info,
         "scene_generation_s": gen_s,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": ncu_traffic("room512"), "kernel": "ig_tiles_kernel<u2> (exact arm, + views_reduce)",
+                     "traffic": ncu_traffic("room512"), "kernel": "ig_warp_tiles_kernel<u2> (exact arm, + views_reduce)",
                      "algorithmic": f"0.25 B per voxel step x {steps_per_launch:.0f} steps per launch",
                      "peak_kind": f"{hbm_kind} (hbm_gbs)"},
-        "roofline_alu": walk_alu_roofline(steps_per_launch, kern_mean, "ig_tiles_kernel<u2> (exact arm, + views_reduce)"),
+        "roofline_alu": walk_alu_roofline(steps_per_launch, kern_mean, "ig_warp_tiles_kernel<u2> (exact arm, + views_reduce)"),
         "roofline_surrogate": {"bound": "tensor", "achieved": s_achieved, "peak": bf16, "unit": "TFLOP/s",
                                "frac": s_achieved / bf16, "traffic": ncu_traffic("surrogate_forward"),
                                "kernel": "surrogate forward (fused layers 0-1, layers 2-3, fc1, fc2)",
@@ -1487,9 +1487,10 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
         "e2e": {"value": job_throughput(n_views * args.steps, world, e2e_total), "unit": "views/s",
                 "h2d_bytes_per_step": int(grid_h.numel() + poses_h.numel() * 4),
                 "d2h_bytes_per_step": int(best_h.numel() * 4 + val_h.numel() * 4)},
-        # pruned step: upload (1) + per batch of 4096 (crops, fused layers 0-1, layer 2, layer 3, features,
-        # fc1, fc2) + top-k + tile kernel + reduce + argmax
-        "gpu_launches": (1 + 7 * n_chunks + 4) * args.steps,
+        # per timed step, pruned arm: upload (1) + brick summaries of the new map (5) + per batch of 4096
+        # (crops, fused layers 0-1, layer 2, layer 3, features, fc1, fc2) + top-k + tile kernel + reduce +
+        # argmax; exact arm: upload (1) + brick summaries (5) + tile kernel + reduce + argmax
+        "gpu_launches": ((1 + 5 + 7 * n_chunks + 4) + (1 + 5 + 3)) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -388,6 +388,7 @@ int nbt_surrogate_param_count(int64_t *n);
 
 /* Create a network on the current device with activation buffers for up
  * to max_batch (1 .. 4096) samples per pass; parameters start at zero.
+ * Also creates the side stream and events nbt_plan_pruned uses.
  * Errors: NBT_EINVAL, NBT_ENOMEM, NBT_ECUDA. */
 int nbt_surrogate_create(int32_t max_batch, nbt_surrogate *out);
 int nbt_surrogate_destroy(nbt_surrogate net);
@@ -541,6 +542,12 @@ int nbt_ig_cost(nbt_id_buffer buf, const nbt_pose *poses, int64_t n_poses, const
  *   workspace:   device buffer of >= nbt_pruned_workspace_size bytes,
  *                256-byte aligned, owned by the caller.
  * Allocates nothing; asynchronous on stream.  n == 0 enqueues nothing.
+ * With more than one batch, the crops of the next batch run on the
+ * network's own high-priority side stream while stream runs the current
+ * batch's forward (event fork / join: the call is ordered on stream as a
+ * whole).  A network
+ * serves one call at a time (its buffers, side stream and events are its
+ * own).
  * Errors: NBT_EINVAL, NBT_EUNSUPPORTED, NBT_EWORKSPACE, NBT_ECUDA. */
 int nbt_pruned_workspace_size(nbt_surrogate net, int64_t n, int32_t seg, int32_t keep, const nbt_camera *cam,
                               int64_t *bytes);

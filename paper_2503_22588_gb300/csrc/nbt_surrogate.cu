@@ -1457,6 +1457,10 @@ struct nbt_surrogate_s {
   float *y = nullptr, *loss = nullptr, *part = nullptr;
   int64_t step = 0;
   float target_scale = 1.0f;  // training targets are multiplied by this in the loss
+  // nbt_plan_pruned: crops of the next batch on a high-priority side stream while the caller's stream
+  // runs the forward of the current one (fork / join through these events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_crop[2] = {nullptr, nullptr}, ev_fwd[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -1470,6 +1474,10 @@ void free_net(nbt_surrogate n) {
     if (n->act[l]) cudaFree(n->act[l]);
     if (n->dact[l]) cudaFree(n->dact[l]);
   }
+  cudaEvent_t evs[] = {n->ev_fork, n->ev_crop[0], n->ev_crop[1], n->ev_fwd[0], n->ev_fwd[1]};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (n->side) cudaStreamDestroy(n->side);
   (void)cudaGetLastError();
   delete n;
 }
@@ -1716,6 +1724,15 @@ int nbt_surrogate_create(int32_t max_batch, nbt_surrogate *out) {
     free_net(n);
     return NBT_ENOMEM;
   }
+  int lo = 0, hi = 0;
+  bool sok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+             cudaStreamCreateWithPriority(&n->side, cudaStreamNonBlocking, hi) == cudaSuccess;
+  cudaEvent_t *evs[] = {&n->ev_fork, &n->ev_crop[0], &n->ev_crop[1], &n->ev_fwd[0], &n->ev_fwd[1]};
+  for (cudaEvent_t *e : evs) sok = sok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+  if (!sok) {
+    free_net(n);
+    return NBT_ECUDA;
+  }
   *out = n;
   return NBT_OK;
 }
@@ -1951,23 +1968,28 @@ constexpr int64_t kCropBytes = (int64_t)kCrop * kCrop * kCrop;  // one uint8 cla
 int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 
 struct PrunedLayout {
-  int64_t crops, feats, scores, idx, kept, ig, ws, ws_bytes, total;
+  int64_t crops, crops_stride, feats, feats_stride, scores, idx, kept, ig, ws, ws_bytes, total;
 };
 
 // Workspace regions (each 256-byte aligned): crops and features of one batch
-// of max_batch candidates, all scores, the kept indices, kept poses and
-// their exact IGs, and the raycast workspace of the kept views.
+// of max_batch candidates (two such buffers when there is more than one
+// batch: the next batch's crops are formed while the current one's forward
+// runs), all scores, the kept indices, kept poses and their exact IGs, and
+// the raycast workspace of the kept views.
 int pruned_layout(nbt_surrogate net, int64_t n, int32_t seg, int32_t keep, const nbt_camera *cam, PrunedLayout *L) {
   const int64_t chunk = std::min<int64_t>(n, net->max_batch);
+  const int64_t bufs = n > chunk ? 2 : 1;
   const int64_t n_kept = n / seg * keep;
   int64_t ws_bytes = 0;
   const int rc = nbt_workspace_size(n_kept, cam, &ws_bytes);
   if (rc != NBT_OK) return rc;
   int64_t o = 0;
   L->crops = o;
-  o += align256(chunk * kCropBytes);
+  L->crops_stride = align256(chunk * kCropBytes);
+  o += bufs * L->crops_stride;
   L->feats = o;
-  o += align256(chunk * kFeat * 2);
+  L->feats_stride = align256(chunk * kFeat * 2);
+  o += bufs * L->feats_stride;
   L->scores = o;
   o += align256(n * 4);
   L->idx = o;
@@ -2019,19 +2041,37 @@ int nbt_plan_pruned(nbt_map map, nbt_surrogate net, const nbt_pose *poses, int64
   if (rc != NBT_OK) return rc;
   if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255u)) return NBT_EWORKSPACE;
   char *w = (char *)workspace;
-  uint8_t *crops = (uint8_t *)(w + L.crops);
-  void *feats = w + L.feats;
   float *scores = (float *)(w + L.scores);
   int32_t *idx = kept_out ? kept_out : (int32_t *)(w + L.idx);
   nbt_pose *kept = (nbt_pose *)(w + L.kept);
   float *ig = (float *)(w + L.ig);
   const int64_t n_kept = n / seg * keep;
-  for (int64_t c0 = 0; c0 < n; c0 += net->max_batch) {
+  // Crops of batch b go into buffer b % 2 on the side stream (high priority: the latency-bound
+  // gather fills issue slots the forward leaves idle), after the forward of batch b - 2 has released
+  // that buffer; the caller's stream waits for them, runs the forward, and at the end has waited for
+  // every side-stream launch (fork / join, so the call stays ordered on the caller's stream).
+  cudaStream_t s = (cudaStream_t)stream;
+  NBT_CUDA_TRY(cudaEventRecord(net->ev_fork, s));
+  NBT_CUDA_TRY(cudaStreamWaitEvent(net->side, net->ev_fork, 0));
+  int64_t b = 0;
+  for (int64_t c0 = 0; c0 < n; c0 += net->max_batch, ++b) {
     const int64_t nc = std::min<int64_t>(net->max_batch, n - c0);
-    rc = nbt_surrogate_crops(map, poses + c0, nc, cam, params, crops, feats, stream);
-    if (rc != NBT_OK) return rc;
+    const int buf = (int)(b & 1);
+    uint8_t *crops = (uint8_t *)(w + L.crops + buf * L.crops_stride);
+    void *feats = w + L.feats + buf * L.feats_stride;
+    if (b >= 2) NBT_CUDA_TRY(cudaStreamWaitEvent(net->side, net->ev_fwd[buf], 0));
+    rc = nbt_surrogate_crops(map, poses + c0, nc, cam, params, crops, feats, net->side);
+    if (rc == NBT_OK) rc = cudaEventRecord(net->ev_crop[buf], net->side) == cudaSuccess ? NBT_OK : NBT_ECUDA;
+    if (rc == NBT_OK) rc = cudaStreamWaitEvent(s, net->ev_crop[buf], 0) == cudaSuccess ? NBT_OK : NBT_ECUDA;
+    if (rc != NBT_OK) {
+      // join the side stream before returning, whatever was enqueued on it
+      if (cudaEventRecord(net->ev_crop[buf], net->side) == cudaSuccess) (void)cudaStreamWaitEvent(s, net->ev_crop[buf], 0);
+      (void)cudaGetLastError();
+      return rc;
+    }
     rc = nbt_surrogate_forward(net, crops, feats, nc, scores + c0, stream);
     if (rc != NBT_OK) return rc;
+    NBT_CUDA_TRY(cudaEventRecord(net->ev_fwd[buf], s));
   }
   rc = nbt_segment_topk(scores, n, seg, keep, idx, poses, kept, stream);
   if (rc != NBT_OK) return rc;

@@ -66,7 +66,7 @@ def surrogate_scores(net: Surrogate, m: Map, poses: torch.Tensor, cam: Camera, p
 
 
 def pruned_workspace(net: Surrogate, n: int, seg: int, keep: int, cam: Camera, device=None) -> torch.Tensor:
-    """A device workspace for nbt_plan_pruned (crops of one batch, scores, kept views, raycast scratch)."""
+    """A device workspace for nbt_plan_pruned (crops of up to two batches, scores, kept views, raycast scratch)."""
     b = C.c_int64()
     check(lib().nbt_pruned_workspace_size(net.handle, int(n), int(seg), int(keep), C.byref(cam), C.byref(b)),
           "nbt_pruned_workspace_size")

@@ -337,6 +337,31 @@ def test_plan_pruned_kept_indices_are_the_top_scores_and_best_is_their_exact_arg
     m.close()
 
 
+def test_plan_pruned_over_many_batches_equals_its_steps_every_time():
+    """The crops of batch b + 1 run on the network's side stream while the forward of batch b runs, in
+    two alternating buffers: over 24 batches, repeated, the kept indices and the best views equal
+    those of the steps run one by one on one stream."""
+    from paper_2503_22588_gb300 import planning as P
+    w = configs.exact64(seed=7, n_views=192)
+    cam = nbt.camera(32, 24, w.camera.fov_h, w.camera.fov_v, 1.0)
+    prm = nbt.ig_params("count")
+    m = nbt.Map.from_grid(torch.from_numpy(w.grid).cuda(), 0.01)
+    pz = torch.from_numpy(w.poses).cuda()
+    net = gs.Surrogate(max_batch=8, params=S.init_params(5))       # 192 candidates: 24 batches
+    scores = P.surrogate_scores(net, m, pz, cam, prm)
+    idx, kp = P.segment_topk(scores, 32, 4, pz)
+    ig, _ = nbt.views_ig(m, kp, cam, prm)
+    b_ref, v_ref = P.segment_argmax(ig, 4, idx.reshape(-1).contiguous())
+    ws = P.pruned_workspace(net, 192, 32, 4, cam)
+    for _ in range(5):
+        best, val, kept = P.pruned_best(net, m, pz, 32, 4, cam, prm, ws)
+        assert torch.equal(kept, idx)
+        assert torch.equal(best, b_ref) and torch.equal(val, v_ref)
+    assert no_device_timeout()
+    net.close()
+    m.close()
+
+
 def test_plan_pruned_refuses_bad_arguments_before_enqueueing():
     from paper_2503_22588_gb300 import planning as P
     w = configs.exact64(seed=6, n_views=32)
