@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "IG views/sec & voxel-steps/s at 1 GB300 (exact vs surrogate-pruned, same best view)"
 L2_FLUSH_BYTES = 256 << 20
 BYTES_PER_STEP = {"f32": 4.0, "u8": 1.0, "u2": 0.25}
+SKIP_WALK_MIN_RAYS = 2 * 152 * 6 * 256   # rays per call above which linear maps take the skipping walk
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SOURCES = ["paper_2503_22588_gb300/csrc/nbt_raycast.cu", "paper_2503_22588_gb300/csrc/nbt_internal.cuh"]
 
@@ -505,6 +506,8 @@ def main() -> None:
     m = nbt.Map(w.n, w.n, w.n, w.voxel_size, w.origin, w.encoding)
     if args.skip is not None:
         m.set_tuning(8, skip=bool(args.skip))
+    # the library takes the uniform-brick skipping walk on linear maps above this many rays per call
+    skip_walk = args.skip != 0 and w.n_poses * w.camera.width * w.camera.height > SKIP_WALK_MIN_RAYS
     ws = nbt.workspace(w.n_poses, cam, dev)
     ig = torch.empty(w.n_poses, dtype=torch.float32, device=dev)
     steps = torch.empty(w.n_poses, dtype=torch.int64, device=dev)
@@ -609,8 +612,9 @@ def main() -> None:
                 "h2d_bytes_per_step": int(grid_host.numel() * grid_host.element_size()
                                           + poses_host.numel() * 4),
                 "d2h_bytes_per_step": int(ig_host.numel() * 4)},
-        # per step: upload (scatter / pack), gain derivation (probability maps only), tile kernel, reduce
-        "gpu_launches": (4 if w.encoding == "f32" else 3) * args.steps,
+        # per step: upload (scatter / pack), gain derivation (probability maps only), the brick summaries
+        # of the new map when the call takes the skipping walk (5), tile kernel, reduce
+        "gpu_launches": ((4 if w.encoding == "f32" else 3) + (5 if skip_walk else 0)) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -704,7 +708,9 @@ def run_traj(args, w, nbt, torch, dev, stream, world, rank, local, dist) -> None
         "e2e": {"value": job_throughput(w.n_poses * args.steps, world, e2e_total), "unit": "views/s",
                 "h2d_bytes_per_step": int(grid_host.numel() + poses_host.numel() * 4 + off_host.numel() * 4),
                 "d2h_bytes_per_step": int(out_host.numel() * 4)},
-        "gpu_launches": 3 * args.steps,
+        # per step: upload, the brick summaries of the new map when the plan takes the skipping walk (5),
+        # and the graph's tile kernel and reduce
+        "gpu_launches": (3 + (5 if tuned.get("skip") else 0)) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
