@@ -461,7 +461,9 @@ __global__ void __launch_bounds__(256) conv0_lookup_kernel(const uint8_t *__rest
 // 16-byte vectors with x' = (x & 1) * 8 + x / 2: the stride-2 reads of
 // layer 1 then hit consecutive vectors.
 // Layer 1: rows = 8^3 output voxels (4 tiles of 128), K = 27 taps x 16
-// channels (padded to 7 stages of 64), six stages in flight: each A chunk is
+// channels (padded to 2 stages of 224: each barrier round trip between the
+// builders and the MMA warp costs more than the 14 MMAs of a stage), both in
+// flight: each A chunk is
 // read from the shared layer-0 activation (per-row offset plus per-chunk
 // offset, zero where the tap falls in the padding: a 3-bit mask test) and
 // stored into TMEM; W1 stays resident in shared memory.  TMEM: layer-0
@@ -473,11 +475,13 @@ constexpr int kThreads = 512;                  // builder threads (plus one MMA 
 constexpr int kK0 = 112;                       // layer-0 K: 28 taps x 4 slots
 constexpr int kTiles0 = 32;                    // 16^3 / 128
 constexpr int kTiles1 = 4;                     // 8^3 / 128
-constexpr int kStages1 = 7;                    // layer-1 K stages of 64 per tile
+constexpr int kChunksS1 = 28;                  // 16-byte A chunks per row in a layer-1 K stage (K = 224)
+constexpr int kStages1 = 56 / kChunksS1;       // layer-1 K stages per tile (K = 27 taps x 16, padded to 448)
+static_assert(56 % kChunksS1 == 0 && kChunksS1 % 2 == 0, "layer-1 stages");
 constexpr int kBuf0 = 4;                       // layer-0 A tiles in flight (56 TMEM columns each)
-constexpr int kBuf1 = 6;                       // layer-1 A stages in flight (32 TMEM columns each)
+constexpr int kBuf1 = 2;                       // layer-1 A stages in flight (112 TMEM columns each)
 constexpr uint32_t kColA = 256;                // TMEM columns 0-127: layer-0 accumulators, 128-255: layer 1
-constexpr uint32_t kColsA0 = kK0 / 2, kColsA1 = 32;
+constexpr uint32_t kColsA0 = kK0 / 2, kColsA1 = 4 * kChunksS1;
 constexpr int kOffCodes = 0;                   // 32 x 32 x-rows x 8 B
 constexpr int kOffAct0 = kOffCodes + 8192;     // 2 x 16^3 x 16 B
 constexpr int kOffW0 = kOffAct0 + 131072;      // 7 K16 blocks x 16 rows x 32 B
@@ -550,7 +554,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // "full" barrier (each after its own TMEM stores have completed); the
 // commit arrives on its "empty" barrier, which the builders wait for before
 // refilling the buffer or reading the accumulator.  No CTA-wide barrier
-// inside the crop loop: the builders run up to four layer-0 tiles / six
+// inside the crop loop: the builders run up to four layer-0 tiles / two
 // layer-1 stages ahead of the tensor core.
 __global__ void __launch_bounds__(fz::kThreads + 32, 1)
     conv01_kernel(const uint8_t *__restrict__ codes, const bf16 *__restrict__ wb, const float *__restrict__ params,
@@ -658,10 +662,10 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
         if (ok && lane == 0) {
           tc::fence_after_sync();
           const uint32_t a0 = tmem + kColA + b * kColsA1;
-          const uint64_t b0 = w1_d + ks * (4 * 32 * 32 / 16);
+          const uint64_t b0 = w1_d + ks * (kChunksS1 / 2 * 32 * 32 / 16);
           const uint32_t d = tmem + 128u + (uint32_t)(mt * 32);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
+          for (int kk = 0; kk < kChunksS1 / 2; ++kk)
             tc::mma_bf16_ta(d, a0 + 8u * kk, b0 + kk * (32 * 32 / 16), idesc1, (ks | kk) != 0 ? 1u : 0u);
           tc::mma_commit(&empty1[b]);
         }
@@ -771,9 +775,9 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
       g0 += kTiles0;
       ok = builders_sync();  // act0 complete
       if (!ok) break;
-      // ---- layer 1: 4 M tiles x 7 K stages, six stages in flight ----
+      // ---- layer 1: 4 M tiles x 2 K stages, both in flight ----
       {
-        const int jj = tid >> 7;  // this thread's chunks of a stage: jj and jj + 4 (warp-uniform)
+        const int jj = tid >> 7;  // this thread's chunks of a stage: jj, jj + 4, ... (warp-uniform)
         const int ox = r & 7, oy = (r >> 3) & 7, ozl = r >> 6;
         for (int s = 0; s < kTiles1 * kStages1 && ok; ++s) {
           const int mt = s / kStages1, ks = s % kStages1;
@@ -787,9 +791,8 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
           const int low = (ox == 0) | ((oy == 0) << 1) | ((oz == 0) << 2) | 8;
           const uint32_t trow = tmem + lane_base + kColA + b * kColsA1;
 #pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const int j = jj + 4 * i;
-            const int2 ti = tapinfo[ks * 8 + j];
+          for (int j = jj; j < kChunksS1; j += 4) {
+            const int2 ti = tapinfo[ks * kChunksS1 + j];
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if ((low & ti.y) == 0) v = *(const uint4 *)(act0 + base + ti.x);
             tc::tmem_st4(trow + 4u * j, v);
@@ -836,32 +839,35 @@ __global__ void __launch_bounds__(fz::kThreads + 32, 1)
 // MMA sequence and same epilogues as the generic implicit GEMM, so the
 // outputs are bit-identical.  Two persistent CTAs per SM, each 8 builder
 // warps (A from the staged input into TMEM, B = the weight stage into
-// shared memory by cp.async) and one MMA warp, four stages in flight on
-// full/empty mbarriers; the next tile's input is staged while the current
-// tile's last MMAs run.
+// shared memory by cp.async) and one MMA warp, two stages of K = 128 in
+// flight on full/empty mbarriers (wider stages, fewer barrier round trips:
+// 2.777 M against 2.758 M views/s with four stages of 64); the next tile's
+// input is staged while the current tile's last MMAs run.
 // ---------------------------------------------------------------------------
 namespace c23 {
 constexpr int kBuilders = 256;                   // builder threads (plus one MMA warp); two CTAs per SM
 constexpr int kParts = kBuilders / 128;          // builders per tile row
-constexpr int kBuf = 4;
-constexpr int kStageB = 64 * 64 * 2;             // 8 KB of weights per stage (A stages live in TMEM)
+constexpr int kSC = 16;                          // 16-byte K chunks per stage row (K = 128 per stage)
+constexpr int kBuf = 2;                          // stages in flight
+constexpr int kStageB = 64 * kSC * 16;           // weights per stage (A stages live in TMEM)
 constexpr int kMaxIn = 2 * 8 * 8 * 8 * 32 * 2;   // two crops of layer 2's input: 64 KB
 constexpr int kOffIn = 0;
 constexpr int kOffStage = kOffIn + kMaxIn;
 constexpr int kOffTap = kOffStage + kBuf * kStageB;
 constexpr int kSmem = kOffTap + 256 * 8;         // 100,352 B
-constexpr uint32_t kColA = 64, kColsA = 32;      // TMEM: accumulator in columns 0-63, A stages after it
+constexpr uint32_t kColA = 64, kColsA = 4 * kSC;  // TMEM: accumulator in columns 0-63, A stages after it
 constexpr uint32_t kTmemCols = 256;
+static_assert(kColA + kBuf * kColsA <= kTmemCols && kSC % 2 == 0 && kSC <= 32, "conv23 stages");
 
 template <int L>
 struct Geo;
 template <>
 struct Geo<2> {
-  static constexpr int din = 8, stride = 2, cin = 32, cg = 4, stages = 14;
+  static constexpr int din = 8, stride = 2, cin = 32, cg = 4, stages = (27 * cg + kSC - 1) / kSC;
 };
 template <>
 struct Geo<3> {
-  static constexpr int din = 4, stride = 1, cin = 64, cg = 8, stages = 27;
+  static constexpr int din = 4, stride = 1, cin = 64, cg = 8, stages = (27 * cg + kSC - 1) / kSC;
 };
 }  // namespace c23
 
@@ -887,7 +893,8 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 2)
   const int64_t n_tiles = (n_views + 1) / 2;
 
   if (tid < 64) sbias[tid] = bias[tid];
-  for (int kc = tid; kc < G::stages * 8; kc += blockDim.x) {
+  static_assert(G::stages * kSC <= 256, "tap table");
+  for (int kc = tid; kc < G::stages * kSC; kc += blockDim.x) {
     // chunk kc = tap * cg + channel group: input offset relative to the output
     // voxel's own, and the padding cases it falls into (bit 6: past K)
     const int tap = kc / G::cg, cgi = kc % G::cg;
@@ -929,7 +936,7 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 2)
           const uint64_t b0 = stg_d + (b * kStageB >> 4);
           const uint32_t a0 = tmem + kColA + b * kColsA;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
+          for (int kk = 0; kk < kSC / 2; ++kk)
             tc::mma_bf16_ta(tmem, a0 + 8u * kk, b0 + kk * (64 * 32 / 16), idesc, (ks | kk) != 0 ? 1u : 0u);
           tc::mma_commit(&empty[b]);
         }
@@ -993,9 +1000,9 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 2)
         uint8_t *sb = stg + b * kStageB;
         const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + kColA + b * kColsA;
 #pragma unroll
-        for (int i = 0; i < 512 / kBuilders; ++i) {  // B: weight rows 0..63, K chunks 8 ks .. 8 ks + 7
-          const int c = tid + kBuilders * i, br = c >> 3, bj = c & 7;
-          const int kc = ks * 8 + bj;
+        for (int i = 0; i < 64 * kSC / kBuilders; ++i) {  // B: weight rows 0..63, K chunks kSC ks ..
+          const int c = tid + kBuilders * i, br = c / kSC, bj = c % kSC;
+          const int kc = ks * kSC + bj;
           const bool valid = kc < kChunks;
           const bf16 *src = w + (valid ? (size_t)br * kK + kc * 8 : 0);
           tc::cp_async16(tc::smem_u32(sb + (bj >> 1) * (64 * 32) + (br >> 3) * 256 + (bj & 1) * 128 + (br & 7) * 16),
@@ -1003,9 +1010,9 @@ __global__ void __launch_bounds__(c23::kBuilders + 32, 2)
         }
         tc::cp_async_commit();
 #pragma unroll
-        for (int i = 0; i < 8 / kParts; ++i) {  // A: im2col from the staged input
+        for (int i = 0; i < kSC / kParts; ++i) {  // A: im2col from the staged input
           const int j = jj + kParts * i;
-          const int2 ti = tapinfo[ks * 8 + j];
+          const int2 ti = tapinfo[ks * kSC + j];
           uint4 v = make_uint4(0u, 0u, 0u, 0u);
           if ((rowmask & ti.y) == 0) v = *(const uint4 *)(sin + base + ti.x);
           tc::tmem_st4(trow + 4u * j, v);
