@@ -44,7 +44,14 @@ struct LayerDims {
 };
 constexpr LayerDims kL[kLayers] = {{8, 16, 2, 32, 16}, {16, 32, 2, 16, 8}, {32, 64, 2, 8, 4}, {64, 64, 1, 4, 4}};
 // (the device-side weight copy kernel repeats these channel counts as literals)
-constexpr int kSplitBytes = 64 << 20;  // weight-gradient split-K partials
+constexpr int kSplitBytes = 64 << 20;  // split-K partials (weight gradients, fc1)
+constexpr int kFc1Splits = 4;            // fc1: 32 row tiles of a 4096 batch x 4 K splits = 128 CTAs
+// The splits launch_gemm makes of fc1's K stages of 64 (it rounds to whole stages per split).
+constexpr int fc1_splits() {
+  constexpr int stages = (kFcIn + 63) / 64, per = (stages + kFc1Splits - 1) / kFc1Splits;
+  return (stages + per - 1) / per;
+}
+static_assert((int64_t)kFc1Splits * 4096 * kHid * 4 <= kSplitBytes, "fc1 partials of the largest batch");
 
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
@@ -1228,6 +1235,17 @@ __global__ void colsum_kernel(const bf16 *__restrict__ a, int64_t rows, int cols
 }
 
 // Split-K weight gradients: dW[co][k] = sum_z part[z][k][co], fixed z order.
+// fc1's split-K partials (planes of n x 128 FP32) summed in split order, plus bias, ReLU, BF16.
+__global__ void fc1_reduce_kernel(const float *__restrict__ part, int splits, int n, const float *__restrict__ bias,
+                                  bf16 *__restrict__ h1) {
+  const int64_t total = (int64_t)n * kHid;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    float acc = part[e];
+    for (int z = 1; z < splits; ++z) acc += part[z * total + e];
+    h1[e] = __float2bfloat16_rn(fmaxf(acc + bias[e % kHid], 0.0f));
+  }
+}
+
 __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, int krows, int cout,
                                     float *__restrict__ dw) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1565,11 +1583,16 @@ int forward_batch(nbt_surrogate net, const uint8_t *crops, const bf16 *feats, in
   }
   put_feats_kernel<<<(n * kFeat + 255) / 256, 256, 0, s>>>(feats, net->x, n);
   NBT_CUDA_TRY(cudaGetLastError());
+  // fc1 (K = 4104: 65 stages of 64) split over K so that its ceil(n / 128) row tiles fill the SMs;
+  // the partials are summed in split order with the bias and ReLU by fc1_reduce_kernel
   const MatLoader la{net->x, n, kFcIn, kFcIn};
   const MatLoader lb{net->f1b, kHid, kFcIn, kFcIn};
-  const EpiBiasRelu ep{net->h1, net->params + kP.g1, kHid, kHid};
-  int rc = gemm(la, lb, ep, n, kHid, kFcIn, 1, s);
+  const EpiF32 ep{net->part, kHid, kHid, (int64_t)n * kHid};
+  int rc = gemm(la, lb, ep, n, kHid, kFcIn, kFc1Splits, s);
   if (rc != NBT_OK) return rc;
+  fc1_reduce_kernel<<<grid_1d((int64_t)n * kHid), 256, 0, s>>>(net->part, fc1_splits(), n, net->params + kP.g1,
+                                                              net->h1);
+  NBT_CUDA_TRY(cudaGetLastError());
   fc2_forward_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(net->h1, net->params, n, pred ? pred : net->y);
   NBT_CUDA_TRY(cudaGetLastError());
   return NBT_OK;
