@@ -498,6 +498,7 @@ int nbt_map_create(const nbt_map_desc *desc, nbt_map *out) {
     tab[d.nx + d.ny + z] = (int32_t)(pz[z >> lb] * b3 + (int64_t)(z & mask) * brick * brick);
 
   m->payload_bytes = d.encoding == NBT_F32_PROB ? m->elems * 4 : (d.encoding == NBT_U2_STATE ? m->elems / 4 : m->elems);
+  m->payload_bytes = (m->payload_bytes + 15) / 16 * 16;  // whole 16-byte words: walks may read the word of the last element
   const int64_t dense_bytes = (int64_t)d.nx * d.ny * d.nz * elem_size(d.encoding);
   m->stage_bytes = std::min(dense_bytes, std::max<int64_t>(kStageBytes, (int64_t)d.nx * d.ny * elem_size(d.encoding)));
   int rc = NBT_OK;

@@ -353,14 +353,21 @@ __device__ __forceinline__ int skip_axis_jump(float &b, float s, float o, float 
 }
 
 // The walk_count loop from the current voxel (payload entry raw, already
-// loaded) for at most `passes` passes of three voxels, up to the first
-// occupied voxel or the first crossing not before tlim.  The walk state ends
-// one crossing past the last visited voxel (so the plane travel is the number
-// visited); last = state of the last visited voxel, ts_out = the crossing the
-// loop stopped on (before tlim if it stopped on the pass count).
+// loaded: the state byte on 1-byte maps, the 32-bit word holding its 2-bit
+// state on 2-bit maps) for at most `passes` passes of three voxels, up to the
+// first occupied voxel or the first crossing not before tlim.  The walk state
+// ends one crossing past the last visited voxel (so the plane travel is the
+// number visited); sacc = the sum of the visited voxels' states (every
+// visited voxel but the last is unknown, 0, or free, 1, so the caller gets
+// the unknown count from it, the visited count and the last state with one
+// add per voxel instead of a test and a conditional add); last = state of the
+// last visited voxel, ts_out = the crossing the loop stopped on (before tlim
+// if it stopped on the pass count).  2-bit maps are read a 32-bit word (16
+// voxels) at a time: the state of element e is bits 2 (e mod 16) of word
+// e / 16, one funnel shift away.
 template <int KIND>
 __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, uint32_t addr, const uint8_t *payload,
-                                               uint32_t addr_max, float tlim, int passes, uint32_t &iacc,
+                                               uint32_t addr_max, float tlim, int passes, uint32_t &sacc,
                                                uint32_t &last, float &ts_out) {
 #define NBT_RUN_PART                                                                             \
   "min.f32 ts, %0, %1, %2;\n\t"                                                                 \
@@ -387,12 +394,11 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
   NBT_RUN_PART                                                                                   \
   "mad.wide.u32 a, lc, %26, %24;\n\t"                                                           \
   "@!pm ld.global.nc.u8 " NXT ", [a];\n\t"                                                      \
-  "setp.eq.u32 pu, " CUR ", 0;\n\t"                                                             \
-  "@pu mad.lo.s32 %7, %26, %26, %7;\n\t"                                                        \
+  "add.u32 %7, %7, " CUR ";\n\t"                                                                \
   "setp.gt.or.u32 pe, " CUR ", 1, pm;\n\t"
     asm volatile(
         "{\n\t"
-        ".reg .pred px, py, pz, pm, pu, pe, pc;\n\t"
+        ".reg .pred px, py, pz, pm, pe, pc;\n\t"
         ".reg .f32 ts, u;\n\t"
         ".reg .b32 r0, r1, r2, lc, cnt;\n\t"
         ".reg .b64 a;\n\t"
@@ -414,7 +420,7 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
         "DONE:\n\t"
         "mov.f32 %9, ts;\n\t"
         "}"
-        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+r"(iacc),
+        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+r"(sacc),
           "=r"(last), "=f"(ts_out)
         : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
           "f"(w.vz), "f"(tlim), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit),
@@ -424,20 +430,18 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
   } else {
 #define NBT_U2_RUN(CUR, SC, NXT, SN)                                                             \
   NBT_RUN_PART                                                                                   \
-  "shr.u32 wb, lc, 2;\n\t"                                                                       \
-  "mad.wide.u32 a, wb, %26, %24;\n\t"                                                           \
-  "@!pm ld.global.nc.u8 " NXT ", [a];\n\t"                                                      \
+  "shr.u32 wb, lc, 4;\n\t"                                                                       \
+  "mad.wide.u32 a, wb, 4, %24;\n\t"                                                             \
+  "@!pm ld.global.nc.b32 " NXT ", [a];\n\t"                                                     \
   "mad.lo.s32 " SN ", lc, %27, 0;\n\t"                                                          \
-  "mul.lo.u32 st, " CUR ", 16843009;\n\t"                                                       \
-  "shf.r.wrap.b32 st, st, st, " SC ";\n\t"                                                      \
+  "shf.r.wrap.b32 st, " CUR ", " CUR ", " SC ";\n\t"                                            \
   "and.b32 st, st, 3;\n\t"                                                                      \
-  "setp.eq.u32 pu, st, 0;\n\t"                                                                  \
-  "@pu mad.lo.s32 %7, %26, %26, %7;\n\t"                                                        \
+  "add.u32 %7, %7, st;\n\t"                                                                     \
   "setp.gt.or.u32 pe, st, 1, pm;\n\t"
     const uint32_t s_first = addr * 2u;
     asm volatile(
         "{\n\t"
-        ".reg .pred px, py, pz, pm, pu, pe, pc;\n\t"
+        ".reg .pred px, py, pz, pm, pe, pc;\n\t"
         ".reg .f32 ts, u;\n\t"
         ".reg .b32 r0, r1, r2, s0, s1, s2, lc, wb, st, cnt;\n\t"
         ".reg .b64 a;\n\t"
@@ -454,7 +458,7 @@ __device__ __forceinline__ void walk_count_run(Walk &w, int &lin, uint32_t raw, 
         "mov.b32 %8, st;\n\t"
         "mov.f32 %9, ts;\n\t"
         "}"
-        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+r"(iacc),
+        : "+f"(w.tx), "+f"(w.ty), "+f"(w.tz), "+f"(w.bx), "+f"(w.by), "+f"(w.bz), "+r"(lin), "+r"(sacc),
           "=r"(last), "=f"(ts_out)
         : "r"(raw), "f"(w.sx), "f"(w.sy), "f"(w.sz), "f"(w.ox), "f"(w.oy), "f"(w.oz), "f"(w.vx), "f"(w.vy),
           "f"(w.vz), "f"(tlim), "r"(w.qx), "r"(w.qy), "r"(w.qz), "l"(payload), "r"(addr_max), "r"(unit),
@@ -644,18 +648,24 @@ __device__ __forceinline__ void ray_skip(const DevMap &m, uint32_t addr_max, con
       // vote, so the lanes stay in step
       const float bx0 = w.bx, by0 = w.by, bz0 = w.bz;
       const uint32_t addr = min((uint32_t)lin, addr_max);
-      const uint32_t raw = raw_load<KIND>(payload, addr);
+      // the first voxel's payload entry (2-bit maps: the 32-bit word holding it)
+      const uint32_t raw = KIND == PAYLOAD_U2 ? __ldg((const uint32_t *)payload + (addr >> 4))
+                                             : raw_load<KIND>(payload, addr);
       uint32_t last = 0u;
       float ts = 0.0f;
       bool occ;
+      uint32_t sacc = 0u;
       if constexpr (KIND == PAYLOAD_GAIN_F32) {
         walk_gain_run<HIT>(w, lin, raw, (const float *)m.payload, addr_max, w.tmax, kRunPasses, facc, last, ts);
         occ = (int32_t)last < 0;                     // sign bit: occupied
       } else {
-        walk_count_run<KIND>(w, lin, raw, addr, payload, addr_max, w.tmax, kRunPasses, iacc, last, ts);
+        walk_count_run<KIND>(w, lin, raw, addr, payload, addr_max, w.tmax, kRunPasses, sacc, last, ts);
         occ = last >= 2u;
       }
-      steps += (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
+      const uint32_t nvis = (uint32_t)(fabsf(w.bx - bx0) + fabsf(w.by - by0) + fabsf(w.bz - bz0));
+      steps += nvis;
+      // every visited voxel but the last has state 0 (unknown) or 1 (free)
+      if constexpr (KIND != PAYLOAD_GAIN_F32) iacc += nvis - 1u - (sacc - last) + (last == 0u ? 1u : 0u);
       done = occ || !(ts < w.tmax);                  // occluded, or the walk's end reached
     }
   }
