@@ -1142,7 +1142,7 @@ def run_surrogate(args, nbt, torch, dev, stream, world, rank, local, dist) -> No
         "e2e": {"value": job_throughput(n * args.steps, world, e2e_total), "unit": "views/s",
                 "h2d_bytes_per_step": int(pz_host.numel() * 4), "d2h_bytes_per_step": int(sc_host.numel() * 4)},
         # per batch: crops, fused layers 0-1, layer 2, layer 3, features, fc1 GEMM, fc2
-        "gpu_launches": 7 * n_b * args.steps,
+        "gpu_launches": 8 * n_b * args.steps,   # per batch: crops, conv01, conv23 x 2, features, fc1, fc1 reduce, fc2
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -1495,9 +1495,10 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
                 "h2d_bytes_per_step": int(grid_h.numel() + poses_h.numel() * 4),
                 "d2h_bytes_per_step": int(best_h.numel() * 4 + val_h.numel() * 4)},
         # per timed step, pruned arm: upload (1) + brick summaries of the new map (5) + per batch of 4096
-        # (crops, fused layers 0-1, layer 2, layer 3, features, fc1, fc2) + top-k + tile kernel + reduce +
-        # argmax; exact arm: upload (1) + brick summaries (5) + tile kernel + reduce + argmax
-        "gpu_launches": ((1 + 5 + 7 * n_chunks + 4) + (1 + 5 + 3)) * args.steps,
+        # (crops, fused layers 0-1, layer 2, layer 3, features, fc1, fc1 reduce, fc2) + top-k + tile
+        # kernel + reduce + argmax; exact arm: upload (1) + brick summaries (5) + tile kernel + reduce +
+        # argmax
+        "gpu_launches": ((1 + 5 + 8 * n_chunks + 4) + (1 + 5 + 3)) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
