@@ -189,6 +189,26 @@ __global__ void brick_summary_kernel(const uint8_t *__restrict__ payload, int nx
     const int y0 = (int)((b / bsx) % bsy) * kSkipB;
     const int z0 = (int)(b / ((int64_t)bsx * bsy)) * kSkipB;
     const int x1 = min(x0 + kSkipB, nx), y1 = min(y0 + kSkipB, ny), z1 = min(z0 + kSkipB, nz);
+    if ((nx & 7) == 0 && x1 - x0 == 8) {
+      // whole 8-voxel rows (nx a multiple of 8): one aligned 16-bit (2-bit states) or 64-bit (bytes)
+      // word per row, compared with the first voxel's class repeated
+      const int64_t v0 = ((int64_t)z0 * ny + y0) * nx + x0;
+      uint32_t first = ENC == NBT_U2_STATE ? payload[v0 >> 2] & 3u : payload[v0];
+      bool uniform = first < 2u;
+      const uint64_t pat = first ? (ENC == NBT_U2_STATE ? 0x5555ull : 0x0101010101010101ull) : 0ull;
+      for (int z = z0; z < z1 && uniform; ++z)
+        for (int y = y0; y < y1; ++y) {
+          const int64_t v = ((int64_t)z * ny + y) * nx + x0;
+          const uint64_t w = ENC == NBT_U2_STATE ? (uint64_t)*(const uint16_t *)(payload + (v >> 2))
+                                                 : *(const uint64_t *)(payload + v);
+          if (w != pat) {
+            uniform = false;
+            break;
+          }
+        }
+      bsum[b] = (uint8_t)(uniform ? first : kSumOther);
+      continue;
+    }
     uint32_t first = 4u;
     bool uniform = true;
     for (int z = z0; z < z1 && uniform; ++z)
