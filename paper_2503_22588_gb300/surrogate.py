@@ -81,6 +81,29 @@ def crops(m: Map, poses: torch.Tensor, cam: Camera, params: IgParams, stream=Non
     return cr, ft
 
 
+def save_checkpoint(state: dict, path) -> None:
+    """Write a ``Surrogate.checkpoint()`` to ``path`` (numpy ``.npz``): the flat FP32 parameters in the
+    nbt_surrogate layout, both Adam moments, the Adam step count and the target scale."""
+    params = np.ascontiguousarray(state["params"], np.float32)
+    if params.size != param_count():
+        raise ValueError(f"checkpoint holds {params.size} parameters, the network has {param_count()}")
+    np.savez(path, params=params, adam_m=np.ascontiguousarray(state["adam_m"], np.float32),
+             adam_v=np.ascontiguousarray(state["adam_v"], np.float32), step=np.int64(state["step"]),
+             target_scale=np.float64(state["target_scale"]))
+
+
+def load_checkpoint(path) -> dict:
+    """Read a checkpoint written by ``save_checkpoint`` (the dict ``Surrogate.restore`` takes)."""
+    with np.load(path) as z:
+        state = {"params": z["params"].astype(np.float32), "adam_m": z["adam_m"].astype(np.float32),
+                 "adam_v": z["adam_v"].astype(np.float32), "step": int(z["step"]),
+                 "target_scale": float(z["target_scale"])}
+    n = param_count()
+    if any(state[k].size != n for k in ("params", "adam_m", "adam_v")):
+        raise ValueError(f"checkpoint does not hold {n} parameters per tensor")
+    return state
+
+
 class Surrogate:
     """nbt_surrogate: network, Adam state and activation buffers on the current device."""
 
@@ -120,6 +143,14 @@ class Surrogate:
         check(lib().nbt_surrogate_set_adam(self.handle, m.ctypes.data, v.ctypes.data, m.size, int(state["step"])),
               "nbt_surrogate_set_adam")
         self.set_target_scale(state["target_scale"])
+
+    def save(self, path) -> None:
+        """``checkpoint()`` written to a file (``save_checkpoint``)."""
+        save_checkpoint(self.checkpoint(), path)
+
+    def load(self, path) -> None:
+        """``restore()`` from a file written by ``save``: training continues from it bit for bit."""
+        self.restore(load_checkpoint(path))
 
     @property
     def handle(self) -> int:

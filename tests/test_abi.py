@@ -213,3 +213,28 @@ def test_handles_that_name_no_live_map_are_rejected_without_reading_them(libnbt)
     t = _lib.Tuning(8, 0, 0)
     assert L.nbt_map_set_tuning(bogus, C.byref(t)) == -1
     assert L.nbt_map_get_tuning(bogus, C.byref(t)) == -1
+
+
+def test_surrogate_checkpoint_file_round_trip_is_bitwise(tmp_path):
+    """save_checkpoint / load_checkpoint keep every bit of the parameters and Adam moments, the step
+    count and the target scale; a file of the wrong size is refused (no GPU needed)."""
+    import numpy as np
+    from paper_2503_22588_gb300 import surrogate as gs
+    n = gs.param_count()
+    rng = np.random.default_rng(0)
+    state = {"params": rng.standard_normal(n).astype(np.float32),
+             "adam_m": rng.standard_normal(n).astype(np.float32) * 1e-3,
+             "adam_v": np.abs(rng.standard_normal(n)).astype(np.float32) * 1e-6,
+             "step": 123456789012, "target_scale": 0.01}
+    state["params"][:3] = [np.float32(-0.0), np.float32(1e-45), np.float32(3.4e38)]
+    gs.save_checkpoint(state, tmp_path / "ck.npz")
+    got = gs.load_checkpoint(tmp_path / "ck.npz")
+    for k in ("params", "adam_m", "adam_v"):
+        assert got[k].dtype == np.float32 and got[k].tobytes() == state[k].tobytes(), k
+    assert got["step"] == state["step"] and got["target_scale"] == state["target_scale"]
+    with pytest.raises(ValueError):
+        gs.save_checkpoint({**state, "params": state["params"][:-1]}, tmp_path / "bad.npz")
+    np.savez(tmp_path / "short.npz", params=state["params"][:-1], adam_m=state["adam_m"],
+             adam_v=state["adam_v"], step=np.int64(1), target_scale=np.float64(1.0))
+    with pytest.raises(ValueError):
+        gs.load_checkpoint(tmp_path / "short.npz")

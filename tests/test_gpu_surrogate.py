@@ -440,9 +440,9 @@ def test_target_scale_equals_prescaled_targets_bitwise():
     b.close()
 
 
-def test_checkpoint_resume_is_bitwise():
-    """N Adam steps in one go equal k steps, a checkpoint restored into a fresh network, and N - k
-    more steps: parameters, Adam moments and step count bit for bit."""
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    """N Adam steps in one go equal k steps, a checkpoint written to a file and loaded into a fresh
+    network, and N - k more steps: parameters, Adam moments and step count bit for bit."""
     cr, ft = _batch(16, seed=9)
     t = torch.rand(16, device="cuda", generator=torch.Generator(device="cuda").manual_seed(2))
     params = S.init_params(10)
@@ -454,9 +454,11 @@ def test_checkpoint_resume_is_bitwise():
         a.train_step(cr, ft, t, lr=1e-3 * (1 + i % 3))
     state = a.checkpoint()
     assert state["step"] == 3
+    a.save(tmp_path / "surrogate.npz")
     a.close()
     b = gs.Surrogate(max_batch=16)
-    b.restore(state)
+    b.load(tmp_path / "surrogate.npz")
+    assert b.target_scale == 0.5
     for i in range(3, 7):
         b.train_step(cr, ft, t, lr=1e-3 * (1 + i % 3))
     want, got = ref.checkpoint(), b.checkpoint()
