@@ -1154,7 +1154,7 @@ def run_surrogate(args, nbt, torch, dev, stream, world, rank, local, dist) -> No
     m.close()
 
 
-PRUNED_MIN_SCENES = 50   # agreement is scored on at least this many scenes (8 PoIs each: >= 400 cases)
+PRUNED_MIN_SCENES = 100  # agreement is scored on at least this many scenes (8 PoIs each: >= 800 cases)
 PRUNED_SEG, PRUNED_KEEP = 4096, 205
 
 
@@ -1265,7 +1265,7 @@ def run_pruned(args, nbt, torch, dev, world, rank, local, dist) -> None:
     arm uploads the map and runs nbt_plan_pruned (crops and network scores of every candidate, the top
     5 % per PoI raycast exactly, the best of them); the exact arm uploads the map and raycasts every
     candidate.  Both are timed with CUDA events on the launching stream, the L2 flushed before each.
-    The same-best-view rate is scored on at least 50 scenes (>= 400 PoI cases); scenes beyond the
+    The same-best-view rate is scored on at least 100 scenes (>= 800 PoI cases); scenes beyond the
     timed steps are evaluated untimed.
     """
     import math
