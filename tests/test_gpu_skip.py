@@ -62,10 +62,12 @@ def test_boxes_spheres_half_unknown(enc):
     run_case(grid, enc, pz, cam)
 
 
-@pytest.mark.parametrize("enc", ["u8", "u2"])
-def test_room_with_partial_bricks_and_an_offset_origin(enc):
-    """Sides 101 x 77 x 90 (no multiple of 8), origin off the grid, cameras inside and outside."""
-    grid = scenes.room_states(128, 150, 0.4, seed=5)[:90, :77, :101]
+@pytest.mark.parametrize("enc,nx", [("u8", 101), ("u2", 101), ("u8", 96), ("u2", 96)])
+def test_room_with_partial_bricks_and_an_offset_origin(enc, nx):
+    """Sides nx x 77 x 90, origin off the grid, cameras inside and outside.  nx = 101: no side a
+    multiple of 8 (summaries voxel by voxel); nx = 96: whole 8-voxel rows read as one word each,
+    bricks cut short along y and z."""
+    grid = scenes.room_states(128, 150, 0.4, seed=5)[:90, :77, :nx]
     origin = (-0.0123, 0.0377, 0.0049)
     c = np.array([0.5, 0.38, 0.45])
     pz = np.concatenate([shell(c, 64, 0.05, 0.3, 2), shell(c, 64, 0.6, 1.2, 3)])
